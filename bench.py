@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""X-ray projections/s of the radiative Gaussian rasterizer on one GB300, with roofline.
+
+Workload (default ``train50k``): 50,000 Gaussians uniform in the scanned cuboid (log-scales
+U[-5,-3] of the cuboid side, random unit quaternions, opacity U[0.05,0.5], intensity
+U[0,1]), 50 cone-beam views evenly spaced over 360 degrees (L_SO 1000 mm, L_SD 1500 mm,
+1 mm pitch), 256x256 detector, 16x16 tiles.  One step = forward of all 50 views
+(project, bin + radix sort, composite), the L1 loss against phantom projections, and the
+backward pass to every Gaussian parameter.  Throughput = views processed per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank runs its own replica of the workload (weak scaling, no
+collective); rank 0 prints one JSON line.  ``--impl reference`` times the CPU oracle on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: Gaussians, views, detector W, H, tile, seed id
+    "train50k": dict(n=50_000, views=50, W=256, H=256, tile=(16, 16), cid=1),
+    "fwd10k": dict(n=10_000, views=1, W=128, H=128, tile=(16, 16), cid=0),
+    "batch100k": dict(n=100_000, views=100, W=256, H=256, tile=(16, 16), cid=2),
+}
+METRIC = "X-ray projections/s fwd and fwd+bwd (50k Gaussians, 256²) and % of roofline"
+
+# FP32 lane instructions charged per evaluated (pixel, list entry) pair of the compositing
+# kernels, and per contributing pair on top ("Roofline").
+FWD_OPS_EVAL, FWD_OPS_CONTRIB = 20, 4
+BWD_OPS_EVAL, BWD_OPS_CONTRIB = 20, 30
+SMS, FP32_LANES = 152, 128
+
+# DRAM traffic per launch from an ncu capture, valid while the kernel source is unchanged.
+TRAFFIC = {}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="train50k")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def _workload(name: str):
+    from paper_2403_04116_gb300 import synth
+    w = WORKLOADS[name]
+    side = synth.scene_side_mm(w["W"])
+    g = synth.gaussians(w["n"], side, synth.rng(w["cid"], 0))
+    views = synth.circular_views(w["views"], w["W"], w["H"])
+    ph = synth.ellipsoid_phantom(10, side, synth.rng(w["cid"], 1))
+    return w, g, views, ph
+
+
+def _config(name: str, w: dict, n_gpus: int) -> dict:
+    return {"workload": name, "gaussians": w["n"], "views": w["views"], "detector": [w["W"], w["H"]],
+            "tile": list(w["tile"]), "loss": "L1 vs FP64 ellipsoid-phantom projections",
+            "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{n_gpus}"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _source_sha(kernel_file: str) -> str:
+    path = os.path.join(ROOT, "paper_2403_04116_gb300", "csrc", kernel_file)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (the baseline and the reference arm)
+# ------------------------------------------------------------------------------------------
+
+def cpu_oracle_rate(name: str, target_seconds: float = 12.0) -> dict:
+    """Oracle forward + gradient (FP64, all host cores) on a bounded sample of the workload:
+    whole views while one view takes under ``target_seconds``, else a random pixel sample
+    of one view; projections/s scaled from the sample."""
+    import oracle
+    from paper_2403_04116_gb300 import synth
+    w, g, views, ph = _workload(name)
+    npx = views[0].width * views[0].height
+    gen = np.random.default_rng(7)
+
+    def run(view_ids, pix=None) -> float:
+        tg = synth.phantom_targets(ph, [views[i] for i in view_ids])
+        t0 = time.perf_counter()
+        for k, i in enumerate(view_ids):
+            v = views[i]
+            r = oracle.render64(g, v, pixels=pix)
+            G = np.sign(np.nan_to_num(r["image"]) - tg[k]) / npx
+            if pix is not None:
+                mask = np.zeros(npx, bool)
+                mask[pix] = True
+                G.reshape(-1)[~mask] = 0.0
+            oracle.grad64(g, v, G, pixels=pix)
+        return time.perf_counter() - t0
+
+    t1 = run([0])
+    if t1 >= target_seconds:
+        p = max(256, int(npx * target_seconds / t1))
+        pix = np.sort(gen.choice(npx, size=p, replace=False)).astype(np.int32)
+        t = run([0], pix)
+        rate, sample = (p / npx) / t, f"view 0 of {w['views']}, {p} of {npx} pixels sampled at random, {t:.1f} s"
+    else:
+        k = max(1, min(len(views), int(round(target_seconds / t1))))
+        ids = list(range(0, len(views), max(1, len(views) // k)))[:k]
+        t = run(ids)
+        rate, sample = len(ids) / t, f"{len(ids)} of {w['views']} views, all pixels, {t:.1f} s"
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": rate, "unit": "projections/s", "cores": threads, "kind": "oracle",
+            "sample": f"FP64 oracle forward + gradient (L1 vs phantom), {sample}"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    per_step = 3.0
+    for _ in range(args.warmup):
+        cpu_oracle_rate(args.workload, target_seconds=0.5)
+    rates = [cpu_oracle_rate(args.workload, target_seconds=per_step) for _ in range(args.steps)]
+    value = statistics.median(r["value"] for r in rates)
+    line = {"metric": METRIC, "value": value, "unit": "projections/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * w["views"] / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(args.workload, w, 1), "impl": "reference",
+            "cpu_baseline": {**rates[-1], "value": value},
+            "e2e": {"value": value, "unit": "projections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+def run_ours(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_2403_04116_gb300 import binding as B
+    from paper_2403_04116_gb300 import synth
+    from paper_2403_04116_gb300.render import Frame, FrameConfig, L1Loss, Renderer, loss_l1_into, render
+
+    B.lib(build_if_missing=True)
+    w, g, views, ph = _workload(args.workload)
+    V, H, W = w["views"], w["H"], w["W"]
+    targets_np = synth.phantom_targets(ph, views)
+    names = ("mean", "scale", "quat", "opacity", "intensity")
+    dev = tuple(torch.from_numpy(g[k]).cuda() for k in names)
+    target = torch.from_numpy(targets_np).cuda()
+
+    # size the pair capacity from one binning pass
+    probe = Frame(w["n"], views, FrameConfig(*w["tile"]), pair_capacity=1 << 20)
+    probe.project(*dev)
+    probe.bin_sort()
+    pairs = int(probe.status().pairs)
+    del probe
+    cap = int(pairs * 1.05) + 4096
+    frame = Frame(w["n"], views, FrameConfig(*w["tile"]), pair_capacity=cap)
+
+    image = torch.empty((V, H, W), dtype=torch.float32, device="cuda")
+    grad_image = torch.empty_like(image)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    grads = tuple(torch.empty_like(t) for t in dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def fwd_step():
+        frame.project(*dev)
+        frame.bin_sort()
+        frame.render_fwd(image)
+
+    def step():
+        fwd_step()
+        loss_l1_into(image, target, grad_image, loss)
+        frame.render_bwd(dev, grad_image, grads)
+
+    def timed(fn, k: int, per_kernel: bool) -> tuple[float, dict]:
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        barrier()
+        torch.cuda.synchronize()
+        frame.read_timing()
+        frame.set_timing(per_kernel)
+        for i in range(k):
+            flush.fill_(i & 0xFF)
+            starts[i].record()
+            fn()
+            ends[i].record()
+        torch.cuda.synchronize()
+        barrier()
+        frame.set_timing(False)
+        kernels = frame.read_timing() if per_kernel else {}
+        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        return ms, kernels
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = frame.status()
+    if st.code != B.XG_OK:
+        raise RuntimeError(f"frame status {B.xg_status_str(st.code)}")
+
+    with ClockSampler(local) as clocks:
+        ms_total, kernels = timed(step, args.steps, per_kernel=True)
+    clock_info = clocks.summary()
+    st = frame.status()
+    ms_fwd, _ = timed(fwd_step, args.steps, per_kernel=False)
+
+    # max over ranks
+    t = torch.tensor([ms_total, ms_fwd], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total, ms_fwd = t.tolist()
+    ms_step = ms_total / args.steps
+    value = world * V * args.steps / (ms_total / 1000.0)
+    fwd_value = world * V * args.steps / (ms_fwd / 1000.0)
+
+    # roofline of the dominant kernel
+    peaks = _peaks()
+    ours = {k: v for k, v in kernels.items() if k != "memset"}
+    dom = max(ours, key=lambda k: ours[k][1])
+    launches, dom_ms = ours[dom]
+    avg_ms = dom_ms / launches
+    clock_mhz = peaks["sm_max_mhz"]
+    alu_peak = SMS * FP32_LANES * clock_mhz * 1e6 / 1e12  # T FP32 lane-instructions / s
+    if dom == "k_render_bwd":
+        ops = BWD_OPS_EVAL * st.bwd_evaluated + BWD_OPS_CONTRIB * st.bwd_contrib
+        roof = {"bound": "alu", "achieved": ops / (avg_ms * 1e-3) / 1e12, "peak": alu_peak, "unit": "TFP32op/s"}
+    elif dom == "k_render_fwd":
+        ops = FWD_OPS_EVAL * st.fwd_evaluated + FWD_OPS_CONTRIB * st.fwd_contrib
+        roof = {"bound": "alu", "achieved": ops / (avg_ms * 1e-3) / 1e12, "peak": alu_peak, "unit": "TFP32op/s"}
+    else:
+        VN = V * w["n"]
+        M = int(st.pairs)
+        algo = {"k_radix_scatter": 24 * M, "k_radix_hist": 4 * M, "k_project": 48 * w["n"] + 48 * VN,
+                "k_emit": 16 * VN + 12 * M, "k_project_bwd": 28 * VN + 56 * w["n"]}.get(dom, 0)
+        roof = {"bound": "hbm", "achieved": algo / (avg_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    src = {"k_render_bwd": "render.cu", "k_render_fwd": "render.cu", "k_radix_scatter": "binning.cu",
+           "k_radix_hist": "binning.cu", "k_project": "project.cu", "k_emit": "binning.cu",
+           "k_project_bwd": "project.cu"}.get(dom)
+    tr = TRAFFIC.get(dom)
+    roof["traffic"] = tr["bytes_per_launch"] if tr and src and tr["source_sha"] == _source_sha(src) else None
+    roof["kernel"] = dom
+    roof["peak_source"] = (f"{SMS} SMs x {FP32_LANES} FP32 lanes x {clock_mhz:.0f} MHz" if roof["bound"] == "alu"
+                           else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")
+    roof["avg_launch_ms"] = avg_ms
+
+    gpu_launches = sum(n for k, (n, _) in kernels.items() if k != "memset") + args.steps  # + the loss kernel
+
+    # end to end through the public API: pinned host inputs in, loss out, every step
+    e2e = None
+    if not args.no_e2e:
+        host = tuple(torch.from_numpy(g[k]).pin_memory() for k in names)
+        host_target = torch.from_numpy(targets_np).pin_memory()
+        renderer = Renderer(views, FrameConfig(*w["tile"]), pair_capacity=cap, check_capacity=False)
+        h2d = sum(t.numel() * 4 for t in host) + host_target.numel() * 4
+
+        def e2e_step():
+            ps = [t.cuda(non_blocking=True).requires_grad_(True) for t in host]
+            tg = host_target.cuda(non_blocking=True)
+            img = render(renderer, *ps)
+            lval = L1Loss.apply(img, tg)
+            lval.backward()
+            return float(lval.item())
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        el = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(el, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * V * args.steps / el.item(), "unit": "projections/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 4}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate(args.workload)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "projections/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": _config(args.workload, w, world),
+                "fwd": {"value": fwd_value, "unit": "projections/s", "ms_per_step": ms_fwd / args.steps},
+                "clocks": clock_info, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
+                "cpu_baseline": cpu, "pairs": int(st.pairs),
+                "work": {"fwd_evaluated": int(st.fwd_evaluated), "fwd_contrib": int(st.fwd_contrib),
+                         "bwd_evaluated": int(st.bwd_evaluated), "bwd_contrib": int(st.bwd_contrib)},
+                "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(kernels.items())}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * xg.h -- C ABI of the GB300 (sm_103a) radiative Gaussian rasterizer.
+ *
+ * The library renders X-ray projections of 3-D Gaussians and differentiates them: the
+ * Differentiable Radiative Rasterization of X-Gaussian (arXiv 2403.04116, Sec. 3.2,
+ * Eq. 5-10), with the cone-beam camera built from the scanner parameters of Sec. 3.3,
+ * Eq. 12.  A frame holds one batch of views that share a detector size; the four stages
+ * run as stream-ordered launches over every view of the frame at once:
+ *
+ *     xg_project    -> xg_bin_sort -> xg_render_fwd          (forward, Eq. 7-10)
+ *                                  -> xg_render_bwd          (gradients to every parameter)
+ *
+ * Conventions shared by every call
+ *   - Device pointers are CUDA device addresses of the current device; host pointers are
+ *     ordinary process memory.  Every array is dense, C order, FP32 unless stated.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - The caller owns every buffer, including the frame's device workspace.  The library
+ *     never allocates or frees device memory and never synchronises, except
+ *     xg_frame_read_status, which waits for `stream`.  The stage calls contain only kernel
+ *     launches and cudaMemsetAsync, so a sequence of them can be captured in a CUDA graph.
+ *   - Argument errors are returned at once, before anything is enqueued.  Conditions met on
+ *     the device (pair capacity exceeded) are recorded in a status word in the workspace;
+ *     after one, the later stages of the frame write zeros.  Read it with
+ *     xg_frame_read_status.  Gaussians with a non-finite attribute are skipped and counted.
+ *
+ * Gaussians (Sec. 3.1, Eq. 1-4) are structure-of-arrays, activated values:
+ *   mean[3][n] (mm, world frame whose origin is the rotation centre), scale[3][n] (mm, > 0),
+ *   quat[4][n] ((w, x, y, z), any non-zero norm; normalised inside), opacity[n] (the
+ *   paper's alpha_i, in [0, 1]), intensity[n] (the radiation intensity i of Eq. 3).
+ *
+ * Readings of the paper used by the kernels: focal length in pixels L_SD / pitch; pixel
+ * (x, y) samples the detector at (x + 1/2, y + 1/2) with the principal point at (W/2, H/2);
+ * Sigma'' gets 0.3 px^2 added on its diagonal; Gaussians with t_z <= near_mm are skipped;
+ * the opacity of Eq. 10 is sigma = min(0.99, alpha * density) and terms with sigma < 1/255
+ * are skipped; blending stops before a term that would take the transmittance below 1e-4;
+ * depth order is ascending t_z, ties by ascending Gaussian index; background 0.
+ */
+#ifndef XG_H
+#define XG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  XG_OK = 0,
+  XG_ERR_INVALID_ARG = 1, /* a pointer, size or geometry argument is unusable */
+  XG_ERR_CAPACITY = 2,    /* the frame's (view, tile, Gaussian) pairs exceed pair_capacity */
+  XG_ERR_CUDA = 3,        /* a CUDA launch or copy failed; see cudaGetLastError */
+  XG_ERR_WORKSPACE = 4,   /* the workspace is too small or misaligned */
+  XG_ERR_CHECK = 5        /* a device-side bounds check failed (a library defect); outputs invalid */
+} xg_status;
+
+/* One cone-beam projection (Sec. 3.3, Eq. 12).  The source orbits at distance sod_mm from
+ * the rotation centre in the z = 0 plane at azimuth angle_rad (elevation 0); the detector
+ * is sdd_mm from the source, width x height pixels of pitch_u_mm x pitch_v_mm. */
+typedef struct {
+  double sod_mm;     /* L_SO, > 0 */
+  double sdd_mm;     /* L_SD, > 0 */
+  double pitch_u_mm; /* detector pixel width, > 0 */
+  double pitch_v_mm; /* detector pixel height, > 0 */
+  double angle_rad;  /* azimuth phi of Eq. 9 and 12 */
+  int32_t width;     /* W, 1 .. 4096 */
+  int32_t height;    /* H, 1 .. 4096 */
+} xg_view;
+
+/* Device arrays of n Gaussians (see above).  n >= 1. */
+typedef struct {
+  const float* mean;
+  const float* scale;
+  const float* quat;
+  const float* opacity;
+  const float* intensity;
+  int64_t n;
+} xg_gaussians;
+
+/* Device arrays receiving dL/d(parameter), same shapes as xg_gaussians; overwritten. */
+typedef struct {
+  float* mean;
+  float* scale;
+  float* quat;
+  float* opacity;
+  float* intensity;
+} xg_grads;
+
+/* Frame configuration.  tile_w, tile_h in {8, 16, 32} with tile_w * tile_h <= 512;
+ * near_mm > 0; 1 <= pair_capacity < 2^31. */
+typedef struct {
+  int32_t tile_w;
+  int32_t tile_h;
+  float near_mm;
+  int32_t reserved; /* set to 0 */
+  int64_t pair_capacity;
+} xg_config;
+
+/* Device-side status of a frame, read back by xg_frame_read_status. */
+typedef struct {
+  int32_t code;      /* XG_OK, XG_ERR_CAPACITY or XG_ERR_CHECK */
+  int32_t reserved;
+  int64_t pairs;     /* (view, tile, Gaussian) pairs of the last xg_bin_sort */
+  int64_t nonfinite; /* Gaussians skipped for a non-finite attribute, summed over xg_project calls */
+  /* work done since the last xg_bin_sort, for throughput accounting: (pixel, list entry)
+   * pairs whose opacity was evaluated, and how many of them contributed */
+  int64_t fwd_evaluated, fwd_contrib;
+  int64_t bwd_evaluated, bwd_contrib;
+} xg_device_status;
+
+/* Byte offsets, inside the workspace, of the frame's intermediate arrays (for inspection).
+ * V views, n Gaussians, T tiles per view, cap = pair_capacity:
+ *   records    float[V*n][8]  (u_x, u_y, conic a, b, c, opacity, intensity, 0); u centred
+ *                             on the principal point; zero where the Gaussian touches no tile
+ *   depth      float[V*n]     t_z (0 where it touches no tile)
+ *   rect       uint16[V*n][4] tile rectangle (x0, y0, x1, y1), inclusive
+ *   count      uint32[V*n]    tiles touched
+ *   offset     uint32[V*n]    exclusive prefix sum of count, view-major
+ *   key_tile   uint32[cap]    sorted pairs: view * T + tile
+ *   key_depth  uint32[cap]    sorted pairs: bits of t_z
+ *   value      uint32[cap]    sorted pairs: Gaussian index
+ *   range      uint32[V*T][2] [start, end) of each tile in the sorted pairs ([0, 0) if empty)
+ *   tfinal     float[V][H][W] transmittance after the last contributor
+ *   last       uint32[V][H][W] 1-based position in the tile's list of the last contributor
+ *   grad2d     float[7][V*n]  per (view, Gaussian): dL/du_x, dL/du_y, dL/da, dL/db, dL/dc,
+ *                             dL/dopacity, dL/dintensity (written by xg_render_bwd) */
+typedef struct {
+  size_t status, cameras, records, depth, rect, count, offset;
+  size_t key_tile, key_depth, value, range, tfinal, last, grad2d;
+  int64_t tiles_per_view;
+  int32_t tiles_x, tiles_y;
+  int32_t sort_passes;
+  int32_t reserved;
+} xg_layout;
+
+typedef struct xg_frame xg_frame;
+
+/* Bytes of device workspace a frame with these sizes needs (0 if the arguments are
+ * invalid).  The workspace must be 256-byte aligned. */
+size_t xg_workspace_bytes(const xg_config* cfg, int64_t n, int32_t n_views, int32_t width, int32_t height);
+
+/* Create a frame for `n_views` views (host array, copied; every view must have the same
+ * width and height) and n Gaussians, inside the caller's device workspace.  Enqueues on
+ * `stream` the upload of the camera table and the clearing of the status word; the host
+ * array may be reused as soon as the call returns.  The frame object itself is host memory
+ * owned by the library; release it with xg_frame_destroy (the workspace stays the
+ * caller's).  Errors: XG_ERR_INVALID_ARG, XG_ERR_WORKSPACE, XG_ERR_CUDA. */
+xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const xg_view* views, int32_t n_views,
+                          void* workspace, size_t workspace_bytes, void* stream);
+void xg_frame_destroy(xg_frame* frame);
+
+/* Project every Gaussian into every view of the frame (Eq. 7-9 and the 2-D covariance of
+ * Sec. 3.2: t = M_ext mu, u = M_int t, Sigma' = J W Sigma W^T J^T, Sigma'' its top-left
+ * block, Sigma = R S S^T R^T of Sec. 3.1) and find the tiles its footprint touches.  Writes
+ * the frame's records, depth, rect and count arrays.  `g` must have the frame's n. */
+xg_status xg_project(xg_frame* frame, const xg_gaussians* g, void* stream);
+
+/* Tile binning and the depth-keyed radix sort (Sec. 3.2): prefix-sums the counts, emits one
+ * (view * T + tile, bits of t_z, Gaussian) pair per touched tile, sorts them by tile and
+ * then depth with a stable LSD radix sort, and extracts each tile's range.  Sets
+ * XG_ERR_CAPACITY in the device status if the pairs exceed pair_capacity. */
+xg_status xg_bin_sort(xg_frame* frame, void* stream);
+
+/* Front-to-back alpha compositing of intensity per detector pixel (Eq. 10).
+ *   image      device float[V][H][W], written
+ *   n_contrib  device uint32[V][H][W] contributor counts, written; may be NULL */
+xg_status xg_render_fwd(xg_frame* frame, float* image, uint32_t* n_contrib, void* stream);
+
+/* Gradients of L = sum_{v,p} grad_image[v][p] * image[v][p] with respect to every
+ * Gaussian parameter, for the image of the last xg_render_fwd of this frame (the frame's
+ * records, sorted pairs, tfinal and last must be unchanged since).  The compositing is
+ * walked back to front, the transmittance recovered by division rather than stored.
+ *   g          the same device Gaussians as xg_project
+ *   grad_image device float[V][H][W]
+ *   out        device gradient arrays, overwritten (sum over the frame's views) */
+xg_status xg_render_bwd(xg_frame* frame, const xg_gaussians* g, const float* grad_image, const xg_grads* out,
+                        void* stream);
+
+/* Wait for `stream`, then copy the frame's device status to *out.  Returns XG_OK if the
+ * copy worked (the device-side code is in out->code), else XG_ERR_CUDA. */
+xg_status xg_frame_read_status(const xg_frame* frame, xg_device_status* out, void* stream);
+
+/* Byte offsets of the frame's arrays inside its workspace. */
+xg_status xg_frame_layout(const xg_frame* frame, xg_layout* out);
+
+/* L1 term of the training objective (Eq. 11):
+ *   *loss = scale * sum_i |image[i] - target[i]|,  grad[i] = scale * sign(image[i] - target[i])
+ * image, target, grad: device float[count]; loss: one device float, overwritten.  Use
+ * scale = 1 / count for the mean.  Not tied to a frame. */
+xg_status xg_loss_l1(const float* image, const float* target, int64_t count, float scale, float* grad, float* loss,
+                     void* stream);
+
+/* Per-kernel timing of a frame's launches.  While enabled, every launch the frame's stage
+ * calls make is bracketed by CUDA events recorded on the launch stream (up to 2048
+ * launches between reads; further launches are not timed).  Keep it disabled while a
+ * stream is being captured into a CUDA graph. */
+typedef struct {
+  char name[32];     /* kernel name, e.g. "k_render_fwd" ("memset" for cudaMemsetAsync) */
+  int64_t launches;
+  double total_ms;   /* summed event-to-event time */
+} xg_kernel_time;
+
+xg_status xg_frame_set_timing(xg_frame* frame, int32_t enable);
+
+/* Wait for the recorded events, write one entry per kernel that ran (at most `capacity`)
+ * and the number written to *count, and start a new accumulation. */
+xg_status xg_frame_read_timing(xg_frame* frame, xg_kernel_time* out, int32_t capacity, int32_t* count);
+
+/* Text for a status code (static storage). */
+const char* xg_status_str(xg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XG_H */

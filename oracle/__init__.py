@@ -65,7 +65,7 @@ def lib():
                                     ctypes.c_int]
             L.xo_render.restype = ctypes.c_int
             L.xo_render_grad.argtypes = [i64, P, P, P, P, P, ctypes.POINTER(_View), ctypes.c_double, P, i64, P,
-                                         P, P, P, P, P, P, ctypes.c_int]
+                                         P, P, P, P, P, P, P, P, ctypes.c_int]
             L.xo_render_grad.restype = ctypes.c_int
             L.xo_project.argtypes = [i64, P, P, P, P, P, ctypes.POINTER(_View), ctypes.c_double, P]
             L.xo_project.restype = None
@@ -135,13 +135,17 @@ def grad64(g: dict, view, dL_dimage: np.ndarray, near_mm: float = NEAR_MM, pixel
     """FP64 gradient of sum_p dL_dimage[p] * I(p) for one view, added into ``out`` if given.
 
     Returns mean (3, n), scale (3, n), quat (4, n), opacity (n,), intensity (n,) and g2d
-    (7, n): this view's dL/du_x, dL/du_y, dL/da, dL/db, dL/dc, dL/do, dL/di.
+    (7, n): this view's dL/du_x, dL/du_y, dL/da, dL/db, dL/dc, dL/do, dL/di.  For judging
+    floating-point error it also returns mag2d (7, n), the sums of |per-pixel term| behind
+    g2d, and ``mag`` (same keys as the gradients, accumulated like them): how much term
+    magnitude reaches each parameter gradient through the linear backward map.
     """
     n, (mean, scale, quat, opac, inten) = _soa(g, np.float64)
     if out is None:
         out = {"mean": np.zeros((3, n)), "scale": np.zeros((3, n)), "quat": np.zeros((4, n)),
-               "opacity": np.zeros(n), "intensity": np.zeros(n)}
+               "opacity": np.zeros(n), "intensity": np.zeros(n), "mag_all": np.zeros((12, n))}
     g2d = np.zeros((7, n))
+    mag2d = np.zeros((7, n))
     dimg = np.ascontiguousarray(dL_dimage, dtype=np.float64).reshape(-1)
     assert dimg.size == view.width * view.height
     pix, npix = _pixels(pixels, view)
@@ -149,10 +153,13 @@ def grad64(g: dict, view, dL_dimage: np.ndarray, near_mm: float = NEAR_MM, pixel
     rc = lib().xo_render_grad(n, _ptr(mean), _ptr(scale), _ptr(quat), _ptr(opac), _ptr(inten), ctypes.byref(cv),
                               near_mm, _ptr(pix) if pix is not None else None, npix, _ptr(dimg), _ptr(out["mean"]),
                               _ptr(out["scale"]), _ptr(out["quat"]), _ptr(out["opacity"]), _ptr(out["intensity"]),
-                              _ptr(g2d), threads)
+                              _ptr(g2d), _ptr(mag2d), _ptr(out["mag_all"]), threads)
     if rc:
         raise MemoryError("oracle gradient ran out of memory")
     out["g2d"] = g2d
+    out["mag2d"] = mag2d
+    m = out["mag_all"]
+    out["mag"] = {"mean": m[0:3], "scale": m[3:6], "quat": m[6:10], "opacity": m[10], "intensity": m[11]}
     return out
 
 

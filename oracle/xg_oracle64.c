@@ -353,17 +353,97 @@ int xo_render(int64_t n, const double* mean, const double* scale, const double* 
   return err ? -1 : 0;
 }
 
+/* Chain rule of one Gaussian in one view (Eq. 7-9, Sigma = R S S^T R^T): from the 2-D
+ * gradients g7 = (dL/du_x, dL/du_y, dL/da, dL/db, dL/dc, dL/do, dL/di) to
+ * out12 = (dL/dmean[3], dL/dscale[3], dL/dquat[4], dL/dopacity, dL/dintensity). */
+static void chain_rule(const xo_pg* p, const double Wv[3][3], double fu, double fv, const double g7[7],
+                       double out12[12]) {
+  double gux = g7[0], guy = g7[1], ga = g7[2], gb = g7[3], gc = g7[4];
+  /* conic K = S''^-1: dL/dS'' = -K G K with G the symmetric gradient of K
+   * (the off-diagonal parameter b sits in two entries, so each gets gb / 2). */
+  double Km[2][2] = {{p->K[0], p->K[1]}, {p->K[1], p->K[2]}};
+  double Gm[2][2] = {{ga, 0.5 * gb}, {0.5 * gb, gc}};
+  double KG[2][2], gS2[2][2];
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c) KG[r][c] = Km[r][0] * Gm[0][c] + Km[r][1] * Gm[1][c];
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c) gS2[r][c] = -(KG[r][0] * Km[0][c] + KG[r][1] * Km[1][c]);
+  /* Sigma' = P Sigma P^T with P = J W; only its top-left block reaches S''. */
+  double gSp[3][3] = {{gS2[0][0], gS2[0][1], 0.0}, {gS2[1][0], gS2[1][1], 0.0}, {0.0, 0.0, 0.0}};
+  double P[3][3], Pt[3][3], tmp[3][3], gSigma[3][3], gP[3][3], gJ[3][3], Wt[3][3];
+  mat3_mul(p->J, p->W, P);
+  mat3_transpose(P, Pt);
+  mat3_mul(Pt, gSp, tmp);
+  mat3_mul(tmp, P, gSigma);
+  mat3_mul(gSp, P, tmp);
+  mat3_mul(tmp, p->Sigma, gP);
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) gP[r][c] *= 2.0;
+  mat3_transpose(p->W, Wt);
+  mat3_mul(gP, Wt, gJ);
+  double tx = p->t[0], ty = p->t[1], tz = p->t[2];
+  double gt[3];
+  /* J entries: J00 = fu/tz, J02 = -fu tx/tz^2, J11 = fv/tz, J12 = -fv ty/tz^2 */
+  gt[0] = gJ[0][2] * (-fu / (tz * tz));
+  gt[1] = gJ[1][2] * (-fv / (tz * tz));
+  gt[2] = gJ[0][0] * (-fu / (tz * tz)) + gJ[0][2] * (2.0 * fu * tx / (tz * tz * tz)) +
+          gJ[1][1] * (-fv / (tz * tz)) + gJ[1][2] * (2.0 * fv * ty / (tz * tz * tz));
+  /* u = (fu tx / tz + W/2, fv ty / tz + H/2) */
+  gt[0] += gux * fu / tz;
+  gt[1] += guy * fv / tz;
+  gt[2] += -gux * fu * tx / (tz * tz) - guy * fv * ty / (tz * tz);
+  /* t = W mu + (0, 0, L) */
+  for (int c = 0; c < 3; ++c) out12[c] = Wv[0][c] * gt[0] + Wv[1][c] * gt[1] + Wv[2][c] * gt[2];
+  /* Sigma = M M^T, M = R S */
+  double M[3][3], gM[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) M[r][c] = p->R[r][c] * p->s[c];
+  mat3_mul(gSigma, M, gM);
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) gM[r][c] *= 2.0;
+  double gR[3][3];
+  for (int c = 0; c < 3; ++c) {
+    double gs = 0.0;
+    for (int r = 0; r < 3; ++r) {
+      gs += gM[r][c] * p->R[r][c];
+      gR[r][c] = gM[r][c] * p->s[c];
+    }
+    out12[3 + c] = gs;
+  }
+  double D[4][3][3];
+  quat_rot_deriv(p->qn, D);
+  double gqn[4];
+  for (int k = 0; k < 4; ++k) {
+    double a = 0.0;
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) a += gR[r][c] * D[k][r][c];
+    gqn[k] = a;
+  }
+  /* qn = q / |q| */
+  double dot = 0.0;
+  for (int k = 0; k < 4; ++k) dot += gqn[k] * p->qn[k];
+  for (int k = 0; k < 4; ++k) out12[6 + k] = (gqn[k] - p->qn[k] * dot) / p->qnorm;
+  out12[10] = g7[5];
+  out12[11] = g7[6];
+}
+
 /*
  * Gradient of L = sum_p G(p) I(p) over the evaluated pixels of one view, ADDED into
  * g_mean[3n], g_scale[3n], g_quat[4n], g_opac[n], g_inten[n] (so calls over several views
  * accumulate).  If g2d is not NULL it receives (overwritten) the per-Gaussian 2-D
  * gradients of this view as 7 planes of n: dL/du_x, dL/du_y, dL/da, dL/db, dL/dc (conic
  * entries, b the off-diagonal), dL/dopacity, dL/dintensity.
+ *
+ * Magnitudes, for judging floating-point error: if mag2d is not NULL it receives the sum
+ * over pixels of |each pixel's term| for the same 7 quantities, and if mag (12 planes of
+ * n, the order of the parameter gradients) is not NULL it is ADDED sum_k |A_k| mag2d_k,
+ * A_k the parameter gradient that a unit 2-D gradient k produces (the backward pass is
+ * linear in the 2-D gradients, so this bounds how term errors reach the parameters).
  */
 int xo_render_grad(int64_t n, const double* mean, const double* scale, const double* quat, const double* opac,
                    const double* inten, const xo_view* view, double near_mm, const int32_t* pix, int64_t npix,
                    const double* dL_dimg, double* g_mean, double* g_scale, double* g_quat, double* g_opac,
-                   double* g_inten, double* g2d, int nthreads) {
+                   double* g_inten, double* g2d, double* mag2d, double* mag, int nthreads) {
   int W = view->width, H = view->height;
   xo_pg* pg = (xo_pg*)malloc(sizeof(xo_pg) * (size_t)(n > 0 ? n : 1));
   if (!pg) return -1;
@@ -375,7 +455,8 @@ int xo_render_grad(int64_t n, const double* mean, const double* scale, const dou
     free(pg);
     return -1;
   }
-  double* acc = (double*)calloc((size_t)nt * 7 * (size_t)n, sizeof(double));
+  const size_t planes = 14; /* 7 sums, 7 sums of magnitudes */
+  double* acc = (double*)calloc((size_t)nt * planes * (size_t)n, sizeof(double));
   if (!acc) {
     free_rows(&rows);
     free(pg);
@@ -390,7 +471,7 @@ int xo_render_grad(int64_t n, const double* mean, const double* scale, const dou
 #else
     int tid = 0;
 #endif
-    double* my = acc + (size_t)tid * 7 * (size_t)n;
+    double* my = acc + (size_t)tid * planes * (size_t)n;
     xo_cand* cand = (xo_cand*)malloc(sizeof(xo_cand) * (size_t)(n > 0 ? n : 1));
     int64_t* contrib = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     double* Tb = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -416,18 +497,22 @@ int xo_render_grad(int64_t n, const double* mean, const double* scale, const dou
         double dC_di = al * Tj;
         double dC_dal = Tj * (ij - A);
         A = al * ij + (1.0 - al) * A;
-        my[6 * n + g] += G * dC_di;
+        double t7[7] = {0, 0, 0, 0, 0, 0, G * dC_di};
         if (c->a0 < XO_ALPHA_MAX) {
           double dL_dal = G * dC_dal;
-          my[5 * n + g] += dL_dal * c->e;
+          t7[5] = dL_dal * c->e;
           double dL_dpow = dL_dal * al;
           const double* K = pg[g].K;
           /* power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = u - p */
-          my[0 * n + g] += dL_dpow * -(K[0] * c->dx + K[1] * c->dy);
-          my[1 * n + g] += dL_dpow * -(K[1] * c->dx + K[2] * c->dy);
-          my[2 * n + g] += dL_dpow * -0.5 * c->dx * c->dx;
-          my[3 * n + g] += dL_dpow * -c->dx * c->dy;
-          my[4 * n + g] += dL_dpow * -0.5 * c->dy * c->dy;
+          t7[0] = dL_dpow * -(K[0] * c->dx + K[1] * c->dy);
+          t7[1] = dL_dpow * -(K[1] * c->dx + K[2] * c->dy);
+          t7[2] = dL_dpow * -0.5 * c->dx * c->dx;
+          t7[3] = dL_dpow * -c->dx * c->dy;
+          t7[4] = dL_dpow * -0.5 * c->dy * c->dy;
+        }
+        for (int q = 0; q < 7; ++q) {
+          my[q * n + g] += t7[q];
+          my[(7 + q) * n + g] += fabs(t7[q]);
         }
       }
     }
@@ -442,83 +527,36 @@ int xo_render_grad(int64_t n, const double* mean, const double* scale, const dou
     return -1;
   }
   for (int t = 1; t < nt; ++t)
-    for (size_t k = 0; k < 7 * (size_t)n; ++k) acc[k] += acc[(size_t)t * 7 * (size_t)n + k];
+    for (size_t k = 0; k < planes * (size_t)n; ++k) acc[k] += acc[(size_t)t * planes * (size_t)n + k];
   if (g2d) memcpy(g2d, acc, sizeof(double) * 7 * (size_t)n);
+  if (mag2d) memcpy(mag2d, acc + 7 * (size_t)n, sizeof(double) * 7 * (size_t)n);
 
   double L, fu, fv, Wv[3][3];
   view_matrices(view, Wv, &L, &fu, &fv);
+  double* outs[5] = {g_mean, g_scale, g_quat, g_opac, g_inten};
+  const int rows_of[5] = {3, 3, 4, 1, 1};
 #pragma omp parallel for num_threads(nt) schedule(static)
   for (int64_t g = 0; g < n; ++g) {
     const xo_pg* p = &pg[g];
     if (!p->ok) continue;
-    double gux = acc[0 * n + g], guy = acc[1 * n + g];
-    double ga = acc[2 * n + g], gb = acc[3 * n + g], gc = acc[4 * n + g];
-    g_opac[g] += acc[5 * n + g];
-    g_inten[g] += acc[6 * n + g];
-    /* conic K = S''^-1: dL/dS'' = -K G K with G the symmetric gradient of K
-     * (the off-diagonal parameter b sits in two entries, so each gets gb / 2). */
-    double Km[2][2] = {{p->K[0], p->K[1]}, {p->K[1], p->K[2]}};
-    double Gm[2][2] = {{ga, 0.5 * gb}, {0.5 * gb, gc}};
-    double KG[2][2], gS2[2][2];
-    for (int r = 0; r < 2; ++r)
-      for (int c = 0; c < 2; ++c) KG[r][c] = Km[r][0] * Gm[0][c] + Km[r][1] * Gm[1][c];
-    for (int r = 0; r < 2; ++r)
-      for (int c = 0; c < 2; ++c) gS2[r][c] = -(KG[r][0] * Km[0][c] + KG[r][1] * Km[1][c]);
-    /* Sigma' = P Sigma P^T with P = J W; only its top-left block reaches S''. */
-    double gSp[3][3] = {{gS2[0][0], gS2[0][1], 0.0}, {gS2[1][0], gS2[1][1], 0.0}, {0.0, 0.0, 0.0}};
-    double P[3][3], Pt[3][3], tmp[3][3], gSigma[3][3], gP[3][3], gJ[3][3], Wt[3][3];
-    mat3_mul(p->J, p->W, P);
-    mat3_transpose(P, Pt);
-    mat3_mul(Pt, gSp, tmp);
-    mat3_mul(tmp, P, gSigma);
-    mat3_mul(gSp, P, tmp);
-    mat3_mul(tmp, p->Sigma, gP);
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) gP[r][c] *= 2.0;
-    mat3_transpose(p->W, Wt);
-    mat3_mul(gP, Wt, gJ);
-    double tx = p->t[0], ty = p->t[1], tz = p->t[2];
-    double gt[3];
-    /* J entries: J00 = fu/tz, J02 = -fu tx/tz^2, J11 = fv/tz, J12 = -fv ty/tz^2 */
-    gt[0] = gJ[0][2] * (-fu / (tz * tz));
-    gt[1] = gJ[1][2] * (-fv / (tz * tz));
-    gt[2] = gJ[0][0] * (-fu / (tz * tz)) + gJ[0][2] * (2.0 * fu * tx / (tz * tz * tz)) +
-            gJ[1][1] * (-fv / (tz * tz)) + gJ[1][2] * (2.0 * fv * ty / (tz * tz * tz));
-    /* u = (fu tx / tz + W/2, fv ty / tz + H/2) */
-    gt[0] += gux * fu / tz;
-    gt[1] += guy * fv / tz;
-    gt[2] += -gux * fu * tx / (tz * tz) - guy * fv * ty / (tz * tz);
-    /* t = W mu + (0, 0, L) */
-    for (int c = 0; c < 3; ++c) g_mean[c * n + g] += Wv[0][c] * gt[0] + Wv[1][c] * gt[1] + Wv[2][c] * gt[2];
-    /* Sigma = M M^T, M = R S */
-    double M[3][3], gM[3][3];
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) M[r][c] = p->R[r][c] * p->s[c];
-    mat3_mul(gSigma, M, gM);
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) gM[r][c] *= 2.0;
-    double gR[3][3];
-    for (int c = 0; c < 3; ++c) {
-      double gs = 0.0;
-      for (int r = 0; r < 3; ++r) {
-        gs += gM[r][c] * p->R[r][c];
-        gR[r][c] = gM[r][c] * p->s[c];
+    double g7[7], out12[12];
+    for (int q = 0; q < 7; ++q) g7[q] = acc[q * n + g];
+    chain_rule(p, Wv, fu, fv, g7, out12);
+    int k12 = 0;
+    for (int a = 0; a < 5; ++a)
+      for (int r = 0; r < rows_of[a]; ++r, ++k12) outs[a][r * n + g] += out12[k12];
+    if (mag) {
+      double m12[12] = {0};
+      for (int q = 0; q < 7; ++q) {
+        double e7[7] = {0, 0, 0, 0, 0, 0, 0}, a12[12];
+        double mq = acc[(7 + q) * n + g];
+        if (mq == 0.0) continue;
+        e7[q] = 1.0;
+        chain_rule(p, Wv, fu, fv, e7, a12);
+        for (int k = 0; k < 12; ++k) m12[k] += fabs(a12[k]) * mq;
       }
-      g_scale[c * n + g] += gs;
+      for (int k = 0; k < 12; ++k) mag[k * n + g] += m12[k];
     }
-    double D[4][3][3];
-    quat_rot_deriv(p->qn, D);
-    double gqn[4];
-    for (int k = 0; k < 4; ++k) {
-      double a = 0.0;
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) a += gR[r][c] * D[k][r][c];
-      gqn[k] = a;
-    }
-    /* qn = q / |q| */
-    double dot = 0.0;
-    for (int k = 0; k < 4; ++k) dot += gqn[k] * p->qn[k];
-    for (int k = 0; k < 4; ++k) g_quat[k * n + g] += (gqn[k] - p->qn[k] * dot) / p->qnorm;
   }
   free(acc);
   free_rows(&rows);

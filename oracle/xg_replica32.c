@@ -12,7 +12,7 @@
  *
  * Transcendentals used in a decision are computed here from basic operations:
  *   exp: Cody-Waite reduction by ln 2 (split into its float rounding and the float of the
- *        remainder), then the degree-5 Taylor polynomial of e^r, |r| <= ln2/2, scaled by 2^k;
+ *        remainder), then the degree-6 Taylor polynomial of e^r, |r| <= ln2/2, scaled by 2^k;
  *   log: x = m 2^e with m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh((m-1)/(m+1)) by its odd
  *        series to s^9, plus e ln 2.
  * Readings of the paper used here: focal in pixels L_SD / pitch; pixel centres at
@@ -59,7 +59,8 @@ float xr_exp(float x) {
   float k = rintf(x * R_L2E);
   float r = fmaf(k, -R_LN2_HI, x);
   r = fmaf(k, -R_LN2_LO, r);
-  float p = fmaf(r, (float)(1.0 / 120.0), (float)(1.0 / 24.0));
+  float p = fmaf(r, (float)(1.0 / 720.0), (float)(1.0 / 120.0));
+  p = fmaf(p, r, (float)(1.0 / 24.0));
   p = fmaf(p, r, (float)(1.0 / 6.0));
   p = fmaf(p, r, 0.5f);
   p = fmaf(p, r, 1.0f);

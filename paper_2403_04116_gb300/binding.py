@@ -1,0 +1,190 @@
+"""ctypes binding of ``include/xg.h``: same names, argument marshalling only.
+
+Every computation happens in ``libxg.so``.  If the library has not been built, loading
+fails loudly: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+XG_OK = 0
+XG_ERR_INVALID_ARG = 1
+XG_ERR_CAPACITY = 2
+XG_ERR_CUDA = 3
+XG_ERR_WORKSPACE = 4
+XG_ERR_CHECK = 5
+
+# Every symbol include/xg.h declares.
+EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_project", "xg_bin_sort",
+           "xg_render_fwd", "xg_render_bwd", "xg_frame_read_status", "xg_frame_layout", "xg_loss_l1",
+           "xg_frame_set_timing", "xg_frame_read_timing", "xg_status_str")
+
+
+class XgView(ctypes.Structure):
+    _fields_ = [("sod_mm", ctypes.c_double), ("sdd_mm", ctypes.c_double), ("pitch_u_mm", ctypes.c_double),
+                ("pitch_v_mm", ctypes.c_double), ("angle_rad", ctypes.c_double), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+class XgGaussians(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("quat", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("intensity", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class XgGrads(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("quat", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("intensity", ctypes.c_void_p)]
+
+
+class XgConfig(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("near_mm", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("pair_capacity", ctypes.c_int64)]
+
+
+class XgDeviceStatus(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_int32), ("reserved", ctypes.c_int32), ("pairs", ctypes.c_int64),
+                ("nonfinite", ctypes.c_int64), ("fwd_evaluated", ctypes.c_int64), ("fwd_contrib", ctypes.c_int64),
+                ("bwd_evaluated", ctypes.c_int64), ("bwd_contrib", ctypes.c_int64)]
+
+
+class XgKernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class XgLayout(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_size_t) for name in
+                ("status", "cameras", "records", "depth", "rect", "count", "offset", "key_tile", "key_depth",
+                 "value", "range", "tfinal", "last", "grad2d")] + [
+        ("tiles_per_view", ctypes.c_int64), ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
+        ("sort_passes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class XgError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {xg_status_str(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """Load libxg.so (raises if it is absent and ``build_if_missing`` is false)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: build it with paper_2403_04116_gb300.build.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    L.xg_workspace_bytes.argtypes = [ctypes.POINTER(XgConfig), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32]
+    L.xg_workspace_bytes.restype = ctypes.c_size_t
+    L.xg_frame_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(XgConfig), ctypes.c_int64,
+                                  ctypes.POINTER(XgView), ctypes.c_int32, P, ctypes.c_size_t, P]
+    L.xg_frame_create.restype = ctypes.c_int
+    L.xg_frame_destroy.argtypes = [P]
+    L.xg_frame_destroy.restype = None
+    L.xg_project.argtypes = [P, ctypes.POINTER(XgGaussians), P]
+    L.xg_project.restype = ctypes.c_int
+    L.xg_bin_sort.argtypes = [P, P]
+    L.xg_bin_sort.restype = ctypes.c_int
+    L.xg_render_fwd.argtypes = [P, P, P, P]
+    L.xg_render_fwd.restype = ctypes.c_int
+    L.xg_render_bwd.argtypes = [P, ctypes.POINTER(XgGaussians), P, ctypes.POINTER(XgGrads), P]
+    L.xg_render_bwd.restype = ctypes.c_int
+    L.xg_frame_read_status.argtypes = [P, ctypes.POINTER(XgDeviceStatus), P]
+    L.xg_frame_read_status.restype = ctypes.c_int
+    L.xg_frame_layout.argtypes = [P, ctypes.POINTER(XgLayout)]
+    L.xg_frame_layout.restype = ctypes.c_int
+    L.xg_loss_l1.argtypes = [P, P, ctypes.c_int64, ctypes.c_float, P, P, P]
+    L.xg_loss_l1.restype = ctypes.c_int
+    L.xg_frame_set_timing.argtypes = [P, ctypes.c_int32]
+    L.xg_frame_set_timing.restype = ctypes.c_int
+    L.xg_frame_read_timing.argtypes = [P, ctypes.POINTER(XgKernelTime), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32)]
+    L.xg_frame_read_timing.restype = ctypes.c_int
+    L.xg_status_str.argtypes = [ctypes.c_int]
+    L.xg_status_str.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(code: int, what: str) -> None:
+    if code != XG_OK:
+        raise XgError(code, what)
+
+
+def xg_status_str(code: int) -> str:
+    return lib().xg_status_str(code).decode()
+
+
+def xg_workspace_bytes(cfg: XgConfig, n: int, n_views: int, width: int, height: int) -> int:
+    return int(lib().xg_workspace_bytes(ctypes.byref(cfg), n, n_views, width, height))
+
+
+def xg_frame_create(cfg: XgConfig, n: int, views, workspace: int, workspace_bytes: int, stream: int) -> int:
+    arr = (XgView * len(views))(*[XgView(v.sod_mm, v.sdd_mm, v.pitch_u_mm, v.pitch_v_mm, v.angle_rad, v.width,
+                                         v.height) for v in views])
+    out = ctypes.c_void_p()
+    _check(lib().xg_frame_create(ctypes.byref(out), ctypes.byref(cfg), n, arr, len(views), workspace,
+                                 workspace_bytes, stream), "xg_frame_create")
+    return out.value
+
+
+def xg_frame_destroy(frame: int) -> None:
+    lib().xg_frame_destroy(frame)
+
+
+def xg_project(frame: int, g: XgGaussians, stream: int) -> None:
+    _check(lib().xg_project(frame, ctypes.byref(g), stream), "xg_project")
+
+
+def xg_bin_sort(frame: int, stream: int) -> None:
+    _check(lib().xg_bin_sort(frame, stream), "xg_bin_sort")
+
+
+def xg_render_fwd(frame: int, image: int, n_contrib: int | None, stream: int) -> None:
+    _check(lib().xg_render_fwd(frame, image, n_contrib, stream), "xg_render_fwd")
+
+
+def xg_render_bwd(frame: int, g: XgGaussians, grad_image: int, out: XgGrads, stream: int) -> None:
+    _check(lib().xg_render_bwd(frame, ctypes.byref(g), grad_image, ctypes.byref(out), stream), "xg_render_bwd")
+
+
+def xg_frame_read_status(frame: int, stream: int) -> XgDeviceStatus:
+    s = XgDeviceStatus()
+    _check(lib().xg_frame_read_status(frame, ctypes.byref(s), stream), "xg_frame_read_status")
+    return s
+
+
+def xg_frame_layout(frame: int) -> XgLayout:
+    L = XgLayout()
+    _check(lib().xg_frame_layout(frame, ctypes.byref(L)), "xg_frame_layout")
+    return L
+
+
+def xg_loss_l1(image: int, target: int, count: int, scale: float, grad: int, loss: int, stream: int) -> None:
+    _check(lib().xg_loss_l1(image, target, count, scale, grad, loss, stream), "xg_loss_l1")
+
+
+def xg_frame_set_timing(frame: int, enable: bool) -> None:
+    _check(lib().xg_frame_set_timing(frame, 1 if enable else 0), "xg_frame_set_timing")
+
+
+def xg_frame_read_timing(frame: int) -> dict:
+    """{kernel name: (launches, total ms)} since the previous read (waits for the events)."""
+    out = (XgKernelTime * 32)()
+    count = ctypes.c_int32()
+    _check(lib().xg_frame_read_timing(frame, out, 32, ctypes.byref(count)), "xg_frame_read_timing")
+    return {out[i].name.decode(): (int(out[i].launches), float(out[i].total_ms)) for i in range(count.value)}

@@ -1,0 +1,356 @@
+// Host side of the C ABI declared in include/xg.h: argument checks, workspace layout, the
+// FP32 camera table built from the scanner parameters (Sec. 3.3, Eq. 12), and the
+// stream-ordered launches of each stage.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "xg_internal.cuh"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool valid_tile(int t) { return t == 8 || t == 16 || t == 32; }
+
+bool valid_config(const xg_config* cfg) {
+  return cfg && valid_tile(cfg->tile_w) && valid_tile(cfg->tile_h) && cfg->tile_w * cfg->tile_h <= 512 &&
+         isfinite(cfg->near_mm) && cfg->near_mm > 0.f && cfg->pair_capacity >= 1 &&
+         cfg->pair_capacity < ((int64_t)1 << 31);
+}
+
+bool valid_sizes(int64_t n, int32_t n_views, int32_t W, int32_t H) {
+  return n >= 1 && n < ((int64_t)1 << 31) && n_views >= 1 && n_views <= xg::kMaxViews && W >= 1 && W <= 4096 &&
+         H >= 1 && H <= 4096 && (int64_t)n_views * n < ((int64_t)1 << 40);
+}
+
+struct Sizes {
+  int32_t tiles_x, tiles_y;
+  int64_t tiles_per_view;
+  int32_t tile_bits, passes;
+};
+
+bool sizes_of(const xg_config* cfg, int64_t n_views, int32_t W, int32_t H, Sizes* s) {
+  s->tiles_x = (W + cfg->tile_w - 1) / cfg->tile_w;
+  s->tiles_y = (H + cfg->tile_h - 1) / cfg->tile_h;
+  s->tiles_per_view = (int64_t)s->tiles_x * s->tiles_y;
+  const int64_t keys = n_views * s->tiles_per_view;
+  if (keys >= ((int64_t)1 << 31)) return false;
+  int bits = 0;
+  while (((int64_t)1 << bits) < keys) ++bits;
+  s->tile_bits = bits;
+  s->passes = 4 + (bits + 7) / 8;
+  return true;
+}
+
+// Byte offsets of every array in the workspace, public and private, in allocation order.
+struct Offsets {
+  size_t status, cameras, records, depth, rect, count, offset, scan_part;
+  size_t key_tile[2], key_depth[2], value[2], hist, range, tfinal, last, grad2d;
+  size_t total;
+};
+
+bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t W, int32_t H, Sizes* s, Offsets* o) {
+  if (!sizes_of(cfg, V, W, H, s)) return false;
+  const size_t VN = (size_t)V * (size_t)n;
+  const size_t cap = (size_t)cfg->pair_capacity;
+  const size_t pix = (size_t)V * (size_t)W * (size_t)H;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  o->status = take(sizeof(xg::DevStatus));
+  o->cameras = take(sizeof(xg::Camera) * (size_t)V);
+  o->records = take(32 * VN);
+  o->depth = take(4 * VN);
+  o->rect = take(8 * VN);
+  o->count = take(4 * VN);
+  o->offset = take(4 * VN);
+  o->scan_part = take(8 * (xg::kSortBlocks + 1));
+  for (int b = 0; b < 2; ++b) o->key_tile[b] = take(4 * cap);
+  for (int b = 0; b < 2; ++b) o->key_depth[b] = take(4 * cap);
+  for (int b = 0; b < 2; ++b) o->value[b] = take(4 * cap);
+  o->hist = take(4 * 256 * (size_t)xg::kSortBlocks);
+  o->range = take(8 * (size_t)V * (size_t)s->tiles_per_view);
+  o->tfinal = take(4 * pix);
+  o->last = take(4 * pix);
+  o->grad2d = take(4 * 7 * VN);
+  o->total = off;
+  return true;
+}
+
+}  // namespace
+
+namespace xg {
+Timed::Timed(xg_frame* frame, int kid, cudaStream_t stream) : f(frame), st(stream), slot(-1) {
+  if (!f->timing) return;
+  if (f->nrec >= kMaxTimingRecs) {
+    ++f->dropped;
+    return;
+  }
+  slot = f->nrec++;
+  f->recs[slot].kid = kid;
+  cudaEventRecord(f->recs[slot].a, st);
+}
+Timed::~Timed() {
+  if (slot >= 0) cudaEventRecord(f->recs[slot].b, st);
+}
+}  // namespace xg
+
+extern "C" {
+
+size_t xg_workspace_bytes(const xg_config* cfg, int64_t n, int32_t n_views, int32_t width, int32_t height) {
+  if (!valid_config(cfg) || !valid_sizes(n, n_views, width, height)) return 0;
+  Sizes s;
+  Offsets o;
+  return make_offsets(cfg, n, n_views, width, height, &s, &o) ? o.total : 0;
+}
+
+xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const xg_view* views, int32_t n_views,
+                          void* workspace, size_t workspace_bytes, void* stream) {
+  if (!out) return XG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!valid_config(cfg) || !views || n_views < 1) return XG_ERR_INVALID_ARG;
+  const int32_t W = views[0].width, H = views[0].height;
+  if (!valid_sizes(n, n_views, W, H)) return XG_ERR_INVALID_ARG;
+  for (int32_t v = 0; v < n_views; ++v) {
+    const xg_view& w = views[v];
+    if (w.width != W || w.height != H) return XG_ERR_INVALID_ARG;
+    if (!(isfinite(w.sod_mm) && w.sod_mm > 0 && isfinite(w.sdd_mm) && w.sdd_mm > 0 && isfinite(w.pitch_u_mm) &&
+          w.pitch_u_mm > 0 && isfinite(w.pitch_v_mm) && w.pitch_v_mm > 0 && isfinite(w.angle_rad)))
+      return XG_ERR_INVALID_ARG;
+  }
+  Sizes s;
+  Offsets o;
+  if (!make_offsets(cfg, n, n_views, W, H, &s, &o)) return XG_ERR_INVALID_ARG;
+  if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < o.total) return XG_ERR_WORKSPACE;
+
+  xg_frame* f = (xg_frame*)calloc(1, sizeof(xg_frame));
+  if (!f) return XG_ERR_INVALID_ARG;
+  f->cfg = *cfg;
+  f->n = n;
+  f->n_views = n_views;
+  f->width = W;
+  f->height = H;
+  f->tiles_x = s.tiles_x;
+  f->tiles_y = s.tiles_y;
+  f->tiles_per_view = s.tiles_per_view;
+  f->tile_bits = s.tile_bits;
+  f->sort_passes = s.passes;
+  f->sorted_buf = s.passes & 1;  // each pass moves the pairs to the other buffer
+  f->workspace = workspace;
+  f->workspace_bytes = workspace_bytes;
+
+  char* base = (char*)workspace;
+  xg::FramePtrs& p = f->p;
+  p.status = (xg::DevStatus*)(base + o.status);
+  p.cam = (xg::Camera*)(base + o.cameras);
+  p.rec = (float4*)(base + o.records);
+  p.depth = (float*)(base + o.depth);
+  p.rect = (ushort4*)(base + o.rect);
+  p.count = (uint32_t*)(base + o.count);
+  p.offset = (uint32_t*)(base + o.offset);
+  p.scan_part = (unsigned long long*)(base + o.scan_part);
+  for (int k = 0; k < 2; ++k) {
+    p.key_tile[k] = (uint32_t*)(base + o.key_tile[k]);
+    p.key_depth[k] = (uint32_t*)(base + o.key_depth[k]);
+    p.value[k] = (uint32_t*)(base + o.value[k]);
+  }
+  p.hist = (uint32_t*)(base + o.hist);
+  p.range = (uint2*)(base + o.range);
+  p.tfinal = (float*)(base + o.tfinal);
+  p.last = (uint32_t*)(base + o.last);
+  p.grad2d = (float*)(base + o.grad2d);
+
+  xg_layout& L = f->layout;
+  L.status = o.status;
+  L.cameras = o.cameras;
+  L.records = o.records;
+  L.depth = o.depth;
+  L.rect = o.rect;
+  L.count = o.count;
+  L.offset = o.offset;
+  L.key_tile = o.key_tile[f->sorted_buf];
+  L.key_depth = o.key_depth[f->sorted_buf];
+  L.value = o.value[f->sorted_buf];
+  L.range = o.range;
+  L.tfinal = o.tfinal;
+  L.last = o.last;
+  L.grad2d = o.grad2d;
+  L.tiles_per_view = s.tiles_per_view;
+  L.tiles_x = s.tiles_x;
+  L.tiles_y = s.tiles_y;
+  L.sort_passes = s.passes;
+
+  // camera table: trigonometry in FP64, rounded once to FP32
+  xg::Camera* cams = (xg::Camera*)calloc((size_t)n_views, sizeof(xg::Camera));
+  if (!cams) {
+    free(f);
+    return XG_ERR_INVALID_ARG;
+  }
+  for (int32_t v = 0; v < n_views; ++v) {
+    const xg_view& w = views[v];
+    xg::Camera& c = cams[v];
+    c.c = (float)cos(w.angle_rad);
+    c.s = (float)sin(w.angle_rad);
+    c.L = (float)w.sod_mm;
+    c.fu = (float)(w.sdd_mm / w.pitch_u_mm);
+    c.fv = (float)(w.sdd_mm / w.pitch_v_mm);
+    c.hw = (float)W * 0.5f - 0.5f;
+    c.hh = (float)H * 0.5f - 0.5f;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(p.cam, cams, sizeof(xg::Camera) * (size_t)n_views, cudaMemcpyHostToDevice, st);
+  free(cams);  // pageable source: the copy has been staged when cudaMemcpyAsync returns
+  if (e == cudaSuccess) e = cudaMemsetAsync(p.status, 0, sizeof(xg::DevStatus), st);
+  if (e != cudaSuccess) {
+    free(f);
+    return XG_ERR_CUDA;
+  }
+  *out = f;
+  return XG_OK;
+}
+
+void xg_frame_destroy(xg_frame* frame) {
+  if (!frame) return;
+  if (frame->recs) {
+    for (int i = 0; i < xg::kMaxTimingRecs; ++i) {
+      cudaEventDestroy(frame->recs[i].a);
+      cudaEventDestroy(frame->recs[i].b);
+    }
+    free(frame->recs);
+  }
+  free(frame);
+}
+
+xg_status xg_frame_set_timing(xg_frame* frame, int32_t enable) {
+  if (!frame) return XG_ERR_INVALID_ARG;
+  if (enable && !frame->recs) {
+    xg::TimingRec* recs = (xg::TimingRec*)calloc(xg::kMaxTimingRecs, sizeof(xg::TimingRec));
+    if (!recs) return XG_ERR_INVALID_ARG;
+    for (int i = 0; i < xg::kMaxTimingRecs; ++i) {
+      if (cudaEventCreate(&recs[i].a) != cudaSuccess || cudaEventCreate(&recs[i].b) != cudaSuccess) {
+        for (int j = 0; j <= i; ++j) {
+          if (recs[j].a) cudaEventDestroy(recs[j].a);
+          if (recs[j].b) cudaEventDestroy(recs[j].b);
+        }
+        free(recs);
+        return XG_ERR_CUDA;
+      }
+    }
+    frame->recs = recs;
+  }
+  frame->timing = enable ? 1 : 0;
+  return XG_OK;
+}
+
+xg_status xg_frame_read_timing(xg_frame* frame, xg_kernel_time* out, int32_t capacity, int32_t* count) {
+  static const char* const names[xg::kNumKernels] = {
+      "k_project", "k_scan_reduce", "k_scan_top", "k_scan_down", "k_emit", "k_radix_hist", "k_radix_scan",
+      "k_radix_scatter", "k_ranges", "k_render_fwd", "k_render_bwd", "k_project_bwd", "memset"};
+  if (!frame || !count || (capacity > 0 && !out)) return XG_ERR_INVALID_ARG;
+  if (frame->nrec > 0) {
+    if (cudaEventSynchronize(frame->recs[frame->nrec - 1].b) != cudaSuccess) return XG_ERR_CUDA;
+    for (int i = 0; i < frame->nrec; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, frame->recs[i].a, frame->recs[i].b) != cudaSuccess) return XG_ERR_CUDA;
+      frame->acc_ms[frame->recs[i].kid] += ms;
+      frame->acc_n[frame->recs[i].kid] += 1;
+    }
+  }
+  int32_t k = 0;
+  for (int kid = 0; kid < xg::kNumKernels; ++kid) {
+    if (!frame->acc_n[kid]) continue;
+    if (k < capacity) {
+      memset(out[k].name, 0, sizeof out[k].name);
+      strncpy(out[k].name, names[kid], sizeof out[k].name - 1);
+      out[k].launches = frame->acc_n[kid];
+      out[k].total_ms = frame->acc_ms[kid];
+    }
+    ++k;
+  }
+  *count = k < capacity ? k : capacity;
+  frame->nrec = 0;
+  frame->dropped = 0;
+  memset(frame->acc_ms, 0, sizeof frame->acc_ms);
+  memset(frame->acc_n, 0, sizeof frame->acc_n);
+  return XG_OK;
+}
+
+xg_status xg_loss_l1(const float* image, const float* target, int64_t count, float scale, float* grad, float* loss,
+                     void* stream) {
+  if (!image || !target || !grad || !loss || count < 1) return XG_ERR_INVALID_ARG;
+  return xg::launch_loss_l1(image, target, count, scale, grad, loss, (cudaStream_t)stream) == cudaSuccess
+             ? XG_OK
+             : XG_ERR_CUDA;
+}
+
+static bool valid_gaussians(const xg_frame* f, const xg_gaussians* g) {
+  return g && g->n == f->n && g->mean && g->scale && g->quat && g->opacity && g->intensity;
+}
+
+xg_status xg_project(xg_frame* frame, const xg_gaussians* g, void* stream) {
+  if (!frame || !valid_gaussians(frame, g)) return XG_ERR_INVALID_ARG;
+  return xg::launch_project(frame, g, (cudaStream_t)stream) == cudaSuccess ? XG_OK : XG_ERR_CUDA;
+}
+
+xg_status xg_bin_sort(xg_frame* frame, void* stream) {
+  if (!frame) return XG_ERR_INVALID_ARG;
+  return xg::launch_bin_sort(frame, (cudaStream_t)stream) == cudaSuccess ? XG_OK : XG_ERR_CUDA;
+}
+
+xg_status xg_render_fwd(xg_frame* frame, float* image, uint32_t* n_contrib, void* stream) {
+  if (!frame || !image) return XG_ERR_INVALID_ARG;
+  return xg::launch_render_fwd(frame, image, n_contrib, (cudaStream_t)stream) == cudaSuccess ? XG_OK : XG_ERR_CUDA;
+}
+
+xg_status xg_render_bwd(xg_frame* frame, const xg_gaussians* g, const float* grad_image, const xg_grads* out,
+                        void* stream) {
+  if (!frame || !valid_gaussians(frame, g) || !grad_image || !out || !out->mean || !out->scale || !out->quat ||
+      !out->opacity || !out->intensity)
+    return XG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (xg::launch_render_bwd(frame, grad_image, st) != cudaSuccess) return XG_ERR_CUDA;
+  return xg::launch_project_bwd(frame, g, out, st) == cudaSuccess ? XG_OK : XG_ERR_CUDA;
+}
+
+xg_status xg_frame_read_status(const xg_frame* frame, xg_device_status* out, void* stream) {
+  if (!frame || !out) return XG_ERR_INVALID_ARG;
+  xg::DevStatus s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&s, frame->p.status, sizeof s, cudaMemcpyDeviceToHost, st) != cudaSuccess) return XG_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return XG_ERR_CUDA;
+  out->code = s.code;
+  out->reserved = 0;
+  out->pairs = s.pairs;
+  out->nonfinite = (int64_t)s.nonfinite;
+  out->fwd_evaluated = (int64_t)s.fwd_evaluated;
+  out->fwd_contrib = (int64_t)s.fwd_contrib;
+  out->bwd_evaluated = (int64_t)s.bwd_evaluated;
+  out->bwd_contrib = (int64_t)s.bwd_contrib;
+  return XG_OK;
+}
+
+xg_status xg_frame_layout(const xg_frame* frame, xg_layout* out) {
+  if (!frame || !out) return XG_ERR_INVALID_ARG;
+  *out = frame->layout;
+  return XG_OK;
+}
+
+const char* xg_status_str(xg_status s) {
+  switch (s) {
+    case XG_OK: return "ok";
+    case XG_ERR_INVALID_ARG: return "invalid argument";
+    case XG_ERR_CAPACITY: return "pair capacity exceeded";
+    case XG_ERR_CUDA: return "CUDA error";
+    case XG_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case XG_ERR_CHECK: return "device-side bounds check failed";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

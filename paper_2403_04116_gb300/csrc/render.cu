@@ -1,0 +1,245 @@
+// Front-to-back alpha compositing of intensity per detector pixel (Eq. 10) and its
+// backward pass.
+//
+// One CTA per (tile, view), one thread per pixel.  The tile's depth-sorted list is staged
+// through shared memory in batches (the record of each Gaussian read once per CTA and
+// broadcast to all its pixels); a CTA stops fetching as soon as every pixel's transmittance
+// has hit the floor (__syncthreads_count).  The backward pass walks each pixel's list back
+// to front from its last contributor, recovering the transmittance by division instead of
+// storing it, reduces the per-Gaussian gradients across the warp with shuffles, then across
+// the CTA in shared memory, and issues one global atomic per (Gaussian, tile, quantity).
+#include "xg_internal.cuh"
+
+namespace xg {
+
+constexpr int kBatch = 256;
+
+__device__ __forceinline__ void stage_batch(const uint32_t* __restrict__ value, const float4* __restrict__ rec,
+                                            int64_t vn_base, uint32_t first, int cnt, float4* s_a, float4* s_b,
+                                            uint32_t* s_g) {
+  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+    const uint32_t g = value[first + j];
+    const float4 a = rec[2 * (vn_base + g)];
+    const float4 b = rec[2 * (vn_base + g) + 1];
+    // (u_x, u_y, -a/2, -b) and (-c/2, opacity, intensity): exact rescalings of the conic
+    s_a[j] = make_float4(a.x, a.y, -0.5f * a.z, -a.w);
+    s_b[j] = make_float4(-0.5f * b.x, b.y, b.z, 0.f);
+    if (s_g) s_g[j] = g;
+  }
+}
+
+// Work counters: one atomic per warp.
+__device__ __forceinline__ void add_counts(uint32_t ev, uint32_t nc, unsigned long long* ev_out,
+                                           unsigned long long* nc_out) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    nc += __shfl_xor_sync(0xffffffffu, nc, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (ev) atomicAdd(ev_out, (unsigned long long)ev);
+    if (nc) atomicAdd(nc_out, (unsigned long long)nc);
+  }
+}
+
+// The exponent -1/2 d^T K d and sigma = min(0.99, o e^p) in the fixed FP32 sequence.
+__device__ __forceinline__ float power_of(const float4 a, const float nc, float px, float py, float& dx, float& dy) {
+  dx = fsub(a.x, px);
+  dy = fsub(a.y, py);
+  float p = fmul(a.w, fmul(dx, dy));
+  p = ffma(nc, fmul(dy, dy), p);
+  p = ffma(a.z, fmul(dx, dx), p);
+  return p;
+}
+
+__global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ range, const uint32_t* __restrict__ value,
+                                                    const float4* __restrict__ rec, int64_t n, int W, int H,
+                                                    int tiles_x, int64_t tiles_per_view, int tw,
+                                                    const Camera* __restrict__ cams, DevStatus* __restrict__ st,
+                                                    float* __restrict__ image, uint32_t* __restrict__ ncontrib,
+                                                    float* __restrict__ tfinal, uint32_t* __restrict__ last) {
+  __shared__ float4 s_a[kBatch], s_b[kBatch];
+  const int tile = blockIdx.x, v = blockIdx.y;
+  const int th_ = blockDim.x / tw;
+  const int x = (tile % tiles_x) * tw + (int)threadIdx.x % tw;
+  const int y = (tile / tiles_x) * th_ + (int)threadIdx.x / tw;
+  const bool inside = x < W && y < H;
+  const Camera cam = cams[v];
+  const float px = fsub((float)x, cam.hw), py = fsub((float)y, cam.hh);
+  const uint2 r = st->code == XG_OK ? range[(int64_t)v * tiles_per_view + tile] : make_uint2(0u, 0u);
+  const int nlist = (int)(r.y - r.x);
+  const int64_t vn_base = (int64_t)v * n;
+
+  float T = 1.0f, C = 0.0f;
+  uint32_t nc = 0, lastp = 0, nev = 0;
+  bool done = !inside;
+  for (int base = 0; base < nlist; base += kBatch) {
+    if (__syncthreads_count(done) == (int)blockDim.x) break;
+    const int cnt = min(kBatch, nlist - base);
+    stage_batch(value, rec, vn_base, r.x + base, cnt, s_a, s_b, nullptr);
+    __syncthreads();
+    if (!done) {
+      for (int j = 0; j < cnt; ++j) {
+        const float4 a = s_a[j];
+        const float4 b = s_b[j];
+        float dx, dy;
+        const float p = power_of(a, b.x, px, py, dx, dy);
+        const float al = fminf(kAlphaMax, fmul(b.y, xg_exp(p)));
+        ++nev;
+        if (al < kAlphaMin) continue;
+        const float Tn = fmul(T, fsub(1.0f, al));
+        if (Tn < kTMin) {
+          done = true;
+          break;
+        }
+        C = ffma(b.z, fmul(al, T), C);
+        T = Tn;
+        ++nc;
+        lastp = (uint32_t)(base + j + 1);
+      }
+    }
+  }
+  if (inside) {
+    const int64_t pix = ((int64_t)v * H + y) * W + x;
+    image[pix] = C;
+    tfinal[pix] = T;
+    last[pix] = lastp;
+    if (ncontrib) ncontrib[pix] = nc;
+  }
+  add_counts(nev, nc, &st->fwd_evaluated, &st->fwd_contrib);
+}
+
+cudaError_t launch_render_fwd(xg_frame* f, float* image, uint32_t* n_contrib, cudaStream_t st) {
+  const FramePtrs& p = f->p;
+  dim3 grid((unsigned)f->tiles_per_view, (unsigned)f->n_views);
+  Timed t(f, kRenderFwd, st);
+  k_render_fwd<<<grid, f->cfg.tile_w * f->cfg.tile_h, 0, st>>>(
+      p.range, p.value[f->sorted_buf], p.rec, f->n, f->width, f->height, f->tiles_x, f->tiles_per_view,
+      f->cfg.tile_w, p.cam, p.status, image, n_contrib, p.tfinal, p.last);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// backward
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ range, const uint32_t* __restrict__ value,
+                                                    const float4* __restrict__ rec, int64_t n, int n_views, int W,
+                                                    int H, int tiles_x, int64_t tiles_per_view, int tw,
+                                                    const Camera* __restrict__ cams, DevStatus* __restrict__ st,
+                                                    const float* __restrict__ grad_image,
+                                                    const float* __restrict__ tfinal, const uint32_t* __restrict__ last,
+                                                    float* __restrict__ g2d) {
+  __shared__ float4 s_a[kBatch], s_b[kBatch];
+  __shared__ uint32_t s_g[kBatch];
+  __shared__ float s_acc[kBatch * 8];
+  __shared__ uint32_t s_maxlast;
+  if (st->code != XG_OK) return;
+  const int tile = blockIdx.x, v = blockIdx.y;
+  const int th_ = blockDim.x / tw;
+  const int x = (tile % tiles_x) * tw + (int)threadIdx.x % tw;
+  const int y = (tile / tiles_x) * th_ + (int)threadIdx.x / tw;
+  const bool inside = x < W && y < H;
+  const Camera cam = cams[v];
+  const float px = fsub((float)x, cam.hw), py = fsub((float)y, cam.hh);
+  const uint2 r = range[(int64_t)v * tiles_per_view + tile];
+  const int64_t vn_base = (int64_t)v * n;
+  const int64_t VN = (int64_t)n_views * n;
+  const int lane = threadIdx.x & 31;
+
+  float G = 0.f, Tc = 1.f;
+  uint32_t L = 0;
+  if (inside) {
+    const int64_t pix = ((int64_t)v * H + y) * W + x;
+    G = grad_image[pix];
+    Tc = tfinal[pix];
+    L = G != 0.f ? last[pix] : 0u;
+  }
+  if (threadIdx.x == 0) s_maxlast = 0;
+  __syncthreads();
+  if (L) atomicMax(&s_maxlast, L);
+  __syncthreads();
+  const int maxl = (int)s_maxlast;
+  float A = 0.f;  // intensity blended behind the current position, per unit transmittance
+  uint32_t nev = 0, ncon = 0;
+
+  for (int end_pos = maxl; end_pos > 0; end_pos -= kBatch) {
+    const int base = max(0, end_pos - kBatch);
+    const int cnt = end_pos - base;
+    stage_batch(value, rec, vn_base, r.x + base, cnt, s_a, s_b, s_g);
+    for (int i = threadIdx.x; i < cnt * 8; i += blockDim.x) s_acc[i] = 0.f;
+    __syncthreads();
+    for (int j = cnt - 1; j >= 0; --j) {
+      float gv[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      bool contrib = false;
+      if ((uint32_t)(base + j) < L) {
+        ++nev;
+        const float4 a = s_a[j];
+        const float4 b = s_b[j];
+        float dx, dy;
+        const float p = power_of(a, b.x, px, py, dx, dy);
+        const float e = xg_exp(p);
+        const float oe = fmul(b.y, e);
+        const float al = fminf(kAlphaMax, oe);
+        if (al >= kAlphaMin) {
+          contrib = true;
+          ++ncon;
+          Tc = __fdividef(Tc, 1.f - al);
+          const float in = b.z;
+          gv[6] = G * al * Tc;                 // dL/d intensity
+          const float dL_dal = G * Tc * (in - A);
+          A = al * in + (1.f - al) * A;
+          if (oe < kAlphaMax) {
+            gv[5] = dL_dal * e;                // dL/d opacity
+            const float dp = dL_dal * al;      // dL/d power
+            gv[0] = dp * (2.f * a.z * dx + a.w * dy);  // dL/du_x = dp * -(a dx + b dy)
+            gv[1] = dp * (2.f * b.x * dy + a.w * dx);  // dL/du_y = dp * -(b dx + c dy)
+            gv[2] = dp * (-0.5f * dx * dx);            // dL/d conic a
+            gv[3] = dp * (-dx * dy);                   // dL/d conic b
+            gv[4] = dp * (-0.5f * dy * dy);            // dL/d conic c
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) gv[k] += __shfl_xor_sync(0xffffffffu, gv[k], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < 7; ++k) atomicAdd(&s_acc[j * 8 + k], gv[k]);
+        }
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      const int64_t vg = vn_base + s_g[j];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const float val = s_acc[j * 8 + k];
+        if (val != 0.f) atomicAdd(&g2d[k * VN + vg], val);
+      }
+    }
+    __syncthreads();
+  }
+  add_counts(nev, ncon, &st->bwd_evaluated, &st->bwd_contrib);
+}
+
+cudaError_t launch_render_bwd(xg_frame* f, const float* grad_image, cudaStream_t st) {
+  const FramePtrs& p = f->p;
+  const int64_t VN = (int64_t)f->n_views * f->n;
+  cudaError_t e;
+  {
+    Timed t(f, kMemset, st);
+    e = cudaMemsetAsync(p.grad2d, 0, sizeof(float) * 7 * (size_t)VN, st);
+  }
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)f->tiles_per_view, (unsigned)f->n_views);
+  Timed t(f, kRenderBwd, st);
+  k_render_bwd<<<grid, f->cfg.tile_w * f->cfg.tile_h, 0, st>>>(
+      p.range, p.value[f->sorted_buf], p.rec, f->n, f->n_views, f->width, f->height, f->tiles_x,
+      f->tiles_per_view, f->cfg.tile_w, p.cam, p.status, grad_image, p.tfinal, p.last, p.grad2d);
+  return cudaGetLastError();
+}
+
+}  // namespace xg

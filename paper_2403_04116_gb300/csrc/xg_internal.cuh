@@ -1,0 +1,181 @@
+// Internal declarations shared by the library's CUDA translation units.
+//
+// FP32 decision sequence.  Every operation that decides which tiles a Gaussian touches,
+// the depth key, or whether a Gaussian contributes to a pixel is written with explicit
+// round-to-nearest intrinsics (__fmul_rn, __fadd_rn, __fmaf_rn, __fdiv_rn, __fsqrt_rn),
+// which the compiler never contracts or reorders.  The sequence is fixed and documented
+// so that an independent FP32 re-implementation reproduces tile ids, sort keys, ranges,
+// contributor counts and last-contributor positions bit for bit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/xg.h"
+
+namespace xg {
+
+constexpr int kMaxViews = 1 << 16;
+constexpr int kSortBlocks = 304;      // 2 x 152 SMs: grid of the scan and radix-sort passes
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;         // keys per thread per radix tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+// Decision constants (float roundings of the paper-level values).
+constexpr double kLn2D = 0.69314718055994530942;
+constexpr float kLog2e = (float)1.44269504088896340736;
+constexpr float kLn2Hi = (float)kLn2D;
+constexpr float kLn2Lo = (float)(kLn2D - (double)(float)kLn2D);
+constexpr float kSqrt2 = (float)1.41421356237309504880;
+constexpr float kAlphaMin = (float)(1.0 / 255.0);
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kDilate = 0.3f;
+constexpr float kRadiusMargin = 1.0009765625f;  // 1 + 2^-10
+
+// Per-view camera table in the workspace (16 floats).
+struct Camera {
+  float c, s;        // cos, sin of the azimuth (rounded from double)
+  float L;           // L_SO
+  float fu, fv;      // focal lengths in pixels, L_SD / pitch
+  float hw, hh;      // W/2 - 1/2, H/2 - 1/2: pixel x has centred coordinate x - hw
+  float pad[9];
+};
+static_assert(sizeof(Camera) == 64, "camera record is 64 bytes");
+
+struct DevStatus {
+  int32_t code;
+  int32_t reserved;
+  long long pairs;
+  unsigned long long nonfinite;
+  unsigned long long fwd_evaluated;   // (pixel, list entry) pairs evaluated by the last forward
+  unsigned long long fwd_contrib;     // of which contributed
+  unsigned long long bwd_evaluated;   // pairs re-evaluated by the last backward
+  unsigned long long bwd_contrib;     // of which contributed
+  unsigned long long scan_total;      // internal: total of the counts (before the capacity check)
+};
+static_assert(sizeof(DevStatus) == 64, "status is 64 bytes");
+
+// ------------------------------------------------------------------------------------------
+// exact FP32 helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+
+// e^x: Cody-Waite reduction by ln 2, degree-6 Taylor polynomial on |r| <= ln2/2, times 2^k.
+__device__ __forceinline__ float xg_exp(float x) {
+  x = fmaxf(x, -80.0f);
+  const float k = rintf(fmul(x, kLog2e));
+  float r = ffma(k, -kLn2Hi, x);
+  r = ffma(k, -kLn2Lo, r);
+  float p = ffma(r, (float)(1.0 / 720.0), (float)(1.0 / 120.0));
+  p = ffma(p, r, (float)(1.0 / 24.0));
+  p = ffma(p, r, (float)(1.0 / 6.0));
+  p = ffma(p, r, 0.5f);
+  p = ffma(p, r, 1.0f);
+  p = ffma(p, r, 1.0f);
+  return fmul(p, __int_as_float(((int)k + 127) << 23));
+}
+
+// ln x for finite x >= 1: x = m 2^e, m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s), s = (m-1)/(m+1).
+__device__ __forceinline__ float xg_log_ge1(float x) {
+  const unsigned b = __float_as_uint(x);
+  int e = (int)(b >> 23) - 127;
+  float m = __uint_as_float((b & 0x7fffffu) | 0x3f800000u);
+  if (m > kSqrt2) {
+    m = fmul(m, 0.5f);
+    e += 1;
+  }
+  const float s = fdiv(fsub(m, 1.0f), fadd(m, 1.0f));
+  const float s2 = fmul(s, s);
+  float p = ffma(s2, (float)(2.0 / 9.0), (float)(2.0 / 7.0));
+  p = ffma(p, s2, (float)(2.0 / 5.0));
+  p = ffma(p, s2, (float)(2.0 / 3.0));
+  p = ffma(p, s2, 2.0f);
+  p = fmul(p, s);
+  const float ef = (float)e;
+  const float t = ffma(ef, kLn2Lo, p);
+  return ffma(ef, kLn2Hi, t);
+}
+
+// ------------------------------------------------------------------------------------------
+// frame
+// ------------------------------------------------------------------------------------------
+struct FramePtrs {
+  DevStatus* status;
+  Camera* cam;
+  float4* rec;        // [V*n][2]
+  float* depth;       // [V*n]
+  ushort4* rect;      // [V*n]
+  uint32_t* count;    // [V*n]
+  uint32_t* offset;   // [V*n]
+  unsigned long long* scan_part;  // [kSortBlocks + 1]
+  uint32_t* key_tile[2];
+  uint32_t* key_depth[2];
+  uint32_t* value[2];
+  uint32_t* hist;     // [256][kSortBlocks]
+  uint2* range;       // [V*T]
+  float* tfinal;      // [V*H*W]
+  uint32_t* last;     // [V*H*W]
+  float* grad2d;      // [7][V*n]
+};
+
+}  // namespace xg
+
+namespace xg {
+enum KernelId {
+  kProject, kScanReduce, kScanTop, kScanDown, kEmit, kRadixHist, kRadixScan, kRadixScatter, kRanges,
+  kRenderFwd, kRenderBwd, kProjectBwd, kMemset, kNumKernels
+};
+struct TimingRec {
+  int kid;
+  cudaEvent_t a, b;
+};
+constexpr int kMaxTimingRecs = 2048;
+}  // namespace xg
+
+struct xg_frame {
+  xg_config cfg;
+  int64_t n;
+  int32_t n_views, width, height;
+  int32_t tiles_x, tiles_y;
+  int64_t tiles_per_view;
+  int32_t tile_bits;   // bits of view * T + tile
+  int32_t sort_passes;
+  int32_t sorted_buf;  // which ping-pong buffer holds the sorted pairs
+  void* workspace;
+  size_t workspace_bytes;
+  xg_layout layout;
+  xg::FramePtrs p;
+  // optional per-kernel timing with CUDA events on the launch stream
+  int timing;
+  int nrec;
+  int dropped;
+  xg::TimingRec* recs;
+  double acc_ms[xg::kNumKernels];
+  long long acc_n[xg::kNumKernels];
+};
+
+namespace xg {
+// Brackets one launch with timing events when the frame's timing is on.
+struct Timed {
+  xg_frame* f;
+  cudaStream_t st;
+  int slot;
+  Timed(xg_frame* frame, int kid, cudaStream_t stream);
+  ~Timed();
+};
+
+// launchers, one per translation unit
+cudaError_t launch_project(xg_frame* f, const xg_gaussians* g, cudaStream_t st);
+cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st);
+cudaError_t launch_render_fwd(xg_frame* f, float* image, uint32_t* n_contrib, cudaStream_t st);
+cudaError_t launch_render_bwd(xg_frame* f, const float* grad_image, cudaStream_t st);
+cudaError_t launch_project_bwd(xg_frame* f, const xg_gaussians* g, const xg_grads* out, cudaStream_t st);
+cudaError_t launch_loss_l1(const float* image, const float* target, int64_t count, float scale, float* grad,
+                           float* loss, cudaStream_t st);
+}  // namespace xg

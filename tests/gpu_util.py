@@ -1,0 +1,59 @@
+"""Helpers shared by the GPU tests: run the CUDA path through the C ABI and pull every
+intermediate array back to the host."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from paper_2403_04116_gb300 import binding as B
+from paper_2403_04116_gb300.render import Frame, FrameConfig
+
+NAMES = ("mean", "scale", "quat", "opacity", "intensity")
+
+
+def to_device(g: dict) -> tuple:
+    return tuple(torch.from_numpy(np.ascontiguousarray(g[k], dtype=np.float32)).cuda() for k in NAMES)
+
+
+def run_forward(g: dict, views, tile=(16, 16), capacity=None, near_mm=0.2) -> dict:
+    """Project, bin, sort and render through the C ABI.  Without ``capacity`` the pair
+    capacity is sized from a first binning pass (so the frame never overflows)."""
+    dev = to_device(g)
+    n = dev[4].shape[0]
+    cap = capacity or max(1 << 16, 16 * n * len(views))
+    f = Frame(n, views, FrameConfig(tile[0], tile[1], near_mm), cap)
+    f.project(*dev)
+    proj = {"records": f.array("records").cpu().numpy(), "depth": f.array("depth").cpu().numpy(),
+            "rect": f.array("rect").cpu().numpy().astype(np.int32), "count": f.array("count").cpu().numpy()}
+    f.bin_sort()
+    st = f.status()
+    if capacity is None and st.code == B.XG_ERR_CAPACITY:
+        f = Frame(n, views, FrameConfig(tile[0], tile[1], near_mm), int(st.pairs))
+        f.project(*dev)
+        f.bin_sort()
+        st = f.status()
+    image = torch.empty((f.V, f.H, f.W), dtype=torch.float32, device="cuda")
+    ncon = torch.empty((f.V, f.H, f.W), dtype=torch.int32, device="cuda")
+    f.render_fwd(image, ncon)
+    torch.cuda.synchronize()
+    M = int(st.pairs) if st.code == B.XG_OK else 0
+    out = {**proj, "status": st, "M": M, "frame": f, "dev": dev,
+           "key_tile": f.array("key_tile")[:M].cpu().numpy().view(np.uint32),
+           "key_depth": f.array("key_depth")[:M].cpu().numpy().view(np.uint32),
+           "value": f.array("value")[:M].cpu().numpy(),
+           "range": f.array("range").cpu().numpy().view(np.uint32),
+           "image": image.cpu().numpy(), "ncontrib": ncon.cpu().numpy(),
+           "tfinal": f.array("tfinal").cpu().numpy().reshape(f.V, f.H, f.W),
+           "last": f.array("last").cpu().numpy().reshape(f.V, f.H, f.W)}
+    return out
+
+
+def run_backward(fwd: dict, grad_image: np.ndarray) -> dict:
+    f, dev = fwd["frame"], fwd["dev"]
+    G = torch.from_numpy(np.ascontiguousarray(grad_image, dtype=np.float32)).cuda()
+    grads = tuple(torch.empty_like(t) for t in dev)
+    f.render_bwd(dev, G, grads)
+    torch.cuda.synchronize()
+    out = {k: t.cpu().numpy() for k, t in zip(NAMES, grads)}
+    out["g2d"] = f.array("grad2d").cpu().numpy()
+    return out

@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads without a GPU, and exports every symbol include/xg.h
+declares; its host-only argument checks work.  No call here touches a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2403_04116_gb300 import binding as B
+from paper_2403_04116_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "xg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(xg_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return B.lib()
+
+
+def test_header_declares_the_binding_names():
+    assert _declared() == sorted(B.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    raw = ctypes.CDLL(build.LIB)
+    for name in _declared():
+        assert hasattr(raw, name), name
+
+
+def test_workspace_bytes_host_checks(lib):
+    cfg = B.XgConfig(16, 16, 0.2, 0, 1 << 20)
+    small = B.xg_workspace_bytes(cfg, 1000, 2, 64, 64)
+    big = B.xg_workspace_bytes(cfg, 1000, 4, 64, 64)
+    assert 0 < small < big
+    assert B.xg_workspace_bytes(cfg, 0, 1, 64, 64) == 0
+    assert B.xg_workspace_bytes(cfg, 10, 1, 0, 64) == 0
+    for bad in (B.XgConfig(12, 16, 0.2, 0, 100), B.XgConfig(32, 32, 0.2, 0, 100), B.XgConfig(16, 16, 0.0, 0, 100),
+                B.XgConfig(16, 16, 0.2, 0, 0), B.XgConfig(16, 16, float("nan"), 0, 100)):
+        assert B.xg_workspace_bytes(bad, 10, 1, 64, 64) == 0
+
+
+def test_frame_create_rejects_bad_arguments_before_touching_the_device(lib):
+    from paper_2403_04116_gb300.synth import View
+    cfg = B.XgConfig(16, 16, 0.2, 0, 1000)
+    good = View(1000.0, 1500.0, 1.0, 1.0, 0.0, 64, 64)
+    cases = [
+        [View(1000.0, 1500.0, 1.0, 1.0, 0.0, 64, 64), View(1000.0, 1500.0, 1.0, 1.0, 0.5, 32, 64)],  # sizes differ
+        [View(-1.0, 1500.0, 1.0, 1.0, 0.0, 64, 64)],
+        [View(1000.0, 1500.0, 0.0, 1.0, 0.0, 64, 64)],
+        [View(1000.0, 1500.0, 1.0, 1.0, float("inf"), 64, 64)],
+        [View(1000.0, 1500.0, 1.0, 1.0, 0.0, 5000, 64)],
+    ]
+    for views in cases:
+        with pytest.raises(B.XgError) as e:
+            B.xg_frame_create(cfg, 10, views, 0, 1 << 30, 0)
+        assert e.value.code == B.XG_ERR_INVALID_ARG
+    # a missing or short workspace is refused
+    with pytest.raises(B.XgError) as e:
+        B.xg_frame_create(cfg, 10, [good], 0, 1 << 30, 0)
+    assert e.value.code == B.XG_ERR_WORKSPACE
+    with pytest.raises(B.XgError) as e:
+        B.xg_frame_create(cfg, 10, [good], 256, 16, 0)
+    assert e.value.code == B.XG_ERR_WORKSPACE
+
+
+def test_status_strings(lib):
+    assert B.xg_status_str(B.XG_OK) == "ok"
+    assert "capacity" in B.xg_status_str(B.XG_ERR_CAPACITY)

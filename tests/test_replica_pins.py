@@ -17,7 +17,7 @@ def test_exp_accuracy(oracle_lib):
     x = np.concatenate([np.linspace(-80, 0, 400001, dtype=np.float32), np.float32([0.0, -1e-30, -5.54, 1e-7])])
     y = oracle.replica_exp(x).astype(np.float64)
     ref = np.exp(x.astype(np.float64))
-    assert np.max(np.abs(y / ref - 1)) < 4e-6
+    assert np.max(np.abs(y / ref - 1)) < 4e-7  # degree-6 Taylor bound 1.2e-7 plus float rounding
     assert oracle.replica_exp(np.float32([0.0]))[0] == 1.0
 
 
