@@ -206,6 +206,38 @@ xg_status xg_frame_set_timing(xg_frame* frame, int32_t enable);
  * and the number written to *count, and start a new accumulation. */
 xg_status xg_frame_read_timing(xg_frame* frame, xg_kernel_time* out, int32_t capacity, int32_t* count);
 
+/* Largest pair count xg_sort_pairs_noalloc accepts. */
+#define XG_NOALLOC_MAX_PAIRS (1 << 20)
+
+/* Allocation-free pair sort.  The paper has no counterpart of this call: it is the stable
+ * radix sort inside xg_bin_sort, offered on its own to callers that cannot allocate device
+ * memory -- plugins hosted by an application that owns the GPU's memory pool, and
+ * real-time pipelines that forbid allocation after start-up (cudaMalloc can synchronise
+ * the device and takes unbounded time).  Such callers could not provide xg_bin_sort's
+ * workspace.
+ *
+ * Sorts `count` (key_tile, key_depth, value) triples stably by key_tile, then key_depth,
+ * into out_key_tile, out_key_depth, out_value (all device uint32[count]; the outputs must
+ * not overlap the inputs).  Only the low `tile_bits` bits of key_tile may be non-zero
+ * (0 <= tile_bits <= 32).  Given the pairs xg_bin_sort emits, the output equals its
+ * sorted pairs.
+ *
+ * Scratch: a static device array of about 12.3 MB inside the library (ping-pong buffers
+ * for XG_NOALLOC_MAX_PAIRS pairs, digit histograms, the pair count), held by every GPU that
+ * loads the library until the process exits.  The call allocates nothing and frees
+ * nothing.  Its first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls on a device
+ * share the array and the last call's contents stay in it: calls whose work overlaps on
+ * the GPU (different streams without ordering between them) race and give wrong results;
+ * order them on one stream.
+ *
+ * Errors: XG_ERR_INVALID_ARG if count < 0, count > XG_NOALLOC_MAX_PAIRS, tile_bits is out
+ * of range or a pointer is NULL (nothing is enqueued); XG_ERR_CUDA if the address lookup
+ * or a launch fails.  count == 0 enqueues nothing. */
+xg_status xg_sort_pairs_noalloc(const uint32_t* key_tile, const uint32_t* key_depth, const uint32_t* value,
+                                int64_t count, int32_t tile_bits, uint32_t* out_key_tile, uint32_t* out_key_depth,
+                                uint32_t* out_value, void* stream);
+
 /* Text for a status code (static storage). */
 const char* xg_status_str(xg_status s);
 

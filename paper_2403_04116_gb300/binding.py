@@ -20,7 +20,8 @@ XG_ERR_CHECK = 5
 # Every symbol include/xg.h declares.
 EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_project", "xg_bin_sort",
            "xg_render_fwd", "xg_render_bwd", "xg_frame_read_status", "xg_frame_layout", "xg_loss_l1",
-           "xg_frame_set_timing", "xg_frame_read_timing", "xg_status_str")
+           "xg_frame_set_timing", "xg_frame_read_timing", "xg_sort_pairs_noalloc", "xg_status_str")
+XG_NOALLOC_MAX_PAIRS = 1 << 20
 
 
 class XgView(ctypes.Structure):
@@ -114,6 +115,8 @@ def lib(build_if_missing: bool = False):
     L.xg_frame_read_timing.argtypes = [P, ctypes.POINTER(XgKernelTime), ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_int32)]
     L.xg_frame_read_timing.restype = ctypes.c_int
+    L.xg_sort_pairs_noalloc.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int32, P, P, P, P]
+    L.xg_sort_pairs_noalloc.restype = ctypes.c_int
     L.xg_status_str.argtypes = [ctypes.c_int]
     L.xg_status_str.restype = ctypes.c_char_p
     _lib = L
@@ -188,3 +191,9 @@ def xg_frame_read_timing(frame: int) -> dict:
     count = ctypes.c_int32()
     _check(lib().xg_frame_read_timing(frame, out, 32, ctypes.byref(count)), "xg_frame_read_timing")
     return {out[i].name.decode(): (int(out[i].launches), float(out[i].total_ms)) for i in range(count.value)}
+
+
+def xg_sort_pairs_noalloc(key_tile: int, key_depth: int, value: int, count: int, tile_bits: int,
+                          out_key_tile: int, out_key_depth: int, out_value: int, stream: int) -> None:
+    _check(lib().xg_sort_pairs_noalloc(key_tile, key_depth, value, count, tile_bits, out_key_tile, out_key_depth,
+                                       out_value, stream), "xg_sort_pairs_noalloc")

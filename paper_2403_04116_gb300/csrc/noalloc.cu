@@ -1,0 +1,97 @@
+// Allocation-free variant of the pair sort inside xg_bin_sort.
+//
+// Some callers cannot allocate device memory: plugins hosted by an application that owns
+// the GPU's memory pool, and real-time pipelines that forbid allocation after start-up
+// (cudaMalloc can synchronise the device and its latency is unbounded).  They can still
+// sort (tile, depth, Gaussian) pairs with xg_sort_pairs_noalloc: the caller passes only
+// the input and output arrays; the ping-pong buffers, the digit histograms and the pair
+// count live in the file-scope device array below.  Every GPU that loads the library holds
+// that array (about 12.3 MB) until the process exits.
+#include <mutex>
+
+#include "xg_internal.cuh"
+
+namespace xg {
+
+constexpr size_t kNoallocStatusBytes = 256;
+constexpr size_t kNoallocHistBytes = (size_t)4 * 256 * kSortBlocks;
+constexpr size_t kNoallocBufBytes = (size_t)4 * XG_NOALLOC_MAX_PAIRS;
+constexpr size_t kNoallocBytes = kNoallocStatusBytes + kNoallocHistBytes + 3 * kNoallocBufBytes;
+
+// Shared by every call on a device; the last call's contents stay behind.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices];
+
+// Device address of the scratch array on the current device, looked up once per device.
+// In host code `g_noalloc_scratch` names a host-side stand-in, never pass it to a kernel.
+xg_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return XG_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return XG_ERR_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = (unsigned char*)g_noalloc_ptr[dev];
+  return XG_OK;
+}
+
+}  // namespace
+
+// The status word the radix kernels read the pair count from; cleared on every call.
+__global__ void k_noalloc_status(DevStatus* st, int64_t count) {
+  if (threadIdx.x != 0) return;
+  st->code = XG_OK;
+  st->reserved = 0;
+  st->pairs = count;
+  st->nonfinite = 0;
+  st->fwd_evaluated = st->fwd_contrib = st->bwd_evaluated = st->bwd_contrib = 0;
+  st->scan_total = (unsigned long long)count;
+}
+
+}  // namespace xg
+
+extern "C" xg_status xg_sort_pairs_noalloc(const uint32_t* key_tile, const uint32_t* key_depth, const uint32_t* value,
+                                           int64_t count, int32_t tile_bits, uint32_t* out_key_tile,
+                                           uint32_t* out_key_depth, uint32_t* out_value, void* stream) {
+  using namespace xg;
+  if (count < 0 || count > XG_NOALLOC_MAX_PAIRS || tile_bits < 0 || tile_bits > 32) return XG_ERR_INVALID_ARG;
+  if (count > 0 && (!key_tile || !key_depth || !value || !out_key_tile || !out_key_depth || !out_value))
+    return XG_ERR_INVALID_ARG;
+  unsigned char* base = nullptr;
+  const xg_status s = noalloc_scratch(&base);
+  if (s != XG_OK) return s;
+  if (count == 0) return XG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevStatus* status = (DevStatus*)base;
+  uint32_t* hist = (uint32_t*)(base + kNoallocStatusBytes);
+  uint32_t* tmp_tile = (uint32_t*)(base + kNoallocStatusBytes + kNoallocHistBytes);
+  uint32_t* tmp_depth = tmp_tile + XG_NOALLOC_MAX_PAIRS;
+  uint32_t* tmp_val = tmp_depth + XG_NOALLOC_MAX_PAIRS;
+
+  k_noalloc_status<<<1, 32, 0, st>>>(status, count);
+  const int passes = 4 + (tile_bits + 7) / 8;
+  // alternate so that the last pass writes the caller's output
+  const uint32_t* src[3] = {key_tile, key_depth, value};
+  for (int pass = 0; pass < passes; ++pass) {
+    const bool to_out = ((passes - 1 - pass) % 2) == 0;
+    uint32_t* dst[3] = {to_out ? out_key_tile : tmp_tile, to_out ? out_key_depth : tmp_depth,
+                        to_out ? out_value : tmp_val};
+    const int digit_word = pass < 4 ? 0 : 1;
+    const int shift = pass < 4 ? 8 * pass : 8 * (pass - 4);
+    k_radix_hist<<<kSortBlocks, kSortThreads, 0, st>>>(digit_word ? src[0] : src[1], shift, status, hist);
+    k_radix_scan<<<1, 1024, 0, st>>>(hist);
+    k_radix_scatter<<<kSortBlocks, kSortThreads, 0, st>>>(src[0], src[1], src[2], dst[0], dst[1], dst[2], digit_word,
+                                                          shift, status, hist);
+    src[0] = dst[0];
+    src[1] = dst[1];
+    src[2] = dst[2];
+  }
+  return cudaGetLastError() == cudaSuccess ? XG_OK : XG_ERR_CUDA;
+}

@@ -178,4 +178,14 @@ cudaError_t launch_render_bwd(xg_frame* f, const float* grad_image, cudaStream_t
 cudaError_t launch_project_bwd(xg_frame* f, const xg_gaussians* g, const xg_grads* out, cudaStream_t st);
 cudaError_t launch_loss_l1(const float* image, const float* target, int64_t count, float scale, float* grad,
                            float* loss, cudaStream_t st);
+
+// radix-sort passes (binning.cu), also launched by the allocation-free pair sort
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ word, int shift,
+                                                             const DevStatus* __restrict__ st,
+                                                             uint32_t* __restrict__ hist);
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist);
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const uint32_t* __restrict__ in_tile, const uint32_t* __restrict__ in_depth, const uint32_t* __restrict__ in_val,
+    uint32_t* __restrict__ out_tile, uint32_t* __restrict__ out_depth, uint32_t* __restrict__ out_val, int digit_word,
+    int shift, DevStatus* __restrict__ st, const uint32_t* __restrict__ hist);
 }  // namespace xg
