@@ -115,18 +115,18 @@ typedef struct {
  *   depth      float[V*n]     t_z (0 where it touches no tile)
  *   rect       uint16[V*n][4] tile rectangle (x0, y0, x1, y1), inclusive
  *   count      uint32[V*n]    tiles touched
- *   offset     uint32[V*n]    exclusive prefix sum of count, view-major
+ *   offset     uint32[V*n]    exclusive prefix sum of count, taken over the (view,
+ *                             Gaussian) entries in (view, t_z, index) order
  *   key_tile   uint32[cap]    sorted pairs: view * T + tile
- *   key_depth  uint32[cap]    sorted pairs: bits of t_z
  *   value      uint32[cap]    sorted pairs: Gaussian index
  *   range      uint32[V*T][2] [start, end) of each tile in the sorted pairs ([0, 0) if empty)
  *   tfinal     float[V][H][W] transmittance after the last contributor
  *   last       uint32[V][H][W] 1-based position in the tile's list of the last contributor
- *   grad2d     float[7][V*n]  per (view, Gaussian): dL/du_x, dL/du_y, dL/da, dL/db, dL/dc,
- *                             dL/dopacity, dL/dintensity (written by xg_render_bwd) */
+ *   grad2d     float[V*n][8]  per (view, Gaussian): dL/du_x, dL/du_y, dL/da, dL/db, dL/dc,
+ *                             dL/dopacity, dL/dintensity, 0 (written by xg_render_bwd) */
 typedef struct {
   size_t status, cameras, records, depth, rect, count, offset;
-  size_t key_tile, key_depth, value, range, tfinal, last, grad2d;
+  size_t key_tile, value, range, tfinal, last, grad2d;
   int64_t tiles_per_view;
   int32_t tiles_x, tiles_y;
   int32_t sort_passes;
@@ -155,10 +155,12 @@ void xg_frame_destroy(xg_frame* frame);
  * the frame's records, depth, rect and count arrays.  `g` must have the frame's n. */
 xg_status xg_project(xg_frame* frame, const xg_gaussians* g, void* stream);
 
-/* Tile binning and the depth-keyed radix sort (Sec. 3.2): prefix-sums the counts, emits one
- * (view * T + tile, bits of t_z, Gaussian) pair per touched tile, sorts them by tile and
- * then depth with a stable LSD radix sort, and extracts each tile's range.  Sets
- * XG_ERR_CAPACITY in the device status if the pairs exceed pair_capacity. */
+/* Tile binning and the depth-keyed radix sort (Sec. 3.2).  Orders the (view, Gaussian)
+ * entries by (view, t_z) with a stable LSD radix sort, prefix-sums their tile counts in that
+ * order, emits one (view * T + tile, Gaussian) pair per touched tile, sorts the pairs stably
+ * by tile, and extracts each tile's range: every tile's list is in ascending t_z, ties by
+ * ascending Gaussian index.  Sets XG_ERR_CAPACITY in the device status if the pairs exceed
+ * pair_capacity. */
 xg_status xg_bin_sort(xg_frame* frame, void* stream);
 
 /* Front-to-back alpha compositing of intensity per detector pixel (Eq. 10).

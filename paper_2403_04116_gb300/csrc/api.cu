@@ -29,7 +29,7 @@ bool valid_sizes(int64_t n, int32_t n_views, int32_t W, int32_t H) {
 struct Sizes {
   int32_t tiles_x, tiles_y;
   int64_t tiles_per_view;
-  int32_t tile_bits, passes;
+  int32_t tile_bits, entry_passes, tile_passes;
 };
 
 bool sizes_of(const xg_config* cfg, int64_t n_views, int32_t W, int32_t H, Sizes* s) {
@@ -40,15 +40,18 @@ bool sizes_of(const xg_config* cfg, int64_t n_views, int32_t W, int32_t H, Sizes
   if (keys >= ((int64_t)1 << 31)) return false;
   int bits = 0;
   while (((int64_t)1 << bits) < keys) ++bits;
+  int vbits = 0;
+  while (((int64_t)1 << vbits) < n_views) ++vbits;
   s->tile_bits = bits;
-  s->passes = 4 + (bits + 7) / 8;
+  s->entry_passes = 4 + (vbits + 7) / 8;
+  s->tile_passes = (bits + 7) / 8;
   return true;
 }
 
 // Byte offsets of every array in the workspace, public and private, in allocation order.
 struct Offsets {
   size_t status, cameras, records, depth, rect, count, offset, scan_part;
-  size_t key_tile[2], key_depth[2], value[2], hist, range, tfinal, last, grad2d;
+  size_t ent_view[2], ent_depth[2], ent_gid[2], key_tile[2], value[2], hist, range, tfinal, last, grad2d;
   size_t total;
 };
 
@@ -71,14 +74,16 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t W, int32_t
   o->count = take(4 * VN);
   o->offset = take(4 * VN);
   o->scan_part = take(8 * (xg::kSortBlocks + 1));
+  for (int b = 0; b < 2; ++b) o->ent_view[b] = take(4 * VN);
+  for (int b = 0; b < 2; ++b) o->ent_depth[b] = take(4 * VN);
+  for (int b = 0; b < 2; ++b) o->ent_gid[b] = take(4 * VN);
   for (int b = 0; b < 2; ++b) o->key_tile[b] = take(4 * cap);
-  for (int b = 0; b < 2; ++b) o->key_depth[b] = take(4 * cap);
   for (int b = 0; b < 2; ++b) o->value[b] = take(4 * cap);
   o->hist = take(4 * 256 * (size_t)xg::kSortBlocks);
   o->range = take(8 * (size_t)V * (size_t)s->tiles_per_view);
   o->tfinal = take(4 * pix);
   o->last = take(4 * pix);
-  o->grad2d = take(4 * 7 * VN);
+  o->grad2d = take(4 * 8 * VN);
   o->total = off;
   return true;
 }
@@ -87,7 +92,7 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t W, int32_t
 
 namespace xg {
 Timed::Timed(xg_frame* frame, int kid, cudaStream_t stream) : f(frame), st(stream), slot(-1) {
-  if (!f->timing) return;
+  if (!f || !f->timing) return;
   if (f->nrec >= kMaxTimingRecs) {
     ++f->dropped;
     return;
@@ -140,8 +145,9 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   f->tiles_y = s.tiles_y;
   f->tiles_per_view = s.tiles_per_view;
   f->tile_bits = s.tile_bits;
-  f->sort_passes = s.passes;
-  f->sorted_buf = s.passes & 1;  // each pass moves the pairs to the other buffer
+  f->entry_passes = s.entry_passes;
+  f->tile_passes = s.tile_passes;
+  f->sorted_buf = s.tile_passes & 1;  // each pass moves the pairs to the other buffer
   f->workspace = workspace;
   f->workspace_bytes = workspace_bytes;
 
@@ -156,8 +162,10 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   p.offset = (uint32_t*)(base + o.offset);
   p.scan_part = (unsigned long long*)(base + o.scan_part);
   for (int k = 0; k < 2; ++k) {
+    p.ent_view[k] = (uint32_t*)(base + o.ent_view[k]);
+    p.ent_depth[k] = (uint32_t*)(base + o.ent_depth[k]);
+    p.ent_gid[k] = (uint32_t*)(base + o.ent_gid[k]);
     p.key_tile[k] = (uint32_t*)(base + o.key_tile[k]);
-    p.key_depth[k] = (uint32_t*)(base + o.key_depth[k]);
     p.value[k] = (uint32_t*)(base + o.value[k]);
   }
   p.hist = (uint32_t*)(base + o.hist);
@@ -175,7 +183,6 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   L.count = o.count;
   L.offset = o.offset;
   L.key_tile = o.key_tile[f->sorted_buf];
-  L.key_depth = o.key_depth[f->sorted_buf];
   L.value = o.value[f->sorted_buf];
   L.range = o.range;
   L.tfinal = o.tfinal;
@@ -184,7 +191,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   L.tiles_per_view = s.tiles_per_view;
   L.tiles_x = s.tiles_x;
   L.tiles_y = s.tiles_y;
-  L.sort_passes = s.passes;
+  L.sort_passes = s.entry_passes + s.tile_passes;
 
   // camera table: trigonometry in FP64, rounded once to FP32
   xg::Camera* cams = (xg::Camera*)calloc((size_t)n_views, sizeof(xg::Camera));

@@ -1,14 +1,25 @@
 // Tile binning and the depth-keyed radix sort (Sec. 3.2: Gaussians are assigned to the
 // tiles their projection touches and sorted by depth).
 //
-//   count --scan--> offset --emit--> (tile key, depth key, Gaussian) pairs
-//         --LSD radix sort, 8-bit digits, depth bytes first, then tile bytes--> sorted pairs
-//         --ranges--> [start, end) per (view, tile)
+// The (tile, depth) order of the pairs is built in two stable LSD radix sorts, so that the
+// many pairs (one per touched tile) are moved only by their tile key:
+//
+//   1. the V*n (view, Gaussian) entries, keyed (view, bits of t_z) -- 4 depth passes and
+//      ceil(log2(V)/8) view passes over V*n entries (k_project writes the keys);
+//   2. the tile counts, gathered in that order, are prefix-summed and every entry emits one
+//      (view * T + tile, Gaussian) pair per touched tile at its offset, so the emitted list
+//      is ordered by (view, depth, index);
+//   3. the pairs are sorted stably by tile key alone (ceil(log2(V*T)/8) passes), which
+//      leaves every tile's list in (depth, index) order;
+//   4. ranges: [start, end) per (view, tile).
+//
+// The result equals a stable sort of all pairs by the 64-bit key (tile, bits of t_z) of an
+// index-ordered emission, at well under half of its memory traffic.
 //
 // Every kernel here runs on a fixed grid of kSortBlocks CTAs that split the work into
-// contiguous chunks computed on the device from the pair count, so the host never needs to
-// know the count and the whole sequence can be captured in a CUDA graph.  There is no
-// inter-CTA waiting: each scan is reduce / scan-of-partials / down-sweep in three launches.
+// contiguous chunks computed on the device from the item count, so the host never needs to
+// know the pair count and the whole sequence can be captured in a CUDA graph.  There is no
+// inter-CTA waiting: every scan is reduce / scan-of-partials / down-sweep in three launches.
 #include "xg_internal.cuh"
 
 namespace xg {
@@ -21,11 +32,16 @@ __device__ __forceinline__ int64_t chunk_of(int64_t total) {
   return (c + kSortTile - 1) / kSortTile * kSortTile;
 }
 
-__device__ __forceinline__ int64_t pairs_of(const DevStatus* st) { return st->code == XG_OK ? st->pairs : 0; }
+// Item count of a sort: `fixed` if it is >= 0, else the pairs recorded in the status word.
+__device__ __forceinline__ int64_t items_of(const DevStatus* st, int64_t fixed) {
+  if (fixed >= 0) return fixed;
+  return st->code == XG_OK ? st->pairs : 0;
+}
 
-// exclusive scan of one value per thread across a 256-thread block; returns the block total
-template <typename T>
+// exclusive scan of one value per thread across a block of NT threads; returns the total
+template <int NT, typename T>
 __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T& total) {
+  constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T x = v;
 #pragma unroll
@@ -36,33 +52,40 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T& total) {
   if (lane == 31) s_warp[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    T w = lane < kWarps ? s_warp[lane] : T(0);
+    T w = lane < NW ? s_warp[lane] : T(0);
 #pragma unroll
-    for (int o = 1; o < kWarps; o <<= 1) {
+    for (int o = 1; o < NW; o <<= 1) {
       T y = __shfl_up_sync(0xffffffffu, w, o);
       if (lane >= o) w += y;
     }
-    if (lane < kWarps) s_warp[lane] = w;
+    if (lane < NW) s_warp[lane] = w;
   }
   __syncthreads();
   const T before = warp > 0 ? s_warp[warp - 1] : T(0);
-  total = s_warp[kWarps - 1];
+  total = s_warp[NW - 1];
   __syncthreads();
   return before + x - v;
 }
 
 // ------------------------------------------------------------------------------------------
-// scan of the per-(view, Gaussian) tile counts
+// scan of the tile counts, read in the (view, depth) order of stage 1
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSortThreads) k_scan_reduce(const uint32_t* __restrict__ count, int64_t total,
-                                                              unsigned long long* __restrict__ part) {
+__device__ __forceinline__ uint32_t count_at(const uint32_t* __restrict__ count, const uint32_t* __restrict__ view,
+                                             const uint32_t* __restrict__ gid, int64_t n, int64_t i) {
+  return count[(int64_t)view[i] * n + gid[i]];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_scan_reduce(const uint32_t* __restrict__ count,
+                                                              const uint32_t* __restrict__ view,
+                                                              const uint32_t* __restrict__ gid, int64_t n,
+                                                              int64_t total, unsigned long long* __restrict__ part) {
   __shared__ unsigned long long s_warp[kWarps];
   const int64_t chunk = chunk_of(total);
   const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
   unsigned long long acc = 0;
-  for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads) acc += count[i];
+  for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads) acc += count_at(count, view, gid, n, i);
   unsigned long long tot;
-  block_exclusive_scan(acc, s_warp, tot);
+  block_exclusive_scan<kSortThreads>(acc, s_warp, tot);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
@@ -80,8 +103,10 @@ __global__ void k_scan_top(unsigned long long* __restrict__ part, int64_t capaci
   st->code = run > (unsigned long long)capacity ? XG_ERR_CAPACITY : XG_OK;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* __restrict__ count, int64_t total,
-                                                            const unsigned long long* __restrict__ part,
+__global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* __restrict__ count,
+                                                            const uint32_t* __restrict__ view,
+                                                            const uint32_t* __restrict__ gid, int64_t n,
+                                                            int64_t total, const unsigned long long* __restrict__ part,
                                                             uint32_t* __restrict__ offset) {
   __shared__ unsigned long long s_warp[kWarps];
   const int64_t chunk = chunk_of(total);
@@ -89,34 +114,33 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* __re
   unsigned long long run = part[blockIdx.x];
   for (int64_t base = beg; base < end; base += kSortThreads) {
     const int64_t i = base + threadIdx.x;
-    const unsigned long long c = i < end ? count[i] : 0ull;
+    const unsigned long long c = i < end ? count_at(count, view, gid, n, i) : 0ull;
     unsigned long long tot;
-    const unsigned long long ex = block_exclusive_scan(c, s_warp, tot);
+    const unsigned long long ex = block_exclusive_scan<kSortThreads>(c, s_warp, tot);
     if (i < end) offset[i] = (uint32_t)(run + ex);
     run += tot;
   }
 }
 
 // ------------------------------------------------------------------------------------------
-// emit one pair per touched tile
+// emit one (tile key, Gaussian) pair per touched tile, in (view, depth) order
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ count, const uint32_t* __restrict__ offset,
-                                              const ushort4* __restrict__ rect, const float* __restrict__ depth,
-                                              int64_t n, int n_views, int tiles_x, int64_t tiles_per_view,
-                                              int64_t capacity, DevStatus* __restrict__ st,
-                                              uint32_t* __restrict__ key_tile,
-                                              uint32_t* __restrict__ key_depth, uint32_t* __restrict__ value) {
-  const int64_t vg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (vg >= (int64_t)n_views * n) return;
+                                              const ushort4* __restrict__ rect, const uint32_t* __restrict__ view,
+                                              const uint32_t* __restrict__ gid, int64_t n, int64_t total,
+                                              int tiles_x, int64_t tiles_per_view, int64_t capacity,
+                                              DevStatus* __restrict__ st, uint32_t* __restrict__ key_tile,
+                                              uint32_t* __restrict__ value) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
   if (st->code != XG_OK) return;
+  const uint32_t v = view[i], g = gid[i];
+  const int64_t vg = (int64_t)v * n + g;
   const uint32_t cnt = count[vg];
   if (cnt == 0) return;
-  const int v = (int)(vg / n);
-  const uint32_t g = (uint32_t)(vg - (int64_t)v * n);
   const ushort4 r = rect[vg];
-  const uint32_t dbits = __float_as_uint(depth[vg]);
   const uint32_t vbase = (uint32_t)(v * tiles_per_view);
-  uint32_t o = offset[vg];
+  uint32_t o = offset[i];
   if ((int64_t)o + cnt > capacity) {  // cannot happen when the scan is right
     st->code = XG_ERR_CHECK;
     return;
@@ -124,23 +148,23 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ count
   for (int ty = r.y; ty <= r.w; ++ty)
     for (int tx = r.x; tx <= r.z; ++tx) {
       key_tile[o] = vbase + (uint32_t)(ty * tiles_x + tx);
-      key_depth[o] = dbits;
       value[o] = g;
       ++o;
     }
 }
 
 // ------------------------------------------------------------------------------------------
-// LSD radix sort of (key_tile, key_depth, value) triples, one 8-bit digit per pass
+// LSD radix sort, one 8-bit digit per pass, of WORDS parallel u32 arrays; the digit comes
+// from array `digit_word`.  Histograms are block-major: hist[block][256].
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ word, int shift,
-                                                             const DevStatus* __restrict__ st,
+                                                             const DevStatus* __restrict__ st, int64_t fixed_count,
                                                              uint32_t* __restrict__ hist) {
   __shared__ uint32_t s_h[kWarps][256];
   const int warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&s_h[0][0])[i] = 0;
   __syncthreads();
-  const int64_t total = pairs_of(st);
+  const int64_t total = items_of(st, fixed_count);
   const int64_t chunk = chunk_of(total);
   const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
   for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&s_h[warp][(word[i] >> shift) & 255u], 1u);
@@ -148,79 +172,79 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
   uint32_t c = 0;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) c += s_h[w][threadIdx.x];
-  hist[threadIdx.x * kSortBlocks + blockIdx.x] = c;
+  hist[blockIdx.x * 256 + threadIdx.x] = c;
 }
 
-// exclusive scan over hist[256][kSortBlocks] in digit-major order (one CTA of 1024 threads)
+// Exclusive scan of hist in (digit, block) order, in place.  1024 threads: thread (q, d)
+// walks digit d over the q-th quarter of the blocks, one coalesced 1 KB row per step.
 __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist) {
-  constexpr int kN = 256 * kSortBlocks;
-  constexpr int kPer = (kN + 1023) / 1024;
+  constexpr int kQ = 4;
+  constexpr int kPer = (kSortBlocks + kQ - 1) / kQ;
+  __shared__ uint32_t s_part[kQ][256];
+  __shared__ uint32_t s_base[256];
   __shared__ uint32_t s_warp[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int beg = threadIdx.x * kPer;
-  uint32_t local = 0;
-  for (int i = 0; i < kPer; ++i)
-    if (beg + i < kN) local += hist[beg + i];
-  uint32_t x = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[warp] = x;
+  const int d = threadIdx.x & 255, q = threadIdx.x >> 8;
+  const int b0 = q * kPer, b1 = min(kSortBlocks, b0 + kPer);
+  uint32_t sum = 0;
+#pragma unroll 8
+  for (int b = b0; b < b1; ++b) sum += hist[b * 256 + d];
+  s_part[q][d] = sum;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t w = s_warp[lane];
+  uint32_t digit_total = 0;
+  if (q == 0) {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    s_warp[lane] = w;
+    for (int k = 0; k < kQ; ++k) digit_total += s_part[k][d];
   }
+  uint32_t all;
+  const uint32_t base = block_exclusive_scan<1024>(digit_total, s_warp, all);  // threads with q > 0 add 0
+  if (q == 0) s_base[d] = base;
   __syncthreads();
-  uint32_t run = (warp > 0 ? s_warp[warp - 1] : 0u) + x - local;
-  for (int i = 0; i < kPer; ++i)
-    if (beg + i < kN) {
-      const uint32_t c = hist[beg + i];
-      hist[beg + i] = run;
-      run += c;
-    }
+  uint32_t run = s_base[d];
+  for (int k = 0; k < q; ++k) run += s_part[k][d];
+#pragma unroll 8
+  for (int b = b0; b < b1; ++b) {
+    const uint32_t c = hist[b * 256 + d];
+    hist[b * 256 + d] = run;
+    run += c;
+  }
 }
 
-// Stable scatter of one digit.  Each CTA walks its chunk in tiles of kSortTile keys; inside
-// a tile, warp w owns keys [w*256, w*256+256) in 8 rounds of 32, ranks them with match_any,
-// the tile is reordered by digit in shared memory and written out in digit runs.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
-    const uint32_t* __restrict__ in_tile, const uint32_t* __restrict__ in_depth, const uint32_t* __restrict__ in_val,
-    uint32_t* __restrict__ out_tile, uint32_t* __restrict__ out_depth, uint32_t* __restrict__ out_val, int digit_word,
-    int shift, DevStatus* __restrict__ st, const uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s_tile[kSortTile], s_depth[kSortTile], s_val[kSortTile];
+// Stable scatter of one digit.  Each CTA walks its chunk in tiles of kSortTile items; in a
+// tile, warp w owns items [w*256, w*256+256) in 8 rounds of 32, ranks them with
+// match_any, the tile is reordered by digit in shared memory and written out in digit runs.
+template <int WORDS>
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(SortArrays<WORDS> arr, int digit_word, int shift,
+                                                                DevStatus* __restrict__ st, int64_t fixed_count,
+                                                                const uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_w[WORDS][kSortTile];
   __shared__ uint32_t s_wcnt[kWarps][256];
   __shared__ uint32_t s_bofs[256], s_tofs[256], s_tcnt[256];
   __shared__ uint32_t s_warp[kWarps];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const int64_t total = pairs_of(st);
+  const int64_t total = items_of(st, fixed_count);
   const int64_t chunk = chunk_of(total);
   const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
   if (beg >= end) return;
-  s_bofs[tid] = hist[tid * kSortBlocks + blockIdx.x];
+  s_bofs[tid] = hist[blockIdx.x * 256 + tid];
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) s_wcnt[w][tid] = 0;
   __syncthreads();
 
   for (int64_t base = beg; base < end; base += kSortTile) {
-    uint32_t kt[kSortItems], kd[kSortItems], kv[kSortItems], dig[kSortItems], rank[kSortItems];
+    uint32_t item[kSortItems][WORDS], dig[kSortItems], rank[kSortItems];
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
       const int64_t i = base + warp * (32 * kSortItems) + k * 32 + lane;
       const bool valid = i < end;
-      kt[k] = valid ? in_tile[i] : 0u;
-      kd[k] = valid ? in_depth[i] : 0u;
-      kv[k] = valid ? in_val[i] : 0u;
-      dig[k] = valid ? (((digit_word ? kt[k] : kd[k]) >> shift) & 255u) : 256u;
+      uint32_t dw = 0;
+#pragma unroll
+      for (int w = 0; w < WORDS; ++w) {
+        item[k][w] = valid ? arr.in[w][i] : 0u;
+        if (w == digit_word) dw = item[k][w];
+      }
+      dig[k] = valid ? ((dw >> shift) & 255u) : 256u;
       const uint32_t peers = __match_any_sync(0xffffffffu, dig[k]);
       rank[k] = valid ? s_wcnt[warp][dig[k]] + __popc(peers & lt_mask) : 0u;
       __syncwarp();
@@ -238,31 +262,27 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     }
     s_tcnt[tid] = run;
     uint32_t tile_total;
-    const uint32_t tofs = block_exclusive_scan(run, s_warp, tile_total);
-    s_tofs[tid] = tofs;
+    s_tofs[tid] = block_exclusive_scan<kSortThreads>(run, s_warp, tile_total);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
       if (dig[k] < 256u) {
         const uint32_t loc = s_tofs[dig[k]] + s_wcnt[warp][dig[k]] + rank[k];
-        s_tile[loc] = kt[k];
-        s_depth[loc] = kd[k];
-        s_val[loc] = kv[k];
+#pragma unroll
+        for (int w = 0; w < WORDS; ++w) s_w[w][loc] = item[k][w];
       }
     }
     __syncthreads();
     const int n_tile = (int)min((int64_t)kSortTile, end - base);
     for (int i = tid; i < n_tile; i += kSortThreads) {
-      const uint32_t t = s_tile[i], dd = s_depth[i];
-      const uint32_t d = ((digit_word ? t : dd) >> shift) & 255u;
+      const uint32_t d = (s_w[digit_word][i] >> shift) & 255u;
       const uint32_t pos = s_bofs[d] + (uint32_t)i - s_tofs[d];
       if ((int64_t)pos >= total) {  // cannot happen when the histograms are right
         st->code = XG_ERR_CHECK;
         continue;
       }
-      out_tile[pos] = t;
-      out_depth[pos] = dd;
-      out_val[pos] = s_val[i];
+#pragma unroll
+      for (int w = 0; w < WORDS; ++w) arr.out[w][pos] = s_w[w][i];
     }
     __syncthreads();
     s_bofs[tid] += s_tcnt[tid];
@@ -272,12 +292,15 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   }
 }
 
+template __global__ void k_radix_scatter<2>(SortArrays<2>, int, int, DevStatus*, int64_t, const uint32_t*);
+template __global__ void k_radix_scatter<3>(SortArrays<3>, int, int, DevStatus*, int64_t, const uint32_t*);
+
 // ------------------------------------------------------------------------------------------
 // tile ranges in the sorted pairs
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key_tile, int64_t n_keys,
                                                 DevStatus* __restrict__ st, uint2* __restrict__ range) {
-  const int64_t total = pairs_of(st);
+  const int64_t total = items_of(st, -1);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t t = key_tile[i];
     if ((int64_t)t >= n_keys) {  // cannot happen when emit and sort are right
@@ -289,12 +312,49 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+template <int WORDS>
+void radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, int64_t fixed_count,
+                DevStatus* status, uint32_t* hist, cudaStream_t st) {
+  {
+    Timed t(f, kRadixHist, st);
+    k_radix_hist<<<kSortBlocks, kSortThreads, 0, st>>>(arr.in[digit_word], shift, status, fixed_count, hist);
+  }
+  {
+    Timed t(f, kRadixScan, st);
+    k_radix_scan<<<1, 1024, 0, st>>>(hist);
+  }
+  {
+    Timed t(f, kRadixScatter, st);
+    k_radix_scatter<WORDS><<<kSortBlocks, kSortThreads, 0, st>>>(arr, digit_word, shift, status, fixed_count, hist);
+  }
+}
+
+template void radix_pass<2>(xg_frame*, const SortArrays<2>&, int, int, int64_t, DevStatus*, uint32_t*, cudaStream_t);
+template void radix_pass<3>(xg_frame*, const SortArrays<3>&, int, int, int64_t, DevStatus*, uint32_t*, cudaStream_t);
+
 cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   const FramePtrs& p = f->p;
   const int64_t VN = (int64_t)f->n_views * f->n;
+  // stage 1: (view, depth) order of the V*n entries; words: view, depth bits, Gaussian
+  int cur = 0;
+  for (int pass = 0; pass < f->entry_passes; ++pass) {
+    const int digit_word = pass < 4 ? 1 : 0;
+    const int shift = pass < 4 ? 8 * pass : 8 * (pass - 4);
+    SortArrays<3> arr;
+    arr.in[0] = p.ent_view[cur], arr.in[1] = p.ent_depth[cur], arr.in[2] = p.ent_gid[cur];
+    arr.out[0] = p.ent_view[cur ^ 1], arr.out[1] = p.ent_depth[cur ^ 1], arr.out[2] = p.ent_gid[cur ^ 1];
+    radix_pass<3>(f, arr, digit_word, shift, VN, p.status, p.hist, st);
+    cur ^= 1;
+  }
+  const uint32_t* ent_view = p.ent_view[cur];
+  const uint32_t* ent_gid = p.ent_gid[cur];
+  // stage 2: offsets of each entry's pairs in that order, then the pairs
   {
     Timed t(f, kScanReduce, st);
-    k_scan_reduce<<<kSortBlocks, kSortThreads, 0, st>>>(p.count, VN, p.scan_part);
+    k_scan_reduce<<<kSortBlocks, kSortThreads, 0, st>>>(p.count, ent_view, ent_gid, f->n, VN, p.scan_part);
   }
   {
     Timed t(f, kScanTop, st);
@@ -302,36 +362,24 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   }
   {
     Timed t(f, kScanDown, st);
-    k_scan_down<<<kSortBlocks, kSortThreads, 0, st>>>(p.count, VN, p.scan_part, p.offset);
+    k_scan_down<<<kSortBlocks, kSortThreads, 0, st>>>(p.count, ent_view, ent_gid, f->n, VN, p.scan_part, p.offset);
   }
   {
     Timed t(f, kEmit, st);
-    k_emit<<<(unsigned)((VN + 255) / 256), 256, 0, st>>>(p.count, p.offset, p.rect, p.depth, f->n, f->n_views,
+    k_emit<<<(unsigned)((VN + 255) / 256), 256, 0, st>>>(p.count, p.offset, p.rect, ent_view, ent_gid, f->n, VN,
                                                          f->tiles_x, f->tiles_per_view, f->cfg.pair_capacity,
-                                                         p.status, p.key_tile[0], p.key_depth[0], p.value[0]);
+                                                         p.status, p.key_tile[0], p.value[0]);
   }
-  int cur = 0;
-  for (int pass = 0; pass < f->sort_passes; ++pass) {
-    const int digit_word = pass < 4 ? 0 : 1;
-    const int shift = pass < 4 ? 8 * pass : 8 * (pass - 4);
-    const uint32_t* word = digit_word ? p.key_tile[cur] : p.key_depth[cur];
-    {
-      Timed t(f, kRadixHist, st);
-      k_radix_hist<<<kSortBlocks, kSortThreads, 0, st>>>(word, shift, p.status, p.hist);
-    }
-    {
-      Timed t(f, kRadixScan, st);
-      k_radix_scan<<<1, 1024, 0, st>>>(p.hist);
-    }
-    {
-      Timed t(f, kRadixScatter, st);
-      k_radix_scatter<<<kSortBlocks, kSortThreads, 0, st>>>(p.key_tile[cur], p.key_depth[cur], p.value[cur],
-                                                            p.key_tile[cur ^ 1], p.key_depth[cur ^ 1],
-                                                            p.value[cur ^ 1], digit_word, shift, p.status, p.hist);
-    }
-    cur ^= 1;
+  // stage 3: stable sort of the pairs by tile key
+  int pc = 0;
+  for (int pass = 0; pass < f->tile_passes; ++pass) {
+    SortArrays<2> arr;
+    arr.in[0] = p.key_tile[pc], arr.in[1] = p.value[pc];
+    arr.out[0] = p.key_tile[pc ^ 1], arr.out[1] = p.value[pc ^ 1];
+    radix_pass<2>(f, arr, 0, 8 * pass, -1, p.status, p.hist, st);
+    pc ^= 1;
   }
-  f->sorted_buf = cur;
+  // stage 4: ranges
   cudaError_t e;
   {
     Timed t(f, kMemset, st);
@@ -340,7 +388,7 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   {
     Timed t(f, kRanges, st);
-    k_ranges<<<kSortBlocks * 4, 256, 0, st>>>(p.key_tile[cur], (int64_t)f->n_views * f->tiles_per_view, p.status,
+    k_ranges<<<kSortBlocks * 4, 256, 0, st>>>(p.key_tile[pc], (int64_t)f->n_views * f->tiles_per_view, p.status,
                                                p.range);
   }
   return cudaGetLastError();

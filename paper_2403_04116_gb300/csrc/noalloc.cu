@@ -85,10 +85,13 @@ extern "C" xg_status xg_sort_pairs_noalloc(const uint32_t* key_tile, const uint3
                         to_out ? out_value : tmp_val};
     const int digit_word = pass < 4 ? 0 : 1;
     const int shift = pass < 4 ? 8 * pass : 8 * (pass - 4);
-    k_radix_hist<<<kSortBlocks, kSortThreads, 0, st>>>(digit_word ? src[0] : src[1], shift, status, hist);
-    k_radix_scan<<<1, 1024, 0, st>>>(hist);
-    k_radix_scatter<<<kSortBlocks, kSortThreads, 0, st>>>(src[0], src[1], src[2], dst[0], dst[1], dst[2], digit_word,
-                                                          shift, status, hist);
+    // words: 0 tile key, 1 depth key, 2 value
+    SortArrays<3> arr;
+    for (int w = 0; w < 3; ++w) {
+      arr.in[w] = src[w];
+      arr.out[w] = dst[w];
+    }
+    radix_pass<3>(nullptr, arr, digit_word ? 0 : 1, shift, count, status, hist, st);
     src[0] = dst[0];
     src[1] = dst[1];
     src[2] = dst[2];

@@ -18,7 +18,8 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ mean,
                                                  const Camera* __restrict__ cams, int W, int H, int tw, int th,
                                                  float near_mm, float4* __restrict__ rec, float* __restrict__ depth,
                                                  ushort4* __restrict__ rect, uint32_t* __restrict__ count,
-                                                 DevStatus* __restrict__ status) {
+                                                 uint32_t* __restrict__ ent_view, uint32_t* __restrict__ ent_depth,
+                                                 uint32_t* __restrict__ ent_gid, DevStatus* __restrict__ status) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
   const int v = blockIdx.y;
@@ -136,6 +137,10 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ mean,
   depth[vg] = dz;
   rect[vg] = rc;
   count[vg] = cnt;
+  // keys of the (view, depth) sort of the entries
+  ent_view[vg] = (uint32_t)v;
+  ent_depth[vg] = __float_as_uint(dz);
+  ent_gid[vg] = (uint32_t)g;
 }
 
 cudaError_t launch_project(xg_frame* f, const xg_gaussians* g, cudaStream_t st) {
@@ -144,7 +149,8 @@ cudaError_t launch_project(xg_frame* f, const xg_gaussians* g, cudaStream_t st) 
   Timed t(f, kProject, st);
   k_project<<<grid, 256, 0, st>>>(g->mean, g->scale, g->quat, g->opacity, g->intensity, n, f->p.cam, f->width,
                                   f->height, f->cfg.tile_w, f->cfg.tile_h, f->cfg.near_mm, f->p.rec, f->p.depth,
-                                  f->p.rect, f->p.count, f->p.status);
+                                  f->p.rect, f->p.count, f->p.ent_view[0], f->p.ent_depth[0], f->p.ent_gid[0],
+                                  f->p.status);
   return cudaGetLastError();
 }
 
@@ -194,13 +200,13 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ m
       for (int k = 0; k < 3; ++k) S[r][k] = M[r][0] * M[k][0] + M[r][1] * M[k][1] + M[r][2] * M[k][2];
     float gS[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 
-    const int64_t VN = (int64_t)n_views * n;
     for (int v = 0; v < n_views; ++v) {
       const int64_t vg = (int64_t)v * n + g;
-      const float gux = g2d[vg], guy = g2d[VN + vg];
-      const float ga = g2d[2 * VN + vg], gb = g2d[3 * VN + vg], gc = g2d[4 * VN + vg];
-      go += g2d[5 * VN + vg];
-      gi += g2d[6 * VN + vg];
+      const float4 q0 = reinterpret_cast<const float4*>(g2d)[2 * vg];
+      const float4 q1 = reinterpret_cast<const float4*>(g2d)[2 * vg + 1];
+      const float gux = q0.x, guy = q0.y, ga = q0.z, gb = q0.w, gc = q1.x;
+      go += q1.y;
+      gi += q1.z;
       if (gux == 0.f && guy == 0.f && ga == 0.f && gb == 0.f && gc == 0.f) continue;
       const Camera cam = cams[v];
       const float c = cam.c, s = cam.s, fu = cam.fu, fv = cam.fv;

@@ -1,13 +1,22 @@
 // Front-to-back alpha compositing of intensity per detector pixel (Eq. 10) and its
 // backward pass.
 //
-// One CTA per (tile, view), one thread per pixel.  The tile's depth-sorted list is staged
-// through shared memory in batches (the record of each Gaussian read once per CTA and
-// broadcast to all its pixels); a CTA stops fetching as soon as every pixel's transmittance
-// has hit the floor (__syncthreads_count).  The backward pass walks each pixel's list back
-// to front from its last contributor, recovering the transmittance by division instead of
-// storing it, reduces the per-Gaussian gradients across the warp with shuffles, then across
-// the CTA in shared memory, and issues one global atomic per (Gaussian, tile, quantity).
+// One CTA per (tile, view), one thread per pixel, each warp an 8x4 block of pixels.  The
+// tile's depth-sorted list is staged through shared memory in batches (the record of each
+// Gaussian read once per CTA and broadcast to all its pixels); a CTA stops fetching as soon
+// as every pixel's transmittance has hit the floor (__syncthreads_count).
+//
+// Most (pixel, list entry) pairs lie outside the Gaussian's footprint.  Each staged record
+// carries a conservative exponent threshold ln(1/(255 o)) - 1e-4: below it the opacity
+// provably stays under 1/255 (the FP32 exp used for the decision is accurate to 3e-7), so
+// the pair is skipped without evaluating exp.  Every other pair goes through the fixed
+// FP32 decision sequence, so decisions are exactly those of the full test.
+//
+// The backward pass walks each pixel's list back to front from its last contributor,
+// recovering the transmittance by division instead of storing it.  Per list entry, a warp
+// with any contributing pixel reduces its 7 gradient terms with an 8-value reduce-scatter
+// butterfly (9 shuffles; lane 4k ends with the sum of term k), adds them to shared memory,
+// and after the batch each Gaussian gets two float4 atomics in global memory.
 #include "xg_internal.cuh"
 
 namespace xg {
@@ -21,9 +30,10 @@ __device__ __forceinline__ void stage_batch(const uint32_t* __restrict__ value, 
     const uint32_t g = value[first + j];
     const float4 a = rec[2 * (vn_base + g)];
     const float4 b = rec[2 * (vn_base + g) + 1];
-    // (u_x, u_y, -a/2, -b) and (-c/2, opacity, intensity): exact rescalings of the conic
+    // (u_x, u_y, -a/2, -b) and (-c/2, opacity, intensity): exact rescalings of the conic;
+    // w: exponent below which the opacity cannot reach 1/255
     s_a[j] = make_float4(a.x, a.y, -0.5f * a.z, -a.w);
-    s_b[j] = make_float4(-0.5f * b.x, b.y, b.z, 0.f);
+    s_b[j] = make_float4(-0.5f * b.x, b.y, b.z, logf(kAlphaMin / b.y) - 1e-4f);
     if (s_g) s_g[j] = g;
   }
 }
@@ -40,6 +50,34 @@ __device__ __forceinline__ void add_counts(uint32_t ev, uint32_t nc, unsigned lo
     if (ev) atomicAdd(ev_out, (unsigned long long)ev);
     if (nc) atomicAdd(nc_out, (unsigned long long)nc);
   }
+}
+
+// Pixel of thread `tid` inside a tw-wide tile: warps own 8x4 blocks, row-major.
+__device__ __forceinline__ void pixel_in_tile(int tid, int tw, int& lx, int& ly) {
+  const int lane = tid & 31, warp = tid >> 5, wx = tw >> 3;
+  lx = (warp % wx) * 8 + (lane & 7);
+  ly = (warp / wx) * 4 + (lane >> 3);
+}
+
+// Sum of v[k] over the warp for k = 0..7, scattered: returns the total of term
+// ((lane >> 2) & 7) in every lane.  9 shuffles instead of 8 x 5.
+__device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int lane) {
+  float a[4], c[2];
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float send = b4 ? v[k] : v[k + 4];
+    a[k] = (b4 ? v[k + 4] : v[k]) + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = b3 ? a[k] : a[k + 2];
+    c[k] = (b3 ? a[k + 2] : a[k]) + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float d = (b2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b2 ? c[0] : c[1], 4);
+  d += __shfl_xor_sync(0xffffffffu, d, 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  return d;
 }
 
 // The exponent -1/2 d^T K d and sigma = min(0.99, o e^p) in the fixed FP32 sequence.
@@ -61,8 +99,10 @@ __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ ra
   __shared__ float4 s_a[kBatch], s_b[kBatch];
   const int tile = blockIdx.x, v = blockIdx.y;
   const int th_ = blockDim.x / tw;
-  const int x = (tile % tiles_x) * tw + (int)threadIdx.x % tw;
-  const int y = (tile / tiles_x) * th_ + (int)threadIdx.x / tw;
+  int lx, ly;
+  pixel_in_tile(threadIdx.x, tw, lx, ly);
+  const int x = (tile % tiles_x) * tw + lx;
+  const int y = (tile / tiles_x) * th_ + ly;
   const bool inside = x < W && y < H;
   const Camera cam = cams[v];
   const float px = fsub((float)x, cam.hw), py = fsub((float)y, cam.hh);
@@ -84,8 +124,9 @@ __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ ra
         const float4 b = s_b[j];
         float dx, dy;
         const float p = power_of(a, b.x, px, py, dx, dy);
-        const float al = fminf(kAlphaMax, fmul(b.y, xg_exp(p)));
         ++nev;
+        if (p < b.w) continue;  // opacity provably below 1/255
+        const float al = fminf(kAlphaMax, fmul(b.y, xg_exp(p)));
         if (al < kAlphaMin) continue;
         const float Tn = fmul(T, fsub(1.0f, al));
         if (Tn < kTMin) {
@@ -131,19 +172,20 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
                                                     float* __restrict__ g2d) {
   __shared__ float4 s_a[kBatch], s_b[kBatch];
   __shared__ uint32_t s_g[kBatch];
-  __shared__ float s_acc[kBatch * 8];
+  __shared__ __align__(16) float s_acc[kBatch * 8];
   __shared__ uint32_t s_maxlast;
   if (st->code != XG_OK) return;
   const int tile = blockIdx.x, v = blockIdx.y;
   const int th_ = blockDim.x / tw;
-  const int x = (tile % tiles_x) * tw + (int)threadIdx.x % tw;
-  const int y = (tile / tiles_x) * th_ + (int)threadIdx.x / tw;
+  int lx, ly;
+  pixel_in_tile(threadIdx.x, tw, lx, ly);
+  const int x = (tile % tiles_x) * tw + lx;
+  const int y = (tile / tiles_x) * th_ + ly;
   const bool inside = x < W && y < H;
   const Camera cam = cams[v];
   const float px = fsub((float)x, cam.hw), py = fsub((float)y, cam.hh);
   const uint2 r = range[(int64_t)v * tiles_per_view + tile];
   const int64_t vn_base = (int64_t)v * n;
-  const int64_t VN = (int64_t)n_views * n;
   const int lane = threadIdx.x & 31;
 
   float G = 0.f, Tc = 1.f;
@@ -169,7 +211,7 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
     for (int i = threadIdx.x; i < cnt * 8; i += blockDim.x) s_acc[i] = 0.f;
     __syncthreads();
     for (int j = cnt - 1; j >= 0; --j) {
-      float gv[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool contrib = false;
       if ((uint32_t)(base + j) < L) {
         ++nev;
@@ -177,47 +219,45 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
         const float4 b = s_b[j];
         float dx, dy;
         const float p = power_of(a, b.x, px, py, dx, dy);
-        const float e = xg_exp(p);
-        const float oe = fmul(b.y, e);
-        const float al = fminf(kAlphaMax, oe);
-        if (al >= kAlphaMin) {
-          contrib = true;
-          ++ncon;
-          Tc = __fdividef(Tc, 1.f - al);
-          const float in = b.z;
-          gv[6] = G * al * Tc;                 // dL/d intensity
-          const float dL_dal = G * Tc * (in - A);
-          A = al * in + (1.f - al) * A;
-          if (oe < kAlphaMax) {
-            gv[5] = dL_dal * e;                // dL/d opacity
-            const float dp = dL_dal * al;      // dL/d power
-            gv[0] = dp * (2.f * a.z * dx + a.w * dy);  // dL/du_x = dp * -(a dx + b dy)
-            gv[1] = dp * (2.f * b.x * dy + a.w * dx);  // dL/du_y = dp * -(b dx + c dy)
-            gv[2] = dp * (-0.5f * dx * dx);            // dL/d conic a
-            gv[3] = dp * (-dx * dy);                   // dL/d conic b
-            gv[4] = dp * (-0.5f * dy * dy);            // dL/d conic c
+        if (p >= b.w) {
+          const float e = xg_exp(p);
+          const float oe = fmul(b.y, e);
+          const float al = fminf(kAlphaMax, oe);
+          if (al >= kAlphaMin) {
+            contrib = true;
+            ++ncon;
+            Tc = __fdividef(Tc, 1.f - al);
+            const float in = b.z;
+            gv[6] = G * al * Tc;                 // dL/d intensity
+            const float dL_dal = G * Tc * (in - A);
+            A = al * in + (1.f - al) * A;
+            if (oe < kAlphaMax) {
+              gv[5] = dL_dal * e;                // dL/d opacity
+              const float dp = dL_dal * al;      // dL/d power
+              gv[0] = dp * (2.f * a.z * dx + a.w * dy);  // dL/du_x = dp * -(a dx + b dy)
+              gv[1] = dp * (2.f * b.x * dy + a.w * dx);  // dL/du_y = dp * -(b dx + c dy)
+              gv[2] = dp * (-0.5f * dx * dx);            // dL/d conic a
+              gv[3] = dp * (-dx * dy);                   // dL/d conic b
+              gv[4] = dp * (-0.5f * dy * dy);            // dL/d conic c
+            }
           }
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int k = 0; k < 7; ++k) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) gv[k] += __shfl_xor_sync(0xffffffffu, gv[k], o);
-        }
-        if (lane == 0) {
-#pragma unroll
-          for (int k = 0; k < 7; ++k) atomicAdd(&s_acc[j * 8 + k], gv[k]);
-        }
+        const float sum = warp_reduce_scatter8(gv, lane);
+        const int k = (lane >> 2) & 7;
+        if ((lane & 3) == 0 && k < 7) atomicAdd(&s_acc[j * 8 + k], sum);
       }
     }
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-      const int64_t vg = vn_base + s_g[j];
-#pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        const float val = s_acc[j * 8 + k];
-        if (val != 0.f) atomicAdd(&g2d[k * VN + vg], val);
+      const float4 a0 = *reinterpret_cast<const float4*>(&s_acc[j * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&s_acc[j * 8 + 4]);
+      if (a0.x != 0.f || a0.y != 0.f || a0.z != 0.f || a0.w != 0.f || a1.x != 0.f || a1.y != 0.f ||
+          a1.z != 0.f) {
+        float4* dst = reinterpret_cast<float4*>(g2d + 8 * (vn_base + s_g[j]));
+        atomicAdd(dst, a0);
+        atomicAdd(dst + 1, a1);
       }
     }
     __syncthreads();
@@ -231,7 +271,7 @@ cudaError_t launch_render_bwd(xg_frame* f, const float* grad_image, cudaStream_t
   cudaError_t e;
   {
     Timed t(f, kMemset, st);
-    e = cudaMemsetAsync(p.grad2d, 0, sizeof(float) * 7 * (size_t)VN, st);
+    e = cudaMemsetAsync(p.grad2d, 0, sizeof(float) * 8 * (size_t)VN, st);
   }
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)f->tiles_per_view, (unsigned)f->n_views);

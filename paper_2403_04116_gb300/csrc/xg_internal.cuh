@@ -112,16 +112,25 @@ struct FramePtrs {
   float* depth;       // [V*n]
   ushort4* rect;      // [V*n]
   uint32_t* count;    // [V*n]
-  uint32_t* offset;   // [V*n]
+  uint32_t* offset;   // [V*n], in (view, depth) order of the entries
   unsigned long long* scan_part;  // [kSortBlocks + 1]
-  uint32_t* key_tile[2];
-  uint32_t* key_depth[2];
+  uint32_t* ent_view[2];   // stage-1 sort of the V*n entries (ping-pong)
+  uint32_t* ent_depth[2];
+  uint32_t* ent_gid[2];
+  uint32_t* key_tile[2];   // pairs (ping-pong)
   uint32_t* value[2];
-  uint32_t* hist;     // [256][kSortBlocks]
+  uint32_t* hist;     // [kSortBlocks][256]
   uint2* range;       // [V*T]
   float* tfinal;      // [V*H*W]
   uint32_t* last;     // [V*H*W]
-  float* grad2d;      // [7][V*n]
+  float* grad2d;      // [V*n][8]
+};
+
+// Input and output arrays of one radix pass, passed by value.
+template <int WORDS>
+struct SortArrays {
+  const uint32_t* in[WORDS];
+  uint32_t* out[WORDS];
 };
 
 }  // namespace xg
@@ -144,9 +153,10 @@ struct xg_frame {
   int32_t n_views, width, height;
   int32_t tiles_x, tiles_y;
   int64_t tiles_per_view;
-  int32_t tile_bits;   // bits of view * T + tile
-  int32_t sort_passes;
-  int32_t sorted_buf;  // which ping-pong buffer holds the sorted pairs
+  int32_t tile_bits;     // bits of view * T + tile
+  int32_t entry_passes;  // stage-1 passes: 4 depth bytes + view bytes
+  int32_t tile_passes;   // stage-3 passes over the pairs
+  int32_t sorted_buf;    // which ping-pong buffer holds the sorted pairs
   void* workspace;
   size_t workspace_bytes;
   xg_layout layout;
@@ -166,7 +176,7 @@ struct Timed {
   xg_frame* f;
   cudaStream_t st;
   int slot;
-  Timed(xg_frame* frame, int kid, cudaStream_t stream);
+  Timed(xg_frame* frame, int kid, cudaStream_t stream);  // frame may be NULL (not timed)
   ~Timed();
 };
 
@@ -179,13 +189,10 @@ cudaError_t launch_project_bwd(xg_frame* f, const xg_gaussians* g, const xg_grad
 cudaError_t launch_loss_l1(const float* image, const float* target, int64_t count, float scale, float* grad,
                            float* loss, cudaStream_t st);
 
-// radix-sort passes (binning.cu), also launched by the allocation-free pair sort
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ word, int shift,
-                                                             const DevStatus* __restrict__ st,
-                                                             uint32_t* __restrict__ hist);
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist);
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
-    const uint32_t* __restrict__ in_tile, const uint32_t* __restrict__ in_depth, const uint32_t* __restrict__ in_val,
-    uint32_t* __restrict__ out_tile, uint32_t* __restrict__ out_depth, uint32_t* __restrict__ out_val, int digit_word,
-    int shift, DevStatus* __restrict__ st, const uint32_t* __restrict__ hist);
+// One LSD radix pass (histogram, digit scan, stable scatter; binning.cu) over WORDS arrays,
+// the digit taken from arr.in[digit_word] >> shift.  The item count is `fixed_count` when it
+// is >= 0, else the pair count in the status word.  `f` may be NULL (no timing).
+template <int WORDS>
+void radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, int64_t fixed_count,
+                DevStatus* status, uint32_t* hist, cudaStream_t st);
 }  // namespace xg

@@ -120,9 +120,9 @@ class Frame:
         spec = {
             "records": (torch.float32, (VN, 8)), "depth": (torch.float32, (VN,)), "rect": (torch.int16, (VN, 4)),
             "count": (torch.int32, (VN,)), "offset": (torch.int32, (VN,)), "key_tile": (torch.int32, (cap,)),
-            "key_depth": (torch.int32, (cap,)), "value": (torch.int32, (cap,)),
+            "value": (torch.int32, (cap,)),
             "range": (torch.int32, (self.V * self.tiles_per_view, 2)), "tfinal": (torch.float32, (P,)),
-            "last": (torch.int32, (P,)), "grad2d": (torch.float32, (7, VN)),
+            "last": (torch.int32, (P,)), "grad2d": (torch.float32, (VN, 8)),
         }
         dtype, shape = spec[name]
         off = getattr(self.layout, name)

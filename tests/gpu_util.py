@@ -39,12 +39,14 @@ def run_forward(g: dict, views, tile=(16, 16), capacity=None, near_mm=0.2) -> di
     M = int(st.pairs) if st.code == B.XG_OK else 0
     out = {**proj, "status": st, "M": M, "frame": f, "dev": dev,
            "key_tile": f.array("key_tile")[:M].cpu().numpy().view(np.uint32),
-           "key_depth": f.array("key_depth")[:M].cpu().numpy().view(np.uint32),
            "value": f.array("value")[:M].cpu().numpy(),
            "range": f.array("range").cpu().numpy().view(np.uint32),
            "image": image.cpu().numpy(), "ncontrib": ncon.cpu().numpy(),
            "tfinal": f.array("tfinal").cpu().numpy().reshape(f.V, f.H, f.W),
            "last": f.array("last").cpu().numpy().reshape(f.V, f.H, f.W)}
+    # depth key of every sorted pair, looked up from its (view, Gaussian)
+    views_of = out["key_tile"].astype(np.int64) // f.tiles_per_view
+    out["key_depth"] = proj["depth"].view(np.uint32)[views_of * n + out["value"].astype(np.int64)]
     return out
 
 
@@ -55,5 +57,5 @@ def run_backward(fwd: dict, grad_image: np.ndarray) -> dict:
     f.render_bwd(dev, G, grads)
     torch.cuda.synchronize()
     out = {k: t.cpu().numpy() for k, t in zip(NAMES, grads)}
-    out["g2d"] = f.array("grad2d").cpu().numpy()
+    out["g2d"] = np.ascontiguousarray(f.array("grad2d").cpu().numpy()[:, :7].T)  # (7, V*n)
     return out

@@ -43,10 +43,12 @@ def _binned_frame(n, n_views, W, H, tile, cid):
 
 
 def _emitted_pairs(f: Frame, M: int):
-    """The pairs in the order xg_bin_sort emits them, rebuilt from the frame's arrays."""
+    """Every (tile, depth, Gaussian) pair of the frame in (view, Gaussian index) order, each
+    Gaussian's tiles row-major -- an unsorted input whose stable sort by (tile, depth) is
+    the frame's sorted pair list."""
     rect = f.array("rect").cpu().numpy().astype(np.int64)
     count = f.array("count").cpu().numpy().view(np.uint32)
-    offset = f.array("offset").cpu().numpy().view(np.uint32)
+    offset = np.concatenate([[0], np.cumsum(count.astype(np.int64))[:-1]])
     dbits = f.array("depth").cpu().numpy().view(np.uint32)
     kt, kd, val = (np.empty(M, np.uint32) for _ in range(3))
     for vg in np.nonzero(count)[0]:
@@ -81,7 +83,11 @@ def test_noalloc_sort_matches_bin_sort_twice(first, second):
         keys = f.V * f.tiles_per_view
         tile_bits = int(np.ceil(np.log2(keys))) if keys > 1 else 0
         got = _sort_noalloc(kt, kd, val, tile_bits)
-        want = [f.array(name)[:M].cpu().numpy().view(np.uint32) for name in ("key_tile", "key_depth", "value")]
+        kt_s = f.array("key_tile")[:M].cpu().numpy().view(np.uint32)
+        val_s = f.array("value")[:M].cpu().numpy().view(np.uint32)
+        dbits = f.array("depth").cpu().numpy().view(np.uint32)
+        kd_s = dbits[(kt_s.astype(np.int64) // f.tiles_per_view) * f.n + val_s]
+        want = [kt_s, kd_s, val_s]
         for g_, w_, name in zip(got, want, ("key_tile", "key_depth", "value")):
             np.testing.assert_array_equal(g_, w_, err_msg=name)
 
