@@ -54,12 +54,13 @@ TRAFFIC = {}
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="train50k")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     return ap.parse_args()
 
 
@@ -232,7 +233,8 @@ def run_ours(args) -> None:
 
     from paper_2403_04116_gb300 import binding as B
     from paper_2403_04116_gb300 import synth
-    from paper_2403_04116_gb300.render import Frame, FrameConfig, L1Loss, Renderer, loss_l1_into, render
+    from paper_2403_04116_gb300.batch import GraphedStep, PlainSteps, autotune, size_pairs
+    from paper_2403_04116_gb300.render import FrameConfig, L1Loss, Renderer, loss_l1_into, render
 
     B.lib(build_if_missing=True)
     w, g, views, ph = _workload(args.workload)
@@ -241,39 +243,31 @@ def run_ours(args) -> None:
     names = ("mean", "scale", "quat", "opacity", "intensity")
     dev = tuple(torch.from_numpy(g[k]).cuda() for k in names)
     target = torch.from_numpy(targets_np).cuda()
+    n = w["n"]
 
-    # size the pair capacity from one binning pass
-    probe = Frame(w["n"], views, FrameConfig(*w["tile"]), pair_capacity=1 << 20)
-    probe.project(*dev)
-    probe.bin_sort()
-    pairs = int(probe.status().pairs)
-    del probe
-    cap = int(pairs * 1.05) + 4096
-    frame = Frame(w["n"], views, FrameConfig(*w["tile"]), pair_capacity=cap)
+    # tile shape and staging batch: autotuned on the graphed step (cached per workload shape)
+    tuned = autotune(n, views, dev, target) if args.autotune else None
+    tile = (tuned.tile_w, tuned.tile_h) if tuned else tuple(w["tile"])
+    batch = tuned.batch if tuned else 256
+    cfg = FrameConfig(tile[0], tile[1], batch=batch)
+    cap = tuned.pair_capacity if tuned else size_pairs(n, views, cfg, dev)
 
-    image = torch.empty((V, H, W), dtype=torch.float32, device="cuda")
-    grad_image = torch.empty_like(image)
-    loss = torch.empty(1, dtype=torch.float32, device="cuda")
-    grads = tuple(torch.empty_like(t) for t in dev)
+    step = GraphedStep(n, views, cfg, cap)
+    step.load(dev, target)
+    step.capture()
+    frame = step.frame
+    fwd_graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(fwd_graph):
+        frame.project(*step.inputs)
+        frame.bin_sort()
+        frame.render_fwd(step.image)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def fwd_step():
-        frame.project(*dev)
-        frame.bin_sort()
-        frame.render_fwd(image)
-
-    def step():
-        fwd_step()
-        loss_l1_into(image, target, grad_image, loss)
-        frame.render_bwd(dev, grad_image, grads)
-
-    def timed(fn, k: int, per_kernel: bool) -> tuple[float, dict]:
+    def timed(fn, k: int) -> float:
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
         barrier()
         torch.cuda.synchronize()
-        frame.read_timing()
-        frame.set_timing(per_kernel)
         for i in range(k):
             flush.fill_(i & 0xFF)
             starts[i].record()
@@ -281,32 +275,50 @@ def run_ours(args) -> None:
             ends[i].record()
         torch.cuda.synchronize()
         barrier()
-        frame.set_timing(False)
-        kernels = frame.read_timing() if per_kernel else {}
-        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-        return ms, kernels
+        return sum(s.elapsed_time(e) for s, e in zip(starts, ends))
 
     for _ in range(args.warmup):
-        step()
+        step.replay()
     torch.cuda.synchronize()
     st = frame.status()
     if st.code != B.XG_OK:
         raise RuntimeError(f"frame status {B.xg_status_str(st.code)}")
 
     with ClockSampler(local) as clocks:
-        ms_total, kernels = timed(step, args.steps, per_kernel=True)
+        ms_total = timed(step.replay, args.steps)
+        ms_fwd = timed(fwd_graph.replay, args.steps)
     clock_info = clocks.summary()
+
+    # per-kernel times: the same step launched on the stream with event timing on
+    def stream_step():
+        frame.project(*step.inputs)
+        frame.bin_sort()
+        frame.render_fwd(step.image)
+        loss_l1_into(step.image, step.target, step.grad_image, step.loss)
+        frame.render_bwd(step.inputs, step.grad_image, step.grads)
+
+    frame.read_timing()
+    frame.set_timing(True)
+    ms_stream = timed(stream_step, args.steps)
+    frame.set_timing(False)
+    kernels = frame.read_timing()
     st = frame.status()
-    ms_fwd, _ = timed(fwd_step, args.steps, per_kernel=False)
+
+    # the plain form: one frame and one launch sequence per view, no graph
+    plain_steps = max(1, min(args.steps, 5))
+    plain = PlainSteps(n, views, cfg, size_pairs(n, views[:1], cfg, dev, margin=1.5))
+    pgrads = tuple(torch.empty_like(t) for t in dev)
+    plain.run(dev, target, pgrads)
+    ms_plain = timed(lambda: plain.run(dev, target, pgrads), plain_steps)
+    del plain
 
     # max over ranks
-    t = torch.tensor([ms_total, ms_fwd], dtype=torch.float64, device="cuda")
+    t = torch.tensor([ms_total, ms_fwd, ms_plain, ms_stream], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total, ms_fwd = t.tolist()
+    ms_total, ms_fwd, ms_plain, ms_stream = t.tolist()
     ms_step = ms_total / args.steps
     value = world * V * args.steps / (ms_total / 1000.0)
-    fwd_value = world * V * args.steps / (ms_fwd / 1000.0)
 
     # roofline of the dominant kernel
     peaks = _peaks()
@@ -323,15 +335,14 @@ def run_ours(args) -> None:
         ops = FWD_OPS_EVAL * st.fwd_evaluated + FWD_OPS_CONTRIB * st.fwd_contrib
         roof = {"bound": "alu", "achieved": ops / (avg_ms * 1e-3) / 1e12, "peak": alu_peak, "unit": "TFP32op/s"}
     else:
-        VN = V * w["n"]
+        VN = V * n
         M = int(st.pairs)
-        algo = {"k_radix_scatter": 24 * M, "k_radix_hist": 4 * M, "k_project": 48 * w["n"] + 48 * VN,
-                "k_emit": 16 * VN + 12 * M, "k_project_bwd": 28 * VN + 56 * w["n"]}.get(dom, 0)
+        algo = {"k_radix_scatter": 24 * VN * 5 + 16 * M * 2, "k_project": 48 * n + 72 * VN,
+                "k_emit": 20 * VN + 8 * M, "k_project_bwd": 32 * VN + 56 * n}.get(dom, 0) / max(1, launches // args.steps)
         roof = {"bound": "hbm", "achieved": algo / (avg_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     src = {"k_render_bwd": "render.cu", "k_render_fwd": "render.cu", "k_radix_scatter": "binning.cu",
-           "k_radix_hist": "binning.cu", "k_project": "project.cu", "k_emit": "binning.cu",
-           "k_project_bwd": "project.cu"}.get(dom)
+           "k_project": "project.cu", "k_emit": "binning.cu", "k_project_bwd": "project.cu"}.get(dom)
     tr = TRAFFIC.get(dom)
     roof["traffic"] = tr["bytes_per_launch"] if tr and src and tr["source_sha"] == _source_sha(src) else None
     roof["kernel"] = dom
@@ -339,14 +350,15 @@ def run_ours(args) -> None:
                            else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")
     roof["avg_launch_ms"] = avg_ms
 
-    gpu_launches = sum(n for k, (n, _) in kernels.items() if k != "memset") + args.steps  # + the loss kernel
+    launches_per_step = sum(nl for k, (nl, _) in kernels.items() if k != "memset") / args.steps + 1  # + loss kernel
+    gpu_launches = int(round(launches_per_step * args.steps))
 
     # end to end through the public API: pinned host inputs in, loss out, every step
     e2e = None
     if not args.no_e2e:
         host = tuple(torch.from_numpy(g[k]).pin_memory() for k in names)
         host_target = torch.from_numpy(targets_np).pin_memory()
-        renderer = Renderer(views, FrameConfig(*w["tile"]), pair_capacity=cap, check_capacity=False)
+        renderer = Renderer(views, cfg, pair_capacity=cap, check_capacity=False)
         h2d = sum(t.numel() * 4 for t in host) + host_target.numel() * 4
 
         def e2e_step():
@@ -370,18 +382,24 @@ def run_ours(args) -> None:
         if world > 1:
             dist.all_reduce(el, op=dist.ReduceOp.MAX)
         e2e = {"value": world * V * args.steps / el.item(), "unit": "projections/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": 4}
+               "d2h_bytes_per_step": 4, "path": "render() autograd + L1Loss, uncaptured stream launches"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_rate(args.workload)
 
     if rank == 0:
+        cfg_line = _config(args.workload, w, world)
+        cfg_line.update({"tile": list(tile), "staging_batch": batch, "graph": "whole step, one CUDA graph",
+                         "autotuned": bool(tuned)})
         line = {"metric": METRIC, "value": value, "unit": "projections/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": _config(args.workload, w, world),
-                "fwd": {"value": fwd_value, "unit": "projections/s", "ms_per_step": ms_fwd / args.steps},
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg_line,
+                "fwd": {"value": world * V * args.steps / (ms_fwd / 1000.0), "unit": "projections/s",
+                        "ms_per_step": ms_fwd / args.steps},
+                "plain_one_view_per_launch": {"value": world * V * plain_steps / (ms_plain / 1000.0),
+                                              "unit": "projections/s", "ms_per_step": ms_plain / plain_steps},
+                "stream_launched": {"ms_per_step": ms_stream / args.steps},
                 "clocks": clock_info, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
                 "cpu_baseline": cpu, "pairs": int(st.pairs),
                 "work": {"fwd_evaluated": int(st.fwd_evaluated), "fwd_contrib": int(st.fwd_contrib),

@@ -87,12 +87,14 @@ typedef struct {
 } xg_grads;
 
 /* Frame configuration.  tile_w, tile_h in {8, 16, 32} with tile_w * tile_h <= 512;
- * near_mm > 0; 1 <= pair_capacity < 2^31. */
+ * near_mm > 0; batch: Gaussians staged in shared memory per round of the compositing
+ * kernels, one of 64, 128, 256 (0 selects 256); 1 <= pair_capacity < 2^31.  The tile
+ * shape and batch change speed only: images and gradients do not depend on them. */
 typedef struct {
   int32_t tile_w;
   int32_t tile_h;
   float near_mm;
-  int32_t reserved; /* set to 0 */
+  int32_t batch;
   int64_t pair_capacity;
 } xg_config;
 

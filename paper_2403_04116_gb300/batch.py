@@ -1,0 +1,168 @@
+"""Batched training steps: every view of a scan in one launch per stage, replayed from a
+CUDA graph, plus the tile-shape / staging-batch autotuner.
+
+``GraphedStep`` captures project -> bin + sort -> composite -> L1 loss -> backward for all
+views of a frame once, then replays it; only tensor contents change between replays (the
+Gaussian parameters and the targets are copied into its input buffers).  ``PlainSteps``
+is the reference form: one frame per view and one launch sequence per view, no graph.
+Both run the same kernels, so their images and gradients agree (gradients up to the order
+of float atomics).
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+from dataclasses import asdict, dataclass
+
+import torch
+
+from . import binding as B
+from .render import Frame, FrameConfig, loss_l1_into
+
+_NAMES = ("mean", "scale", "quat", "opacity", "intensity")
+CANDIDATE_TILES = ((8, 8), (16, 16), (32, 16), (16, 8), (16, 32))
+CANDIDATE_BATCHES = (64, 128, 256)
+_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+
+def size_pairs(n: int, views, cfg: FrameConfig, gaussians: tuple, margin: float = 1.05) -> int:
+    """Pair count of one binning pass (synchronises), with a margin, for sizing frames."""
+    probe = Frame(n, views, cfg, pair_capacity=1 << 20)
+    probe.project(*gaussians)
+    probe.bin_sort()
+    st = probe.status()
+    if st.code not in (B.XG_OK, B.XG_ERR_CAPACITY):
+        raise B.XgError(st.code, "xg_bin_sort")
+    return int(st.pairs * margin) + 4096
+
+
+class GraphedStep:
+    """Forward + L1 loss + backward of all views, captured in one CUDA graph."""
+
+    def __init__(self, n: int, views, cfg: FrameConfig, pair_capacity: int, device="cuda"):
+        self.frame = Frame(n, views, cfg, pair_capacity, device)
+        V, H, W = self.frame.V, self.frame.H, self.frame.W
+        self.inputs = (torch.zeros(3, n, device=device), torch.ones(3, n, device=device),
+                       torch.zeros(4, n, device=device), torch.zeros(n, device=device), torch.zeros(n, device=device))
+        self.inputs[2][0] = 1.0
+        self.target = torch.zeros(V, H, W, device=device)
+        self.image = torch.empty(V, H, W, device=device)
+        self.grad_image = torch.empty_like(self.image)
+        self.loss = torch.empty(1, device=device)
+        self.grads = tuple(torch.empty_like(t) for t in self.inputs)
+        self.graph = None
+
+    def _run(self) -> None:
+        f = self.frame
+        f.project(*self.inputs)
+        f.bin_sort()
+        f.render_fwd(self.image)
+        loss_l1_into(self.image, self.target, self.grad_image, self.loss)
+        f.render_bwd(self.inputs, self.grad_image, self.grads)
+
+    def load(self, gaussians: tuple, target: torch.Tensor | None = None) -> None:
+        for dst, src in zip(self.inputs, gaussians):
+            dst.copy_(src, non_blocking=True)
+        if target is not None:
+            self.target.copy_(target, non_blocking=True)
+
+    def capture(self) -> None:
+        """Warm up on a side stream, then record the step (the frame must not overflow)."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self._run()
+        torch.cuda.current_stream().wait_stream(side)
+        st = self.frame.status()
+        if st.code != B.XG_OK:
+            raise B.XgError(st.code, "graph warm-up")
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._run()
+
+    def replay(self) -> None:
+        self.graph.replay()
+
+
+class PlainSteps:
+    """The same step as one frame and one launch sequence per view (no graph)."""
+
+    def __init__(self, n: int, views, cfg: FrameConfig, pair_capacity_per_view: int, device="cuda"):
+        self.frames = [Frame(n, [v], cfg, pair_capacity_per_view, device) for v in views]
+        H, W = self.frames[0].H, self.frames[0].W
+        self.images = [torch.empty(1, H, W, device=device) for _ in views]
+        self.grad_images = [torch.empty(1, H, W, device=device) for _ in views]
+        self.loss = torch.empty(1, device=device)
+        self.view_grads = [None] * len(views)
+
+    def run(self, gaussians: tuple, target: torch.Tensor, grads: tuple) -> None:
+        for g in grads:
+            g.zero_()
+        tmp = tuple(torch.empty_like(g) for g in grads)
+        for v, f in enumerate(self.frames):
+            f.project(*gaussians)
+            f.bin_sort()
+            f.render_fwd(self.images[v])
+            loss_l1_into(self.images[v], target[v:v + 1], self.grad_images[v], self.loss,
+                         scale=1.0 / target.numel())
+            f.render_bwd(gaussians, self.grad_images[v], tmp)
+            for g, t in zip(grads, tmp):
+                g.add_(t)
+
+
+@dataclass
+class TuneResult:
+    tile_w: int
+    tile_h: int
+    batch: int
+    ms: float
+    pair_capacity: int
+
+
+def _key(n: int, views) -> str:
+    bucket = 1 << max(0, (n - 1).bit_length())
+    v0 = views[0]
+    return f"n<={bucket}|V={len(views)}|{v0.width}x{v0.height}"
+
+
+def autotune(n: int, views, gaussians: tuple, target: torch.Tensor, tiles=CANDIDATE_TILES,
+             batches=CANDIDATE_BATCHES, reps: int = 5, use_cache: bool = True) -> TuneResult:
+    """Pick the tile shape and staging batch with the fastest graphed step (cached on disk).
+
+    Every candidate computes the same image (tiles and batch are pure acceleration), so the
+    choice never changes results."""
+    key = _key(n, views)
+    cache = {}
+    if use_cache and os.path.exists(_CACHE):
+        try:
+            cache = json.load(open(_CACHE))
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            return TuneResult(**cache[key])
+    best = None
+    for tw, th in tiles:
+        cap = size_pairs(n, views, FrameConfig(tw, th), gaussians)
+        for b in batches:
+            step = GraphedStep(n, views, FrameConfig(tw, th, batch=b), cap)
+            step.load(gaussians, target)
+            step.capture()
+            times = []
+            for _ in range(reps):
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record()
+                step.replay()
+                e.record()
+                torch.cuda.synchronize()
+                times.append(s.elapsed_time(e))
+            ms = statistics.median(times)
+            if best is None or ms < best.ms:
+                best = TuneResult(tw, th, b, ms, cap)
+            del step
+    cache[key] = asdict(best)
+    if use_cache:
+        os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
+        with open(_CACHE, "w") as fh:
+            json.dump(cache, fh, indent=1)
+    return best

@@ -15,8 +15,11 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 bool valid_tile(int t) { return t == 8 || t == 16 || t == 32; }
 
+bool valid_batch(int b) { return b == 0 || b == 64 || b == 128 || b == 256; }
+
 bool valid_config(const xg_config* cfg) {
   return cfg && valid_tile(cfg->tile_w) && valid_tile(cfg->tile_h) && cfg->tile_w * cfg->tile_h <= 512 &&
+         valid_batch(cfg->batch) &&
          isfinite(cfg->near_mm) && cfg->near_mm > 0.f && cfg->pair_capacity >= 1 &&
          cfg->pair_capacity < ((int64_t)1 << 31);
 }
@@ -137,6 +140,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   xg_frame* f = (xg_frame*)calloc(1, sizeof(xg_frame));
   if (!f) return XG_ERR_INVALID_ARG;
   f->cfg = *cfg;
+  if (f->cfg.batch == 0) f->cfg.batch = 256;
   f->n = n;
   f->n_views = n_views;
   f->width = W;

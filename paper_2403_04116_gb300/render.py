@@ -37,6 +37,7 @@ class FrameConfig:
     tile_w: int = 16
     tile_h: int = 16
     near_mm: float = NEAR_MM
+    batch: int = 256  # Gaussians staged per round of the compositing kernels
 
 
 class Frame:
@@ -55,7 +56,7 @@ class Frame:
         self.W, self.H = self.views[0].width, self.views[0].height
         self.pair_capacity = int(pair_capacity)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        self._c = B.XgConfig(self.cfg.tile_w, self.cfg.tile_h, self.cfg.near_mm, 0, self.pair_capacity)
+        self._c = B.XgConfig(self.cfg.tile_w, self.cfg.tile_h, self.cfg.near_mm, self.cfg.batch, self.pair_capacity)
         nbytes = B.xg_workspace_bytes(self._c, self.n, self.V, self.W, self.H)
         if nbytes == 0:
             raise ValueError("invalid frame configuration")
