@@ -61,6 +61,7 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the one-view-per-launch form")
     return ap.parse_args()
 
 
@@ -142,6 +143,22 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def reduce_max(values, device="cpu") -> list:
+    """Element-wise maximum of ``values`` over all ranks (identity without a process group):
+    every rank times its own replica of the workload, the slowest one sets the time."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def throughput(views_per_step: int, steps: int, world: int, total_ms: float) -> float:
+    """Projections per second of the whole job: every rank renders its own views."""
+    return world * views_per_step * steps / (total_ms / 1000.0)
 
 
 def _source_sha(kernel_file: str) -> str:
@@ -249,7 +266,8 @@ def run_ours(args) -> None:
     tuned = autotune(n, views, dev, target) if args.autotune else None
     tile = (tuned.tile_w, tuned.tile_h) if tuned else tuple(w["tile"])
     batch = tuned.batch if tuned else 256
-    cfg = FrameConfig(tile[0], tile[1], batch=batch)
+    ppt = tuned.pixels_per_thread if tuned else 2
+    cfg = FrameConfig(tile[0], tile[1], batch=batch, pixels_per_thread=ppt)
     cap = tuned.pair_capacity if tuned else size_pairs(n, views, cfg, dev)
 
     step = GraphedStep(n, views, cfg, cap)
@@ -297,28 +315,29 @@ def run_ours(args) -> None:
         loss_l1_into(step.image, step.target, step.grad_image, step.loss)
         frame.render_bwd(step.inputs, step.grad_image, step.grads)
 
+    timing_steps = max(1, min(args.steps, 40))  # the library times up to 2048 launches between reads
     frame.read_timing()
     frame.set_timing(True)
-    ms_stream = timed(stream_step, args.steps)
+    ms_stream = timed(stream_step, timing_steps)
     frame.set_timing(False)
     kernels = frame.read_timing()
     st = frame.status()
 
     # the plain form: one frame and one launch sequence per view, no graph
     plain_steps = max(1, min(args.steps, 5))
-    plain = PlainSteps(n, views, cfg, size_pairs(n, views[:1], cfg, dev, margin=1.5))
-    pgrads = tuple(torch.empty_like(t) for t in dev)
-    plain.run(dev, target, pgrads)
-    ms_plain = timed(lambda: plain.run(dev, target, pgrads), plain_steps)
-    del plain
+    ms_plain = float("nan")
+    if not args.no_plain:
+        plain = PlainSteps(n, views, cfg, size_pairs(n, views[:1], cfg, dev, margin=1.5))
+        pgrads = tuple(torch.empty_like(t) for t in dev)
+        plain.run(dev, target, pgrads)
+        ms_plain = timed(lambda: plain.run(dev, target, pgrads), plain_steps)
+        del plain
 
     # max over ranks
-    t = torch.tensor([ms_total, ms_fwd, ms_plain, ms_stream], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total, ms_fwd, ms_plain, ms_stream = t.tolist()
+    ms_total, ms_fwd, ms_plain, ms_stream_step = reduce_max([ms_total, ms_fwd, ms_plain, ms_stream / timing_steps],
+                                                            device="cuda")
     ms_step = ms_total / args.steps
-    value = world * V * args.steps / (ms_total / 1000.0)
+    value = throughput(V, args.steps, world, ms_total)
 
     # roofline of the dominant kernel
     peaks = _peaks()
@@ -338,7 +357,7 @@ def run_ours(args) -> None:
         VN = V * n
         M = int(st.pairs)
         algo = {"k_radix_scatter": 24 * VN * 5 + 16 * M * 2, "k_project": 48 * n + 72 * VN,
-                "k_emit": 20 * VN + 8 * M, "k_project_bwd": 32 * VN + 56 * n}.get(dom, 0) / max(1, launches // args.steps)
+                "k_emit": 20 * VN + 8 * M, "k_project_bwd": 32 * VN + 56 * n}.get(dom, 0) / max(1, launches // timing_steps)
         roof = {"bound": "hbm", "achieved": algo / (avg_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     src = {"k_render_bwd": "render.cu", "k_render_fwd": "render.cu", "k_radix_scatter": "binning.cu",
@@ -350,7 +369,7 @@ def run_ours(args) -> None:
                            else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")
     roof["avg_launch_ms"] = avg_ms
 
-    launches_per_step = sum(nl for k, (nl, _) in kernels.items() if k != "memset") / args.steps + 1  # + loss kernel
+    launches_per_step = sum(nl for k, (nl, _) in kernels.items() if k != "memset") / timing_steps + 1  # + loss kernel
     gpu_launches = int(round(launches_per_step * args.steps))
 
     # end to end through the public API: pinned host inputs in, loss out, every step
@@ -378,10 +397,9 @@ def run_ours(args) -> None:
             e2e_step()
         torch.cuda.synchronize()
         barrier()
-        el = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(el, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * V * args.steps / el.item(), "unit": "projections/s", "h2d_bytes_per_step": h2d,
+        (el,) = reduce_max([time.perf_counter() - t0], device="cuda")
+        e2e = {"value": throughput(V, args.steps, world, 1000.0 * el), "unit": "projections/s",
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 4, "path": "render() autograd + L1Loss, uncaptured stream launches"}
 
     cpu = None
@@ -390,21 +408,23 @@ def run_ours(args) -> None:
 
     if rank == 0:
         cfg_line = _config(args.workload, w, world)
-        cfg_line.update({"tile": list(tile), "staging_batch": batch, "graph": "whole step, one CUDA graph",
+        cfg_line.update({"tile": list(tile), "staging_batch": batch, "pixels_per_thread": ppt,
+                         "graph": "whole step, one CUDA graph",
                          "autotuned": bool(tuned)})
         line = {"metric": METRIC, "value": value, "unit": "projections/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg_line,
-                "fwd": {"value": world * V * args.steps / (ms_fwd / 1000.0), "unit": "projections/s",
+                "fwd": {"value": throughput(V, args.steps, world, ms_fwd), "unit": "projections/s",
                         "ms_per_step": ms_fwd / args.steps},
-                "plain_one_view_per_launch": {"value": world * V * plain_steps / (ms_plain / 1000.0),
-                                              "unit": "projections/s", "ms_per_step": ms_plain / plain_steps},
-                "stream_launched": {"ms_per_step": ms_stream / args.steps},
+                "plain_one_view_per_launch": None if args.no_plain else {
+                    "value": throughput(V, plain_steps, world, ms_plain), "unit": "projections/s",
+                    "ms_per_step": ms_plain / plain_steps},
+                "stream_launched": {"ms_per_step": ms_stream_step},
                 "clocks": clock_info, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
                 "cpu_baseline": cpu, "pairs": int(st.pairs),
                 "work": {"fwd_evaluated": int(st.fwd_evaluated), "fwd_contrib": int(st.fwd_contrib),
                          "bwd_evaluated": int(st.bwd_evaluated), "bwd_contrib": int(st.bwd_contrib)},
-                "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(kernels.items())}}
+                "kernels_ms_per_step": {k: round(v[1] / timing_steps, 4) for k, v in sorted(kernels.items())}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -86,16 +86,20 @@ typedef struct {
   float* intensity;
 } xg_grads;
 
-/* Frame configuration.  tile_w, tile_h in {8, 16, 32} with tile_w * tile_h <= 512;
- * near_mm > 0; batch: Gaussians staged in shared memory per round of the compositing
- * kernels, one of 64, 128, 256 (0 selects 256); 1 <= pair_capacity < 2^31.  The tile
- * shape and batch change speed only: images and gradients do not depend on them. */
+/* Frame configuration.  tile_w, tile_h in {8, 16, 32}; pixels_per_thread: pixels each
+ * compositing thread owns, 1, 2 or 4 (0 selects 2), with tile_h a multiple of
+ * 4 * pixels_per_thread and tile_w * tile_h <= 512 * pixels_per_thread; near_mm > 0;
+ * batch: Gaussians staged in shared memory per round of the compositing kernels, one of
+ * 64, 128, 256 (0 selects 256); 1 <= pair_capacity < 2^31.  Tile shape, batch and pixels
+ * per thread change speed only: images and gradients do not depend on them. */
 typedef struct {
   int32_t tile_w;
   int32_t tile_h;
   float near_mm;
   int32_t batch;
   int64_t pair_capacity;
+  int32_t pixels_per_thread;
+  int32_t reserved; /* set to 0 */
 } xg_config;
 
 /* Device-side status of a frame, read back by xg_frame_read_status. */
@@ -226,7 +230,7 @@ xg_status xg_frame_read_timing(xg_frame* frame, xg_kernel_time* out, int32_t cap
  * (0 <= tile_bits <= 32).  Given the pairs xg_bin_sort emits, the output equals its
  * sorted pairs.
  *
- * Scratch: a static device array of about 12.3 MB inside the library (ping-pong buffers
+ * Scratch: a static device array of about 12.6 MB inside the library (ping-pong buffers
  * for XG_NOALLOC_MAX_PAIRS pairs, digit histograms, the pair count), held by every GPU that
  * loads the library until the process exits.  The call allocates nothing and frees
  * nothing.  Its first call on a device looks up the array's device address (with that

@@ -116,8 +116,12 @@ class TuneResult:
     tile_w: int
     tile_h: int
     batch: int
+    pixels_per_thread: int
     ms: float
     pair_capacity: int
+
+    def config(self) -> FrameConfig:
+        return FrameConfig(self.tile_w, self.tile_h, batch=self.batch, pixels_per_thread=self.pixels_per_thread)
 
 
 def _key(n: int, views) -> str:
@@ -127,8 +131,9 @@ def _key(n: int, views) -> str:
 
 
 def autotune(n: int, views, gaussians: tuple, target: torch.Tensor, tiles=CANDIDATE_TILES,
-             batches=CANDIDATE_BATCHES, reps: int = 5, use_cache: bool = True) -> TuneResult:
-    """Pick the tile shape and staging batch with the fastest graphed step (cached on disk).
+             batches=CANDIDATE_BATCHES, ppts=(1, 2, 4), reps: int = 5, use_cache: bool = True) -> TuneResult:
+    """Pick the tile shape, staging batch and pixels per thread with the fastest graphed step
+    (cached on disk).
 
     Every candidate computes the same image (tiles and batch are pure acceleration), so the
     choice never changes results."""
@@ -140,12 +145,15 @@ def autotune(n: int, views, gaussians: tuple, target: torch.Tensor, tiles=CANDID
         except (OSError, ValueError):
             cache = {}
         if key in cache:
-            return TuneResult(**cache[key])
+            try:
+                return TuneResult(**cache[key])
+            except TypeError:
+                pass
     best = None
     for tw, th in tiles:
         cap = size_pairs(n, views, FrameConfig(tw, th), gaussians)
-        for b in batches:
-            step = GraphedStep(n, views, FrameConfig(tw, th, batch=b), cap)
+        for b, ppt in [(b, p) for b in batches for p in ppts if th % (4 * p) == 0]:
+            step = GraphedStep(n, views, FrameConfig(tw, th, batch=b, pixels_per_thread=ppt), cap)
             step.load(gaussians, target)
             step.capture()
             times = []
@@ -158,7 +166,7 @@ def autotune(n: int, views, gaussians: tuple, target: torch.Tensor, tiles=CANDID
                 times.append(s.elapsed_time(e))
             ms = statistics.median(times)
             if best is None or ms < best.ms:
-                best = TuneResult(tw, th, b, ms, cap)
+                best = TuneResult(tw, th, b, ppt, ms, cap)
             del step
     cache[key] = asdict(best)
     if use_cache:

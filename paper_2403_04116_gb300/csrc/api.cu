@@ -18,8 +18,10 @@ bool valid_tile(int t) { return t == 8 || t == 16 || t == 32; }
 bool valid_batch(int b) { return b == 0 || b == 64 || b == 128 || b == 256; }
 
 bool valid_config(const xg_config* cfg) {
-  return cfg && valid_tile(cfg->tile_w) && valid_tile(cfg->tile_h) && cfg->tile_w * cfg->tile_h <= 512 &&
-         valid_batch(cfg->batch) &&
+  if (!cfg) return false;
+  const int ppt = cfg->pixels_per_thread == 0 ? 2 : cfg->pixels_per_thread;
+  return (ppt == 1 || ppt == 2 || ppt == 4) && valid_tile(cfg->tile_w) && valid_tile(cfg->tile_h) &&
+         cfg->tile_h % (4 * ppt) == 0 && cfg->tile_w * cfg->tile_h <= 512 * ppt && valid_batch(cfg->batch) &&
          isfinite(cfg->near_mm) && cfg->near_mm > 0.f && cfg->pair_capacity >= 1 &&
          cfg->pair_capacity < ((int64_t)1 << 31);
 }
@@ -82,7 +84,7 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t W, int32_t
   for (int b = 0; b < 2; ++b) o->ent_gid[b] = take(4 * VN);
   for (int b = 0; b < 2; ++b) o->key_tile[b] = take(4 * cap);
   for (int b = 0; b < 2; ++b) o->value[b] = take(4 * cap);
-  o->hist = take(4 * 256 * (size_t)xg::kSortBlocks);
+  o->hist = take(4 * 256 * ((size_t)xg::kSortBlocks + 1));
   o->range = take(8 * (size_t)V * (size_t)s->tiles_per_view);
   o->tfinal = take(4 * pix);
   o->last = take(4 * pix);
@@ -141,6 +143,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   if (!f) return XG_ERR_INVALID_ARG;
   f->cfg = *cfg;
   if (f->cfg.batch == 0) f->cfg.batch = 256;
+  if (f->cfg.pixels_per_thread == 0) f->cfg.pixels_per_thread = 2;
   f->n = n;
   f->n_views = n_views;
   f->width = W;
@@ -261,7 +264,7 @@ xg_status xg_frame_set_timing(xg_frame* frame, int32_t enable) {
 
 xg_status xg_frame_read_timing(xg_frame* frame, xg_kernel_time* out, int32_t capacity, int32_t* count) {
   static const char* const names[xg::kNumKernels] = {
-      "k_project", "k_scan_reduce", "k_scan_top", "k_scan_down", "k_emit", "k_radix_hist", "k_radix_scan",
+      "k_project", "k_scan_reduce", "k_scan_top", "k_scan_down", "k_emit", "k_radix_hist", "k_radix_colscan",
       "k_radix_scatter", "k_ranges", "k_render_fwd", "k_render_bwd", "k_project_bwd", "memset"};
   if (!frame || !count || (capacity > 0 && !out)) return XG_ERR_INVALID_ARG;
   if (frame->nrec > 0) {

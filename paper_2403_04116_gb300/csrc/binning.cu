@@ -89,18 +89,21 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_reduce(const uint32_t* __
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_top(unsigned long long* __restrict__ part, int64_t capacity, DevStatus* __restrict__ st) {
-  if (threadIdx.x != 0) return;
-  unsigned long long run = 0;
-  for (int b = 0; b < kSortBlocks; ++b) {
-    const unsigned long long c = part[b];
-    part[b] = run;
-    run += c;
+__global__ void __launch_bounds__(1024) k_scan_top(unsigned long long* __restrict__ part, int64_t capacity,
+                                                  DevStatus* __restrict__ st) {
+  static_assert(kSortBlocks <= 1024, "one partial per thread");
+  __shared__ unsigned long long s_warp[32];
+  const int b = threadIdx.x;
+  const unsigned long long c = b < kSortBlocks ? part[b] : 0ull;
+  unsigned long long run;
+  const unsigned long long ex = block_exclusive_scan<1024>(c, s_warp, run);
+  if (b < kSortBlocks) part[b] = ex;
+  if (b == 0) {
+    st->scan_total = run;
+    st->pairs = (long long)run;
+    st->fwd_evaluated = st->fwd_contrib = st->bwd_evaluated = st->bwd_contrib = 0ull;
+    st->code = run > (unsigned long long)capacity ? XG_ERR_CAPACITY : XG_OK;
   }
-  st->scan_total = run;
-  st->pairs = (long long)run;
-  st->fwd_evaluated = st->fwd_contrib = st->bwd_evaluated = st->bwd_contrib = 0ull;
-  st->code = run > (unsigned long long)capacity ? XG_ERR_CAPACITY : XG_OK;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* __restrict__ count,
@@ -155,7 +158,8 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ count
 
 // ------------------------------------------------------------------------------------------
 // LSD radix sort, one 8-bit digit per pass, of WORDS parallel u32 arrays; the digit comes
-// from array `digit_word`.  Histograms are block-major: hist[block][256].
+// from array `digit_word`.  Histograms are block-major: hist[block][256], then the 256
+// digit totals.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ word, int shift,
                                                              const DevStatus* __restrict__ st, int64_t fixed_count,
@@ -175,38 +179,30 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
   hist[blockIdx.x * 256 + threadIdx.x] = c;
 }
 
-// Exclusive scan of hist in (digit, block) order, in place.  1024 threads: thread (q, d)
-// walks digit d over the q-th quarter of the blocks, one coalesced 1 KB row per step.
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist) {
-  constexpr int kQ = 4;
-  constexpr int kPer = (kSortBlocks + kQ - 1) / kQ;
-  __shared__ uint32_t s_part[kQ][256];
-  __shared__ uint32_t s_base[256];
-  __shared__ uint32_t s_warp[32];
-  const int d = threadIdx.x & 255, q = threadIdx.x >> 8;
-  const int b0 = q * kPer, b1 = min(kSortBlocks, b0 + kPer);
-  uint32_t sum = 0;
-#pragma unroll 8
-  for (int b = b0; b < b1; ++b) sum += hist[b * 256 + d];
-  s_part[q][d] = sum;
-  __syncthreads();
-  uint32_t digit_total = 0;
-  if (q == 0) {
+// Per digit, the exclusive prefix over blocks of hist[block][digit], in place, and the
+// digit's total in hist[kSortBlocks][digit].  One CTA per digit; the scatter turns the totals
+// into digit bases itself.
+__global__ void __launch_bounds__(256) k_radix_colscan(uint32_t* __restrict__ hist) {
+  constexpr int kPer = (kSortBlocks + 255) / 256;
+  __shared__ uint32_t s_warp[kWarps];
+  const int d = blockIdx.x;
+  const int b0 = threadIdx.x * kPer;
+  uint32_t c[kPer];
+  uint32_t local = 0;
 #pragma unroll
-    for (int k = 0; k < kQ; ++k) digit_total += s_part[k][d];
+  for (int k = 0; k < kPer; ++k) {
+    c[k] = b0 + k < kSortBlocks ? hist[(b0 + k) * 256 + d] : 0u;
+    local += c[k];
   }
-  uint32_t all;
-  const uint32_t base = block_exclusive_scan<1024>(digit_total, s_warp, all);  // threads with q > 0 add 0
-  if (q == 0) s_base[d] = base;
-  __syncthreads();
-  uint32_t run = s_base[d];
-  for (int k = 0; k < q; ++k) run += s_part[k][d];
-#pragma unroll 8
-  for (int b = b0; b < b1; ++b) {
-    const uint32_t c = hist[b * 256 + d];
-    hist[b * 256 + d] = run;
-    run += c;
-  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan<256>(local, s_warp, total);
+#pragma unroll
+  for (int k = 0; k < kPer; ++k)
+    if (b0 + k < kSortBlocks) {
+      hist[(b0 + k) * 256 + d] = run;
+      run += c[k];
+    }
+  if (threadIdx.x == 0) hist[kSortBlocks * 256 + d] = total;
 }
 
 // Stable scatter of one digit.  Each CTA walks its chunk in tiles of kSortTile items; in a
@@ -227,7 +223,11 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(SortArrays<WORDS
   const int64_t chunk = chunk_of(total);
   const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
   if (beg >= end) return;
-  s_bofs[tid] = hist[blockIdx.x * 256 + tid];
+  {
+    uint32_t all;
+    const uint32_t digit_base = block_exclusive_scan<kSortThreads>(hist[kSortBlocks * 256 + tid], s_warp, all);
+    s_bofs[tid] = digit_base + hist[blockIdx.x * 256 + tid];
+  }
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) s_wcnt[w][tid] = 0;
   __syncthreads();
@@ -324,7 +324,7 @@ void radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int s
   }
   {
     Timed t(f, kRadixScan, st);
-    k_radix_scan<<<1, 1024, 0, st>>>(hist);
+    k_radix_colscan<<<256, 256, 0, st>>>(hist);
   }
   {
     Timed t(f, kRadixScatter, st);
@@ -358,7 +358,7 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   }
   {
     Timed t(f, kScanTop, st);
-    k_scan_top<<<1, 32, 0, st>>>(p.scan_part, f->cfg.pair_capacity, p.status);
+    k_scan_top<<<1, 1024, 0, st>>>(p.scan_part, f->cfg.pair_capacity, p.status);
   }
   {
     Timed t(f, kScanDown, st);

@@ -6,7 +6,7 @@
 // sort (tile, depth, Gaussian) pairs with xg_sort_pairs_noalloc: the caller passes only
 // the input and output arrays; the ping-pong buffers, the digit histograms and the pair
 // count live in the file-scope device array below.  Every GPU that loads the library holds
-// that array (about 12.3 MB) until the process exits.
+// that array (about 12.6 MB) until the process exits.
 #include <mutex>
 
 #include "xg_internal.cuh"
@@ -14,7 +14,7 @@
 namespace xg {
 
 constexpr size_t kNoallocStatusBytes = 256;
-constexpr size_t kNoallocHistBytes = (size_t)4 * 256 * kSortBlocks;
+constexpr size_t kNoallocHistBytes = (size_t)4 * 256 * (kSortBlocks + 1);
 constexpr size_t kNoallocBufBytes = (size_t)4 * XG_NOALLOC_MAX_PAIRS;
 constexpr size_t kNoallocBytes = kNoallocStatusBytes + kNoallocHistBytes + 3 * kNoallocBufBytes;
 

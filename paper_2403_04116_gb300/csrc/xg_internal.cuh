@@ -16,7 +16,7 @@
 namespace xg {
 
 constexpr int kMaxViews = 1 << 16;
-constexpr int kSortBlocks = 304;      // 2 x 152 SMs: grid of the scan and radix-sort passes
+constexpr int kSortBlocks = 608;      // 4 x 152 SMs: grid of the scan and radix-sort passes
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;         // keys per thread per radix tile
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -119,7 +119,7 @@ struct FramePtrs {
   uint32_t* ent_gid[2];
   uint32_t* key_tile[2];   // pairs (ping-pong)
   uint32_t* value[2];
-  uint32_t* hist;     // [kSortBlocks][256]
+  uint32_t* hist;     // [kSortBlocks + 1][256]: per-block digit counts, then digit totals
   uint2* range;       // [V*T]
   float* tfinal;      // [V*H*W]
   uint32_t* last;     // [V*H*W]

@@ -38,6 +38,7 @@ class FrameConfig:
     tile_h: int = 16
     near_mm: float = NEAR_MM
     batch: int = 256  # Gaussians staged per round of the compositing kernels
+    pixels_per_thread: int = 2  # pixels each compositing thread owns (1, 2 or 4)
 
 
 class Frame:
@@ -56,7 +57,8 @@ class Frame:
         self.W, self.H = self.views[0].width, self.views[0].height
         self.pair_capacity = int(pair_capacity)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        self._c = B.XgConfig(self.cfg.tile_w, self.cfg.tile_h, self.cfg.near_mm, self.cfg.batch, self.pair_capacity)
+        self._c = B.XgConfig(self.cfg.tile_w, self.cfg.tile_h, self.cfg.near_mm, self.cfg.batch, self.pair_capacity,
+                             self.cfg.pixels_per_thread, 0)
         nbytes = B.xg_workspace_bytes(self._c, self.n, self.V, self.W, self.H)
         if nbytes == 0:
             raise ValueError("invalid frame configuration")

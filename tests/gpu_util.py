@@ -15,20 +15,21 @@ def to_device(g: dict) -> tuple:
     return tuple(torch.from_numpy(np.ascontiguousarray(g[k], dtype=np.float32)).cuda() for k in NAMES)
 
 
-def run_forward(g: dict, views, tile=(16, 16), capacity=None, near_mm=0.2) -> dict:
+def run_forward(g: dict, views, tile=(16, 16), capacity=None, near_mm=0.2, batch=256, ppt=2) -> dict:
     """Project, bin, sort and render through the C ABI.  Without ``capacity`` the pair
     capacity is sized from a first binning pass (so the frame never overflows)."""
     dev = to_device(g)
     n = dev[4].shape[0]
     cap = capacity or max(1 << 16, 16 * n * len(views))
-    f = Frame(n, views, FrameConfig(tile[0], tile[1], near_mm), cap)
+    cfg = FrameConfig(tile[0], tile[1], near_mm, batch=batch, pixels_per_thread=ppt)
+    f = Frame(n, views, cfg, cap)
     f.project(*dev)
     proj = {"records": f.array("records").cpu().numpy(), "depth": f.array("depth").cpu().numpy(),
             "rect": f.array("rect").cpu().numpy().astype(np.int32), "count": f.array("count").cpu().numpy()}
     f.bin_sort()
     st = f.status()
     if capacity is None and st.code == B.XG_ERR_CAPACITY:
-        f = Frame(n, views, FrameConfig(tile[0], tile[1], near_mm), int(st.pairs))
+        f = Frame(n, views, cfg, int(st.pairs))
         f.project(*dev)
         f.bin_sort()
         st = f.status()

@@ -41,9 +41,11 @@ def test_workspace_bytes_host_checks(lib):
     assert 0 < small < big
     assert B.xg_workspace_bytes(cfg, 0, 1, 64, 64) == 0
     assert B.xg_workspace_bytes(cfg, 10, 1, 0, 64) == 0
-    for bad in (B.XgConfig(12, 16, 0.2, 0, 100), B.XgConfig(32, 32, 0.2, 0, 100), B.XgConfig(16, 16, 0.0, 0, 100),
-                B.XgConfig(16, 16, 0.2, 0, 0), B.XgConfig(16, 16, float("nan"), 0, 100),
-                B.XgConfig(16, 16, 0.2, 100, 100)):
+    assert B.xg_workspace_bytes(B.XgConfig(32, 32, 0.2, 0, 100, 2, 0), 10, 1, 64, 64) > 0
+    for bad in (B.XgConfig(12, 16, 0.2, 0, 100), B.XgConfig(32, 32, 0.2, 0, 100, 1, 0),
+                B.XgConfig(16, 16, 0.0, 0, 100), B.XgConfig(16, 16, 0.2, 0, 0),
+                B.XgConfig(16, 16, float("nan"), 0, 100), B.XgConfig(16, 16, 0.2, 100, 100),
+                B.XgConfig(16, 16, 0.2, 0, 100, 3, 0), B.XgConfig(16, 8, 0.2, 0, 100, 4, 0)):
         assert B.xg_workspace_bytes(bad, 10, 1, 64, 64) == 0
 
 

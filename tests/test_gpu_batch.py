@@ -84,7 +84,7 @@ def test_autotune_choice_keeps_the_image():
     n = dev[4].shape[0]
     best = autotune(n, views, dev, target, tiles=((8, 8), (16, 16)), batches=(64, 256), reps=2, use_cache=False)
     assert (best.tile_w, best.tile_h) in ((8, 8), (16, 16)) and best.batch in (64, 256) and best.ms > 0
-    a = GraphedStep(n, views, FrameConfig(best.tile_w, best.tile_h, batch=best.batch), best.pair_capacity)
+    a = GraphedStep(n, views, best.config(), best.pair_capacity)
     b = GraphedStep(n, views, FrameConfig(32, 16, batch=128), size_pairs(n, views, FrameConfig(32, 16), dev))
     for s in (a, b):
         s.load(dev, target)

@@ -267,10 +267,23 @@ def test_views_in_one_frame_equal_separate_frames():
         np.testing.assert_array_equal(together["last"][v], alone["last"][0])
 
 
-def test_tile_size_does_not_change_the_image():
+def test_tile_shape_batch_and_pixels_per_thread_do_not_change_the_image():
     g, views, _ = _case("ragged_3views_32x16")
     base = run_forward(g, views, (16, 16))
-    for tile in [(8, 8), (32, 16), (8, 32), (32, 8)]:
-        other = run_forward(g, views, tile)
+    for tile, batch, ppt in [((8, 8), 64, 1), ((32, 16), 128, 1), ((8, 32), 256, 2), ((32, 8), 64, 2),
+                             ((16, 16), 128, 1), ((32, 32), 256, 2), ((16, 16), 64, 4), ((32, 32), 128, 4),
+                             ((8, 16), 256, 4)]:
+        other = run_forward(g, views, tile, batch=batch, ppt=ppt)
         np.testing.assert_array_equal(other["image"], base["image"])
         np.testing.assert_array_equal(other["ncontrib"], base["ncontrib"])
+        np.testing.assert_array_equal(other["tfinal"], base["tfinal"])
+
+
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+def test_backward_pixels_per_thread_variants_agree(ppt):
+    g, views, tile = _case("tall_2views_16x32")
+    G = np.random.default_rng(5).choice([-1.0, 1.0], size=(len(views), views[0].height, views[0].width))
+    a = run_backward(run_forward(g, views, tile, batch=64, ppt=ppt), G)
+    b = run_backward(run_forward(g, views, (16, 16), batch=256, ppt=1 if ppt != 1 else 2), G)
+    for k in NAMES:
+        np.testing.assert_allclose(a[k], b[k], rtol=1e-4, atol=1e-5 * np.abs(b[k]).max())
