@@ -307,9 +307,9 @@ void xr_render(const float* rec, const uint32_t* range, const int32_t* list, con
         const float* r = rec + 8 * (int64_t)list[k];
         float na = -0.5f * r[2], nb = -r[3], nc2 = -0.5f * r[4];
         float dx = r[0] - px, dy = r[1] - py;
-        float p = nb * (dx * dy);
-        p = fmaf(nc2, dy * dy, p);
-        p = fmaf(na, dx * dx, p);
+        /* dx (na dx + nb dy) + (nc dy) dy */
+        float t = fmaf(na, dx, nb * dy);
+        float p = fmaf(dx, t, (nc2 * dy) * dy);
         float ex = xr_exp(p);
         float al = fminf(R_ALPHA_MAX, r[5] * ex);
         if (al < R_ALPHA_MIN) continue;

@@ -16,11 +16,10 @@
 //
 // The backward pass walks each pixel's list back to front from its last contributor,
 // recovering the transmittance by division instead of storing it.  Per list entry, a warp
-// with any contributing pixel reduces its 7 per-pixel terms (five moments of dL/dpower times
-// the offset d, and the opacity and intensity terms) with an 8-value reduce-scatter
-// butterfly (9 shuffles; lane 4k ends with the sum of term k) and adds them to shared
-// memory; after the batch each Gaussian's sums are turned into dL/du and dL/dconic and
-// added to global memory with two float4 atomics.
+// with contributing pixels sums its 7 per-pixel terms (six moments of dL/dpower and the
+// intensity term) with an 8-value reduce-scatter butterfly (9 shuffles; lane 4k ends with
+// the sum of term k) into shared memory.  After the batch each Gaussian's sums are turned into dL/du, dL/dconic and
+// dL/dopacity and added to global memory with two float4 atomics.
 #include "xg_internal.cuh"
 
 namespace xg {
@@ -122,14 +121,13 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int l
   return d;
 }
 
-// The exponent -1/2 d^T K d and sigma = min(0.99, o e^p) in the fixed FP32 sequence.
+// The exponent -1/2 d^T K d = dx (na dx + nb dy) + (nc dy) dy, with na = -a/2, nb = -b,
+// nc = -c/2, in the fixed FP32 sequence.
 __device__ __forceinline__ float power_of(const float4 a, const float nc, float px, float py, float& dx, float& dy) {
   dx = fsub(a.x, px);
   dy = fsub(a.y, py);
-  float p = fmul(a.w, fmul(dx, dy));
-  p = ffma(nc, fmul(dy, dy), p);
-  p = ffma(a.z, fmul(dx, dx), p);
-  return p;
+  const float t = ffma(a.z, dx, fmul(a.w, dy));
+  return ffma(dx, t, fmul(fmul(nc, dy), dy));
 }
 
 template <int kBatch, int PPT>
@@ -182,6 +180,7 @@ __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ ra
     __syncthreads();
     if (__all_sync(0xffffffffu, all_done())) continue;
     const int m = warp_list(s_box, cnt, bx0, by0, by1, my_list, lane);
+#pragma unroll 2
     for (int k = 0; k < m; ++k) {
       if (all_done()) break;
       const int j = my_list[k];
@@ -344,15 +343,17 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
           const float dL_dal = G[q] * Tc[q] * (in - A[q]);
           A[q] = al * in + (1.f - al) * A[q];
           if (oe < kAlphaMax) {
-            gv[5] += dL_dal * e;                      // dL/d opacity
-            const float dp = dL_dal * al;             // dL/d power
-            // moments of dL/d power; the conic enters once per Gaussian at the flush
+            // moments of dp = dL/d power: sum dp (dL/d opacity = sum dp / opacity, as
+            // d sigma / d opacity = e^p = sigma / opacity) and sum dp d, dp d d^T; the
+            // conic and the opacity enter once per Gaussian at the flush
+            const float dp = dL_dal * al;
             const float sx = dp * dx, sy = dp * dy;
             gv[0] += sx;
             gv[1] += sy;
             gv[2] += sx * dx;
             gv[3] += sx * dy;
             gv[4] += sy * dy;
+            gv[5] += dp;
           }
         }
         if (__any_sync(0xffffffffu, contrib)) {
@@ -364,9 +365,10 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
     }
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-      // sums over the tile's pixels: S_x, S_y, S_xx, S_xy, S_yy of dL/dpower times d, and
-      // dL/dopacity, dL/dintensity.  power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = u - p:
-      // dL/du = -(K (S_x, S_y)), dL/d(a, b, c) = (-S_xx / 2, -S_xy, -S_yy / 2).
+      // sums over the tile's pixels: S_x, S_y, S_xx, S_xy, S_yy, S_1 of dp = dL/dpower times
+      // (d, d d^T, 1), and dL/dintensity.  power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = u - p:
+      // dL/du = -(K (S_x, S_y)), dL/d(a, b, c) = (-S_xx / 2, -S_xy, -S_yy / 2),
+      // dL/dopacity = S_1 / opacity.
       const float4 m0 = *reinterpret_cast<const float4*>(&s_acc[j * 8]);
       const float4 m1 = *reinterpret_cast<const float4*>(&s_acc[j * 8 + 4]);
       if (m0.x != 0.f || m0.y != 0.f || m0.z != 0.f || m0.w != 0.f || m1.x != 0.f || m1.y != 0.f ||
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
         const float nc = s_b[j].x;  // -c/2
         const float4 q0 = make_float4(2.f * a.z * m0.x + a.w * m0.y, a.w * m0.x + 2.f * nc * m0.y, -0.5f * m0.z,
                                       -m0.w);
-        const float4 q1 = make_float4(-0.5f * m1.x, m1.y, m1.z, 0.f);
+        const float4 q1 = make_float4(-0.5f * m1.x, __fdividef(m1.y, s_b[j].y), m1.z, 0.f);
         float4* dst = reinterpret_cast<float4*>(g2d + 8 * (vn_base + s_g[j]));
         atomicAdd(dst, q0);
         atomicAdd(dst + 1, q1);
