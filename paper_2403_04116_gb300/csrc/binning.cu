@@ -128,32 +128,71 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* __re
 // ------------------------------------------------------------------------------------------
 // emit one (tile key, Gaussian) pair per touched tile, in (view, depth) order
 // ------------------------------------------------------------------------------------------
+// A warp takes 32 consecutive entries, whose pairs are contiguous in the output; lane l
+// writes pairs l, l+32, ... of the warp, finding its entry by a binary search over the
+// warp's prefix of counts, so every store instruction writes consecutive addresses.
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ count, const uint32_t* __restrict__ offset,
                                               const ushort4* __restrict__ rect, const uint32_t* __restrict__ view,
                                               const uint32_t* __restrict__ gid, int64_t n, int64_t total,
                                               int tiles_x, int64_t tiles_per_view, int64_t capacity,
                                               DevStatus* __restrict__ st, uint32_t* __restrict__ key_tile,
                                               uint32_t* __restrict__ value) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= total) return;
   if (st->code != XG_OK) return;
-  const uint32_t v = view[i], g = gid[i];
-  const int64_t vg = (int64_t)v * n + g;
-  const uint32_t cnt = count[vg];
-  if (cnt == 0) return;
-  const ushort4 r = rect[vg];
-  const uint32_t vbase = (uint32_t)(v * tiles_per_view);
-  uint32_t o = offset[i];
-  if ((int64_t)o + cnt > capacity) {  // cannot happen when the scan is right
-    st->code = XG_ERR_CHECK;
+  const int64_t warp_first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31;
+  if (warp_first >= total) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = warp_first + lane;
+  uint32_t v = 0, g = 0, cnt = 0, o = 0, xy0 = 0, xy1 = 0;
+  if (i < total) {
+    v = view[i];
+    g = gid[i];
+    const int64_t vg = (int64_t)v * n + g;
+    cnt = count[vg];
+    o = offset[i];
+    if (cnt) {
+      const ushort4 r = rect[vg];
+      xy0 = (uint32_t)r.x | ((uint32_t)r.y << 16);
+      xy1 = (uint32_t)r.z | ((uint32_t)r.w << 16);
+    }
+  }
+  // exclusive prefix of the counts over the warp
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const uint32_t pre = incl - cnt;
+  const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+  const uint32_t base = __shfl_sync(0xffffffffu, o, 0);
+  if ((int64_t)base + tot > capacity) {  // cannot happen when the scan is right
+    if (lane == 0) st->code = XG_ERR_CHECK;
     return;
   }
-  for (int ty = r.y; ty <= r.w; ++ty)
-    for (int tx = r.x; tx <= r.z; ++tx) {
-      key_tile[o] = vbase + (uint32_t)(ty * tiles_x + tx);
-      value[o] = g;
-      ++o;
+  for (uint32_t p0 = 0; p0 < tot; p0 += 32) {
+    const uint32_t p = p0 + lane;
+    // the last entry whose prefix is <= p (entries without pairs share the next prefix)
+    int e = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int cand = min(e + step, 31);
+      const uint32_t pc = __shfl_sync(0xffffffffu, pre, cand);
+      if (e + step <= 31 && pc <= p) e = cand;
     }
+    const uint32_t e_pre = __shfl_sync(0xffffffffu, pre, e);
+    const uint32_t e_xy0 = __shfl_sync(0xffffffffu, xy0, e);
+    const uint32_t e_xy1 = __shfl_sync(0xffffffffu, xy1, e);
+    const uint32_t e_v = __shfl_sync(0xffffffffu, v, e);
+    const uint32_t e_g = __shfl_sync(0xffffffffu, g, e);
+    if (p < tot) {
+      const uint32_t k = p - e_pre;
+      const uint32_t x0 = e_xy0 & 0xffffu, y0 = e_xy0 >> 16, x1 = e_xy1 & 0xffffu;
+      const uint32_t wdt = x1 - x0 + 1u;
+      const uint32_t ty = y0 + k / wdt, tx = x0 + k % wdt;
+      key_tile[base + p] = (uint32_t)(e_v * tiles_per_view) + ty * (uint32_t)tiles_x + tx;
+      value[base + p] = e_g;
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -234,16 +273,21 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(SortArrays<WORDS
 
   for (int64_t base = beg; base < end; base += kSortTile) {
     uint32_t item[kSortItems][WORDS], dig[kSortItems], rank[kSortItems];
+    // all loads of the tile first, so that kSortItems * WORDS of them are in flight
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+      const int64_t i = base + warp * (32 * kSortItems) + k * 32 + lane;
+#pragma unroll
+      for (int w = 0; w < WORDS; ++w) item[k][w] = i < end ? __ldg(arr.in[w] + i) : 0u;
+    }
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
       const int64_t i = base + warp * (32 * kSortItems) + k * 32 + lane;
       const bool valid = i < end;
       uint32_t dw = 0;
 #pragma unroll
-      for (int w = 0; w < WORDS; ++w) {
-        item[k][w] = valid ? arr.in[w][i] : 0u;
+      for (int w = 0; w < WORDS; ++w)
         if (w == digit_word) dw = item[k][w];
-      }
       dig[k] = valid ? ((dw >> shift) & 255u) : 256u;
       const uint32_t peers = __match_any_sync(0xffffffffu, dig[k]);
       rank[k] = valid ? s_wcnt[warp][dig[k]] + __popc(peers & lt_mask) : 0u;
