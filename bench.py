@@ -47,8 +47,13 @@ FWD_OPS_EVAL, FWD_OPS_CONTRIB = 20, 4
 BWD_OPS_EVAL, BWD_OPS_CONTRIB = 20, 30
 SMS, FP32_LANES = 152, 128
 
-# DRAM traffic per launch from an ncu capture, valid while the kernel source is unchanged.
-TRAFFIC = {}
+# DRAM traffic per launch from an ncu capture (profiles/k_render_train50k.md), valid while
+# the kernel source is unchanged (sha256 prefix of the .cu file) and for the configuration
+# it was taken with.
+TRAFFIC = {"k_render_bwd": {"bytes_per_launch": 204.2e6, "source_sha": "76631297de68b4a2",
+                            "config": (16, 16, 128, 2), "workload": "train50k"},
+           "k_render_fwd": {"bytes_per_launch": 124.2e6, "source_sha": "76631297de68b4a2",
+                            "config": (16, 16, 128, 2), "workload": "train50k"}}
 
 
 def _args():
@@ -62,6 +67,8 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the one-view-per-launch form")
+    ap.add_argument("--config", default=None, help="tile and kernel shape TWxTH:batch:pixels_per_thread "
+                                                    "(e.g. 16x16:128:2) instead of autotuning")
     return ap.parse_args()
 
 
@@ -263,7 +270,14 @@ def run_ours(args) -> None:
     n = w["n"]
 
     # tile shape and staging batch: autotuned on the graphed step (cached per workload shape)
-    tuned = autotune(n, views, dev, target) if args.autotune else None
+    if args.config:
+        tw_th, b_s, p_s = args.config.split(":")
+        tw_s, th_s = tw_th.split("x")
+        from paper_2403_04116_gb300.batch import TuneResult
+        c0 = FrameConfig(int(tw_s), int(th_s), batch=int(b_s), pixels_per_thread=int(p_s))
+        tuned = TuneResult(c0.tile_w, c0.tile_h, c0.batch, c0.pixels_per_thread, 0.0, size_pairs(n, views, c0, dev))
+    else:
+        tuned = autotune(n, views, dev, target) if args.autotune else None
     tile = (tuned.tile_w, tuned.tile_h) if tuned else tuple(w["tile"])
     batch = tuned.batch if tuned else 256
     ppt = tuned.pixels_per_thread if tuned else 2
@@ -363,7 +377,9 @@ def run_ours(args) -> None:
     src = {"k_render_bwd": "render.cu", "k_render_fwd": "render.cu", "k_radix_scatter": "binning.cu",
            "k_project": "project.cu", "k_emit": "binning.cu", "k_project_bwd": "project.cu"}.get(dom)
     tr = TRAFFIC.get(dom)
-    roof["traffic"] = tr["bytes_per_launch"] if tr and src and tr["source_sha"] == _source_sha(src) else None
+    same = (tr and src and tr["source_sha"] == _source_sha(src) and tr["workload"] == args.workload
+            and tr["config"] == (tile[0], tile[1], batch, ppt))
+    roof["traffic"] = tr["bytes_per_launch"] if same else None
     roof["kernel"] = dom
     roof["peak_source"] = (f"{SMS} SMs x {FP32_LANES} FP32 lanes x {clock_mhz:.0f} MHz" if roof["bound"] == "alu"
                            else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")
