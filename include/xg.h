@@ -214,6 +214,76 @@ xg_status xg_frame_set_timing(xg_frame* frame, int32_t enable);
  * and the number written to *count, and start a new accumulation. */
 xg_status xg_frame_read_timing(xg_frame* frame, xg_kernel_time* out, int32_t capacity, int32_t* count);
 
+/* ------------------------------------------------------------------------------------ */
+/* The rest of a training step (Sec. 3.1, Eq. 3 and 11; implementation details of Sec. 4.1) */
+/* ------------------------------------------------------------------------------------ */
+
+/* Learnable parameters that are activated before projection (mean and quaternion are used
+ * as they are).  Device arrays: log_scale[3][n], opacity_logit[n], features[n_features][n]
+ * (the feature vector f of Eq. 3), lambda[n_features] (the constant weights of Eq. 3).
+ * 1 <= n_features <= 64. */
+typedef struct {
+  const float* log_scale;
+  const float* opacity_logit;
+  const float* features;
+  const float* lambda;
+  int32_t n_features;
+  int32_t reserved;
+  int64_t n;
+} xg_raw_gaussians;
+
+/* Activations of the radiative Gaussian model: scale = exp(log_scale), opacity =
+ * sigmoid(opacity_logit), and the radiation intensity response function (Eq. 3),
+ * intensity = sigmoid(sum_k lambda_k f_k) -- the weights applied as an inner product.
+ * Writes device scale[3][n], opacity[n], intensity[n]. */
+xg_status xg_activate(const xg_raw_gaussians* raw, float* scale, float* opacity, float* intensity, void* stream);
+
+/* Chain rule of xg_activate: from dL/dscale[3][n], dL/dopacity[n], dL/dintensity[n] (as
+ * xg_render_bwd writes them) to dL/dlog_scale[3][n], dL/dopacity_logit[n],
+ * dL/dfeatures[n_features][n] (overwritten). */
+xg_status xg_activate_bwd(const xg_raw_gaussians* raw, const float* g_scale, const float* g_opacity,
+                          const float* g_intensity, float* g_log_scale, float* g_opacity_logit, float* g_features,
+                          void* stream);
+
+/* Device workspace bytes of xg_loss_l1_ssim for n_views images of width x height. */
+size_t xg_loss_workspace_bytes(int32_t n_views, int32_t width, int32_t height);
+
+/* Training objective of Eq. 11 over n_views images: loss = (1 - gamma) * mean |I - I*| +
+ * gamma * (1 - mean SSIM(I, I*)), SSIM with the 11-tap Gaussian window of sigma 1.5, zero
+ * padding, C1 = 0.01^2, C2 = 0.03^2 (intensities in [0, 1]); the mean runs over all pixels
+ * of all views.  grad[V][H][W] receives dloss/dI; loss (3 device floats) receives the
+ * loss, the mean L1 and the mean SSIM.  The workspace (16-byte aligned) is scratch. */
+xg_status xg_loss_l1_ssim(const float* image, const float* target, int32_t n_views, int32_t width, int32_t height,
+                          float gamma, float* grad, float* loss, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/* One Adam step (Sec. 4.1) over up to XG_ADAM_MAX_GROUPS parameter groups.  Each group:
+ * device param, grad, first and second moments m, v (count floats each, updated in place),
+ * the learning rate lr, and, when decay_steps > 0, an exponential decay from lr to lr_final
+ * over decay_steps steps.  step points to a device int32 holding the number of steps
+ * taken so far; the call uses it for bias correction and the schedule and increments it,
+ * so a captured step can be replayed. */
+#define XG_ADAM_MAX_GROUPS 8
+typedef struct {
+  float* param;
+  const float* grad;
+  float* m;
+  float* v;
+  int64_t count;
+  float lr;
+  float lr_final;
+  int32_t decay_steps;
+  int32_t reserved;
+} xg_adam_group;
+
+xg_status xg_adam_step(const xg_adam_group* groups, int32_t n_groups, int32_t* step, float beta1, float beta2,
+                       float eps, void* stream);
+
+/* Peak signal-to-noise ratio (peak 1) of each of n_views images of pixels_per_view pixels:
+ * psnr[v] = -10 log10(mean (I - I*)^2) (device floats, overwritten). */
+xg_status xg_psnr(const float* image, const float* target, int32_t n_views, int64_t pixels_per_view, float* psnr,
+                  void* stream);
+
 /* Largest pair count xg_sort_pairs_noalloc accepts. */
 #define XG_NOALLOC_MAX_PAIRS (1 << 20)
 

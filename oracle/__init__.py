@@ -11,6 +11,9 @@ Two C sources, built here with gcc (OpenMP, ``-ffp-contract=off``):
   per-pixel reverse recursion and the analytic chain rule.
 * ``xg_replica32.c`` -- the FP32 replica of the index work and per-pixel decisions,
   which the GPU must match bit for bit.
+* ``train64.py`` -- FP64 NumPy/SciPy versions of the rest of a training step: the
+  activations and RIRF (Eq. 3), the (1 - gamma) L1 + gamma (1 - SSIM) objective (Eq. 11)
+  with its gradient, Adam, PSNR.
 """
 from __future__ import annotations
 

@@ -20,7 +20,10 @@ XG_ERR_CHECK = 5
 # Every symbol include/xg.h declares.
 EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_project", "xg_bin_sort",
            "xg_render_fwd", "xg_render_bwd", "xg_frame_read_status", "xg_frame_layout", "xg_loss_l1",
-           "xg_frame_set_timing", "xg_frame_read_timing", "xg_sort_pairs_noalloc", "xg_status_str")
+           "xg_frame_set_timing", "xg_frame_read_timing", "xg_activate", "xg_activate_bwd",
+           "xg_loss_workspace_bytes", "xg_loss_l1_ssim", "xg_adam_step", "xg_psnr", "xg_sort_pairs_noalloc",
+           "xg_status_str")
+XG_ADAM_MAX_GROUPS = 8
 XG_NOALLOC_MAX_PAIRS = 1 << 20
 
 
@@ -62,6 +65,18 @@ class XgLayout(ctypes.Structure):
                  "range", "tfinal", "last", "grad2d")] + [
         ("tiles_per_view", ctypes.c_int64), ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
         ("sort_passes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class XgRawGaussians(ctypes.Structure):
+    _fields_ = [("log_scale", ctypes.c_void_p), ("opacity_logit", ctypes.c_void_p), ("features", ctypes.c_void_p),
+                ("lambda_", ctypes.c_void_p), ("n_features", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n", ctypes.c_int64)]
+
+
+class XgAdamGroup(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("count", ctypes.c_int64), ("lr", ctypes.c_float),
+                ("lr_final", ctypes.c_float), ("decay_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class XgError(RuntimeError):
@@ -116,6 +131,20 @@ def lib(build_if_missing: bool = False):
     L.xg_frame_read_timing.argtypes = [P, ctypes.POINTER(XgKernelTime), ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_int32)]
     L.xg_frame_read_timing.restype = ctypes.c_int
+    L.xg_activate.argtypes = [ctypes.POINTER(XgRawGaussians), P, P, P, P]
+    L.xg_activate.restype = ctypes.c_int
+    L.xg_activate_bwd.argtypes = [ctypes.POINTER(XgRawGaussians), P, P, P, P, P, P, P]
+    L.xg_activate_bwd.restype = ctypes.c_int
+    L.xg_loss_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    L.xg_loss_workspace_bytes.restype = ctypes.c_size_t
+    L.xg_loss_l1_ssim.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, P, P, P,
+                                  ctypes.c_size_t, P]
+    L.xg_loss_l1_ssim.restype = ctypes.c_int
+    L.xg_adam_step.argtypes = [ctypes.POINTER(XgAdamGroup), ctypes.c_int32, P, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, P]
+    L.xg_adam_step.restype = ctypes.c_int
+    L.xg_psnr.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, P, P]
+    L.xg_psnr.restype = ctypes.c_int
     L.xg_sort_pairs_noalloc.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int32, P, P, P, P]
     L.xg_sort_pairs_noalloc.restype = ctypes.c_int
     L.xg_status_str.argtypes = [ctypes.c_int]
@@ -198,3 +227,32 @@ def xg_sort_pairs_noalloc(key_tile: int, key_depth: int, value: int, count: int,
                           out_key_tile: int, out_key_depth: int, out_value: int, stream: int) -> None:
     _check(lib().xg_sort_pairs_noalloc(key_tile, key_depth, value, count, tile_bits, out_key_tile, out_key_depth,
                                        out_value, stream), "xg_sort_pairs_noalloc")
+
+
+def xg_activate(raw: XgRawGaussians, scale: int, opacity: int, intensity: int, stream: int) -> None:
+    _check(lib().xg_activate(ctypes.byref(raw), scale, opacity, intensity, stream), "xg_activate")
+
+
+def xg_activate_bwd(raw: XgRawGaussians, g_scale: int, g_opacity: int, g_intensity: int, g_log_scale: int,
+                    g_opacity_logit: int, g_features: int, stream: int) -> None:
+    _check(lib().xg_activate_bwd(ctypes.byref(raw), g_scale, g_opacity, g_intensity, g_log_scale, g_opacity_logit,
+                                 g_features, stream), "xg_activate_bwd")
+
+
+def xg_loss_workspace_bytes(n_views: int, width: int, height: int) -> int:
+    return int(lib().xg_loss_workspace_bytes(n_views, width, height))
+
+
+def xg_loss_l1_ssim(image: int, target: int, n_views: int, width: int, height: int, gamma: float, grad: int,
+                    loss: int, workspace: int, workspace_bytes: int, stream: int) -> None:
+    _check(lib().xg_loss_l1_ssim(image, target, n_views, width, height, gamma, grad, loss, workspace,
+                                 workspace_bytes, stream), "xg_loss_l1_ssim")
+
+
+def xg_adam_step(groups, step: int, beta1: float, beta2: float, eps: float, stream: int) -> None:
+    arr = (XgAdamGroup * len(groups))(*groups)
+    _check(lib().xg_adam_step(arr, len(groups), step, beta1, beta2, eps, stream), "xg_adam_step")
+
+
+def xg_psnr(image: int, target: int, n_views: int, pixels_per_view: int, psnr: int, stream: int) -> None:
+    _check(lib().xg_psnr(image, target, n_views, pixels_per_view, psnr, stream), "xg_psnr")

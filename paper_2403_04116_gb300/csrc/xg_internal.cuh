@@ -126,6 +126,12 @@ struct FramePtrs {
   float* grad2d;      // [V*n][8]
 };
 
+// Parameter groups of one Adam step, passed by value.
+struct AdamGroups {
+  xg_adam_group g[XG_ADAM_MAX_GROUPS];
+  int count;
+};
+
 // Input and output arrays of one radix pass, passed by value.
 template <int WORDS>
 struct SortArrays {

@@ -1,0 +1,260 @@
+"""Training of the radiative Gaussian model on cone-beam projections (Sec. 3, Eq. 11; the
+optimiser settings of Sec. 4.1), every step replayed from a CUDA graph.
+
+A step takes one group of views (8 by default) and runs, all in libxg.so:
+activate (exp, sigmoid, RIRF) -> project -> bin + sort -> composite -> (1 - gamma) L1 +
+gamma (1 - SSIM) -> composite backward -> activation backward -> Adam.  Views are split
+into fixed groups, one frame and one captured graph per group, replayed in turn.
+
+    python -m paper_2403_04116_gb300.train [--steps 20000] [--gaussians 200000] ...
+
+prints one JSON line: wall time, steps/s, training loss, held-out PSNR before and after.
+The number of Gaussians is fixed (the paper's adaptive density control is not part of
+this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import binding as B
+from . import synth
+from .batch import size_pairs
+from .render import Frame, FrameConfig, _stream_handle
+
+NAMES = ("mean", "log_scale", "quat", "opacity_logit", "features")
+
+
+@dataclass
+class TrainConfig:
+    n_features: int = 16            # N_f (Sec. 4.4: 16 is on par with 32)
+    gamma: float = 0.2              # Eq. 11
+    views_per_step: int = 8
+    lr_position: float = 1.9e-4     # times position_scale, decaying exponentially to lr_position_final
+    lr_position_final: float = 1.9e-6
+    position_scale: float = 1.0     # scene extent in mm
+    lr_feature: float = 2e-3
+    lr_opacity: float = 8e-3
+    lr_scale: float = 5e-3
+    lr_rotation: float = 1e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+    decay_steps: int = 20000
+
+
+def raw_from_activated(g: dict, n_features: int, gen: np.random.Generator) -> dict:
+    """Raw parameters whose activations reproduce the given Gaussians (lambda = 1):
+    log of the scales, logit of the opacities, features summing to logit(intensity)."""
+    inten = np.clip(g["intensity"].astype(np.float64), 1e-4, 1 - 1e-4)
+    op = np.clip(g["opacity"].astype(np.float64), 1e-6, 1 - 1e-6)
+    z = np.log(inten / (1 - inten))
+    noise = gen.normal(0, 0.01, size=(n_features, inten.size))
+    noise -= noise.mean(axis=0, keepdims=True)
+    return {"mean": g["mean"].astype(np.float32), "log_scale": np.log(g["scale"]).astype(np.float32),
+            "quat": g["quat"].astype(np.float32), "opacity_logit": np.log(op / (1 - op)).astype(np.float32),
+            "features": (z / n_features + noise).astype(np.float32)}
+
+
+class Trainer:
+    def __init__(self, raw: dict, views, targets: torch.Tensor, cfg: TrainConfig, frame_cfg: FrameConfig,
+                 device="cuda", capacity_margin: float = 1.6):
+        self.cfg = cfg
+        self.frame_cfg = frame_cfg
+        self.device = torch.device(device)
+        self.p = {k: torch.from_numpy(np.ascontiguousarray(raw[k])).to(self.device) for k in NAMES}
+        self.n = self.p["mean"].shape[1]
+        self.nf = self.p["features"].shape[0]
+        self.lam = torch.ones(self.nf, device=self.device)
+        self.m = {k: torch.zeros_like(v) for k, v in self.p.items()}
+        self.v = {k: torch.zeros_like(v) for k, v in self.p.items()}
+        self.g = {k: torch.zeros_like(v) for k, v in self.p.items()}
+        n = self.n
+        self.act = {"scale": torch.empty(3, n, device=self.device), "opacity": torch.empty(n, device=self.device),
+                    "intensity": torch.empty(n, device=self.device)}
+        self.g_act = {"scale": torch.empty(3, n, device=self.device), "opacity": torch.empty(n, device=self.device),
+                      "intensity": torch.empty(n, device=self.device)}
+        self.step_count = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.loss = torch.zeros(3, device=self.device)
+        k = cfg.views_per_step
+        self.groups = [list(range(i, min(i + k, len(views)))) for i in range(0, len(views), k)]
+        self.views = list(views)
+        self.targets = targets
+        self.capacity_margin = capacity_margin
+        self.frames, self.images, self.grad_images, self.loss_ws, self.graphs = [], [], [], [], []
+        self._raw = self._raw_struct()
+        self._groups = self._adam_groups()
+        self._build()
+
+    # ---- plumbing ---------------------------------------------------------------------
+    def _raw_struct(self) -> B.XgRawGaussians:
+        return B.XgRawGaussians(self.p["log_scale"].data_ptr(), self.p["opacity_logit"].data_ptr(),
+                                self.p["features"].data_ptr(), self.lam.data_ptr(), self.nf, 0, self.n)
+
+    def _adam_groups(self) -> list:
+        c = self.cfg
+        lrs = {"mean": (c.lr_position * c.position_scale, c.lr_position_final * c.position_scale, c.decay_steps),
+               "log_scale": (c.lr_scale, 0.0, 0), "quat": (c.lr_rotation, 0.0, 0),
+               "opacity_logit": (c.lr_opacity, 0.0, 0), "features": (c.lr_feature, 0.0, 0)}
+        return [B.XgAdamGroup(self.p[k].data_ptr(), self.g[k].data_ptr(), self.m[k].data_ptr(), self.v[k].data_ptr(),
+                              self.p[k].numel(), lr, lr_f, ds, 0) for k, (lr, lr_f, ds) in lrs.items()]
+
+    def _activated(self) -> tuple:
+        return (self.p["mean"], self.act["scale"], self.p["quat"], self.act["opacity"], self.act["intensity"])
+
+    def _build(self) -> None:
+        s = _stream_handle()
+        B.xg_activate(self._raw, self.act["scale"].data_ptr(), self.act["opacity"].data_ptr(),
+                      self.act["intensity"].data_ptr(), s)
+        for idx in self.groups:
+            vs = [self.views[i] for i in idx]
+            cap = int(size_pairs(self.n, vs, self.frame_cfg, self._activated(), margin=self.capacity_margin))
+            f = Frame(self.n, vs, self.frame_cfg, cap, self.device)
+            H, W = f.H, f.W
+            self.frames.append(f)
+            self.images.append(torch.empty(len(vs), H, W, device=self.device))
+            self.grad_images.append(torch.empty(len(vs), H, W, device=self.device))
+            nb = B.xg_loss_workspace_bytes(len(vs), W, H)
+            self.loss_ws.append(torch.empty(nb // 4 + 4, dtype=torch.float32, device=self.device))
+        self.target_groups = [self.targets[idx[0]:idx[-1] + 1].contiguous() for idx in self.groups]
+        self.graphs = [None] * len(self.groups)
+
+    def _step_calls(self, gi: int) -> None:
+        s = _stream_handle()
+        f, img, gimg = self.frames[gi], self.images[gi], self.grad_images[gi]
+        tgt, ws = self.target_groups[gi], self.loss_ws[gi]
+        B.xg_activate(self._raw, self.act["scale"].data_ptr(), self.act["opacity"].data_ptr(),
+                      self.act["intensity"].data_ptr(), s)
+        f.project(*self._activated())
+        f.bin_sort()
+        f.render_fwd(img)
+        B.xg_loss_l1_ssim(img.data_ptr(), tgt.data_ptr(), f.V, f.W, f.H, self.cfg.gamma, gimg.data_ptr(),
+                          self.loss.data_ptr(), ws.data_ptr(), ws.numel() * 4, s)
+        f.render_bwd(self._activated(), gimg, (self.g["mean"], self.g_act["scale"], self.g["quat"],
+                                               self.g_act["opacity"], self.g_act["intensity"]))
+        B.xg_activate_bwd(self._raw, self.g_act["scale"].data_ptr(), self.g_act["opacity"].data_ptr(),
+                          self.g_act["intensity"].data_ptr(), self.g["log_scale"].data_ptr(),
+                          self.g["opacity_logit"].data_ptr(), self.g["features"].data_ptr(), s)
+        B.xg_adam_step(self._groups, self.step_count.data_ptr(), self.cfg.beta1, self.cfg.beta2, self.cfg.eps, s)
+
+    def capture(self) -> None:
+        """Record one CUDA graph per view group (each group is stepped once while warming up)."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for gi in range(len(self.groups)):
+                self._step_calls(gi)
+        torch.cuda.current_stream().wait_stream(side)
+        self.check_capacity()
+        for gi in range(len(self.groups)):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self._step_calls(gi)
+            self.graphs[gi] = g
+
+    def check_capacity(self) -> bool:
+        """True when every frame's pairs fitted (synchronises); frames that overflowed are
+        rebuilt with more room and their graphs dropped."""
+        ok = True
+        for gi, f in enumerate(self.frames):
+            st = f.status()
+            if st.code == B.XG_ERR_CAPACITY:
+                ok = False
+                self.frames[gi] = Frame(self.n, f.views, self.frame_cfg, int(st.pairs * self.capacity_margin),
+                                        self.device)
+                self.graphs[gi] = None
+            elif st.code != B.XG_OK:
+                raise B.XgError(st.code, "training step")
+        return ok
+
+    # ---- public -------------------------------------------------------------------------
+    def step(self, t: int) -> None:
+        gi = t % len(self.groups)
+        if self.graphs[gi] is None:
+            self._step_calls(gi)
+        else:
+            self.graphs[gi].replay()
+
+    def train(self, steps: int, check_every: int = 500) -> None:
+        for t in range(steps):
+            self.step(t)
+            if check_every and (t + 1) % check_every == 0 and not self.check_capacity():
+                self.capture()
+
+    @torch.no_grad()
+    def render(self, views) -> torch.Tensor:
+        s = _stream_handle()
+        B.xg_activate(self._raw, self.act["scale"].data_ptr(), self.act["opacity"].data_ptr(),
+                      self.act["intensity"].data_ptr(), s)
+        out = []
+        for i in range(0, len(views), self.cfg.views_per_step):
+            vs = views[i:i + self.cfg.views_per_step]
+            cap = size_pairs(self.n, vs, self.frame_cfg, self._activated(), margin=1.1)
+            f = Frame(self.n, vs, self.frame_cfg, cap, self.device)
+            img = torch.empty(len(vs), f.H, f.W, device=self.device)
+            f.project(*self._activated())
+            f.bin_sort()
+            f.render_fwd(img)
+            out.append(img)
+        return torch.cat(out)
+
+    def psnr(self, views, targets: torch.Tensor) -> np.ndarray:
+        img = self.render(views)
+        out = torch.empty(len(views), device=self.device)
+        B.xg_psnr(img.data_ptr(), targets.data_ptr(), len(views), img[0].numel(), out.data_ptr(), _stream_handle())
+        return out.cpu().numpy()
+
+
+def config3(n: int, W: int, seed_id: int = 3):
+    """Scan of the paper's protocol (Sec. 4.1): 100 projections over 0-180 degrees, the even
+    ones for training, the odd ones held out; cuboid-uniform initial Gaussians."""
+    side = synth.scene_side_mm(W)
+    views = synth.circular_views(100, W, W, span_rad=math.pi)
+    ph = synth.ellipsoid_phantom(10, side, synth.rng(seed_id, 1))
+    targets = synth.phantom_targets(ph, views)
+    g = synth.gaussians(n, side, synth.rng(seed_id, 0))
+    return side, views[0::2], targets[0::2], views[1::2], targets[1::2], g
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--gaussians", type=int, default=200_000)
+    ap.add_argument("--detector", type=int, default=512)
+    ap.add_argument("--views-per-step", type=int, default=8)
+    ap.add_argument("--tile", default="16x16:128:2")
+    args = ap.parse_args()
+    tw_th, b, p = args.tile.split(":")
+    tw, th = (int(x) for x in tw_th.split("x"))
+    fcfg = FrameConfig(tw, th, batch=int(b), pixels_per_thread=int(p))
+    side, tr_v, tr_t, te_v, te_t, g = config3(args.gaussians, args.detector)
+    cfg = TrainConfig(views_per_step=args.views_per_step, position_scale=side, decay_steps=args.steps)
+    raw = raw_from_activated(g, cfg.n_features, synth.rng(3, 2))
+    dev = torch.device("cuda")
+    tr_t, te_t = torch.from_numpy(tr_t).to(dev), torch.from_numpy(te_t).to(dev)
+    trainer = Trainer(raw, tr_v, tr_t, cfg, fcfg)
+    psnr0 = trainer.psnr(te_v, te_t)
+    trainer.capture()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    trainer.train(args.steps)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    loss = trainer.loss.cpu().numpy()
+    psnr1 = trainer.psnr(te_v, te_t)
+    print(json.dumps({"workload": "config3", "gaussians": args.gaussians, "detector": args.detector,
+                      "train_views": len(tr_v), "test_views": len(te_v), "views_per_step": args.views_per_step,
+                      "steps": args.steps, "wall_s": wall, "steps_per_s": args.steps / wall,
+                      "last_loss": float(loss[0]), "last_l1": float(loss[1]), "last_ssim": float(loss[2]),
+                      "heldout_psnr_before": float(psnr0.mean()), "heldout_psnr_after": float(psnr1.mean()),
+                      "tile": args.tile}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

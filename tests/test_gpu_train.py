@@ -1,0 +1,185 @@
+"""Parity of the training-step calls (activations, L1 + SSIM loss, Adam, PSNR) with the FP64
+training oracle, of their composition with the rasterizer's backward pass, and a short
+graph-replayed training run that must lower the loss and raise held-out PSNR."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from oracle import train64 as T  # noqa: E402
+from paper_2403_04116_gb300 import binding as B  # noqa: E402
+from paper_2403_04116_gb300 import synth  # noqa: E402
+from paper_2403_04116_gb300.render import Frame, FrameConfig, _stream_handle  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2403_04116_gb300 import build
+    build.build()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def _raw(gen, n, nf):
+    ls = gen.uniform(-2, 1, size=(3, n))
+    ol = gen.normal(0, 2, size=n)
+    f = gen.normal(0, 1, size=(nf, n))
+    lam = gen.uniform(0.5, 1.5, size=nf)
+    return ls, ol, f, lam
+
+
+def test_activations_match_oracle():
+    gen = np.random.default_rng(0)
+    n, nf = 5000, 16
+    ls, ol, f, lam = _raw(gen, n, nf)
+    d = [_dev(a) for a in (ls, ol, f, lam)]
+    raw = B.XgRawGaussians(d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr(), nf, 0, n)
+    sc, op, it = torch.empty(3, n, device="cuda"), torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+    B.xg_activate(raw, sc.data_ptr(), op.data_ptr(), it.data_ptr(), _stream_handle())
+    # the oracle runs on the float32 inputs the kernel saw
+    ws, wo, wi = T.activate64(*(a.astype(np.float32) for a in (ls, ol, f, lam)))
+    np.testing.assert_allclose(sc.cpu().numpy(), ws, rtol=2e-6)
+    np.testing.assert_allclose(op.cpu().numpy(), wo, rtol=2e-6, atol=1e-7)
+    np.testing.assert_allclose(it.cpu().numpy(), wi, rtol=5e-6, atol=1e-7)
+    gs, go, gi = gen.normal(size=(3, n)), gen.normal(size=n), gen.normal(size=n)
+    out = [torch.empty(3, n, device="cuda"), torch.empty(n, device="cuda"), torch.empty(nf, n, device="cuda")]
+    gd = [_dev(a) for a in (gs, go, gi)]
+    B.xg_activate_bwd(raw, gd[0].data_ptr(), gd[1].data_ptr(), gd[2].data_ptr(), out[0].data_ptr(),
+                      out[1].data_ptr(), out[2].data_ptr(), _stream_handle())
+    want = T.activate_bwd64(*(a.astype(np.float32) for a in (ls, ol, f, lam)), *(a.astype(np.float32) for a in
+                                                                                 (gs, go, gi)))
+    for got, w in zip(out, want):
+        np.testing.assert_allclose(got.cpu().numpy(), w, rtol=1e-5, atol=1e-6 * np.abs(w).max())
+
+
+@pytest.mark.parametrize("V,H,W", [(2, 37, 53), (1, 128, 128), (3, 11, 9)])
+def test_l1_ssim_loss_matches_oracle(V, H, W):
+    gen = np.random.default_rng(V * 100 + H)
+    y = gen.uniform(0, 1, size=(V, H, W)).astype(np.float32)
+    x = np.clip(y + gen.normal(0, 0.1, size=y.shape), 0, 1).astype(np.float32)
+    xd, yd = _dev(x), _dev(y)
+    grad = torch.empty_like(xd)
+    loss = torch.empty(3, device="cuda")
+    nb = B.xg_loss_workspace_bytes(V, W, H)
+    ws = torch.empty(nb // 4 + 4, device="cuda")
+    B.xg_loss_l1_ssim(xd.data_ptr(), yd.data_ptr(), V, W, H, 0.2, grad.data_ptr(), loss.data_ptr(), ws.data_ptr(),
+                      nb, _stream_handle())
+    ref = T.loss_l1_ssim64(x, y, 0.2)
+    got = loss.cpu().numpy()
+    assert got[0] == pytest.approx(ref["loss"], abs=2e-6)
+    assert got[1] == pytest.approx(ref["l1"], abs=2e-6)
+    assert got[2] == pytest.approx(ref["ssim"], abs=2e-6)
+    g = grad.cpu().numpy()
+    np.testing.assert_allclose(g, ref["grad"], rtol=0, atol=1e-4 * np.abs(ref["grad"]).max())
+
+
+def test_adam_matches_oracle_over_steps():
+    gen = np.random.default_rng(5)
+    sizes = [1000, 37, 4096]
+    ps = [gen.normal(size=k) for k in sizes]
+    dev_p = [_dev(p) for p in ps]
+    dev_g = [torch.empty_like(p) for p in dev_p]
+    dev_m = [torch.zeros_like(p) for p in dev_p]
+    dev_v = [torch.zeros_like(p) for p in dev_p]
+    cfg = [(1e-2, 0.0, 0), (3e-3, 0.0, 0), (1.9e-4, 1.9e-6, 4)]
+    groups = [B.XgAdamGroup(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), p.numel(), lr, lf, ds, 0)
+              for p, g, m, v, (lr, lf, ds) in zip(dev_p, dev_g, dev_m, dev_v, cfg)]
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ref = [(p.astype(np.float32).astype(np.float64), np.zeros_like(p), np.zeros_like(p)) for p in ps]
+    for t in range(1, 7):
+        grads = [gen.normal(size=k).astype(np.float32) for k in sizes]
+        for d, gv in zip(dev_g, grads):
+            d.copy_(torch.from_numpy(gv))
+        B.xg_adam_step(groups, step.data_ptr(), 0.9, 0.999, 1e-15, _stream_handle())
+        ref = [T.adam64(p, gv, m, v, t, lr, lr_final=lf or None, decay_steps=ds)
+               for (p, m, v), gv, (lr, lf, ds) in zip(ref, grads, cfg)]
+    assert int(step.item()) == 6
+    for d, (p, _, _) in zip(dev_p, ref):
+        np.testing.assert_allclose(d.cpu().numpy(), p, rtol=1e-5, atol=1e-7)
+
+
+def test_psnr_matches_oracle():
+    gen = np.random.default_rng(6)
+    x = gen.uniform(0, 1, size=(4, 33, 17)).astype(np.float32)
+    y = np.clip(x + gen.normal(0, 0.05, size=x.shape), 0, 1).astype(np.float32)
+    out = torch.empty(4, device="cuda")
+    xd, yd = _dev(x), _dev(y)  # keep the tensors alive while the kernel reads them
+    B.xg_psnr(xd.data_ptr(), yd.data_ptr(), 4, 33 * 17, out.data_ptr(), _stream_handle())
+    np.testing.assert_allclose(out.cpu().numpy(), T.psnr64(x, y), atol=1e-3)
+
+
+def test_activation_backward_composes_with_render_backward():
+    """raw parameters -> activate -> render -> the oracle's loss gradient -> render_bwd ->
+    activate_bwd, against the FP64 chain on the same upstream gradient."""
+    gen = np.random.default_rng(7)
+    W = H = 48
+    n, nf = 1500, 4
+    side = synth.scene_side_mm(W)
+    g = synth.gaussians(n, side, synth.rng(50, 0))
+    lam = gen.uniform(0.5, 1.5, size=nf).astype(np.float32)
+    ls = np.log(g["scale"]).astype(np.float32)
+    ol = gen.normal(-1.0, 0.5, size=n).astype(np.float32)
+    f = gen.normal(0, 0.5, size=(nf, n)).astype(np.float32)
+    views = synth.circular_views(2, W, H, first_rad=0.4)
+    d_ls, d_ol, d_f, d_lam = (_dev(a) for a in (ls, ol, f, lam))
+    raw = B.XgRawGaussians(d_ls.data_ptr(), d_ol.data_ptr(), d_f.data_ptr(), d_lam.data_ptr(), nf, 0, n)
+    sc, op, it = torch.empty(3, n, device="cuda"), torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+    B.xg_activate(raw, sc.data_ptr(), op.data_ptr(), it.data_ptr(), _stream_handle())
+    mean, quat = _dev(g["mean"]), _dev(g["quat"])
+    act = (mean, sc, quat, op, it)
+    fr = Frame(n, views, FrameConfig(16, 16), 1 << 18)
+    fr.project(*act)
+    fr.bin_sort()
+    img = torch.empty(2, H, W, device="cuda")
+    fr.render_fwd(img)
+    # FP64 side: activated parameters from the same float32 raw values
+    s64, o64, i64 = T.activate64(ls, ol, f, lam)
+    g64 = {"mean": g["mean"].astype(np.float64), "scale": s64, "quat": g["quat"].astype(np.float64),
+           "opacity": o64, "intensity": i64}
+    target = gen.uniform(0, 0.5, size=(2, H, W))
+    imgs64, Gs = [], []
+    for v, view in enumerate(views):
+        r = oracle.render64(g64, view)
+        imgs64.append(r["image"])
+        Gs.append(np.where(r["ambiguous"] != 0, 0.0, 1.0))
+    loss = T.loss_l1_ssim64(np.stack(imgs64), target, 0.2)
+    G = loss["grad"] * np.stack(Gs) * 1e4  # scaled so that the gradients sit above the absolute floor
+    ref = None
+    for v, view in enumerate(views):
+        ref = oracle.grad64(g64, view, G[v], out=ref)
+    ga = [torch.empty_like(t) for t in act]
+    fr.render_bwd(act, _dev(G), ga)
+    out = [torch.empty(3, n, device="cuda"), torch.empty(n, device="cuda"), torch.empty(nf, n, device="cuda")]
+    B.xg_activate_bwd(raw, ga[1].data_ptr(), ga[3].data_ptr(), ga[4].data_ptr(), out[0].data_ptr(),
+                      out[1].data_ptr(), out[2].data_ptr(), _stream_handle())
+    want = T.activate_bwd64(ls, ol, f, lam, ref["scale"], ref["opacity"], ref["intensity"])
+    mags = T.activate_bwd64(ls, ol, f, lam, ref["mag"]["scale"], ref["mag"]["opacity"], ref["mag"]["intensity"])
+    for got, w, mg in zip(out, want, mags):
+        gv = got.cpu().numpy().astype(np.float64)
+        bad = np.abs(gv - w) > 1e-3 * np.abs(w) + 1e-6 + 3e-5 * np.abs(mg)
+        assert not bad.any(), (gv[bad][:4], w[bad][:4])
+    assert np.abs(want[2]).max() > 1e-3
+
+
+def test_short_training_run_improves_heldout_psnr():
+    from paper_2403_04116_gb300.train import TrainConfig, Trainer, config3, raw_from_activated
+    side, tr_v, tr_t, te_v, te_t, g = config3(20_000, 128, seed_id=60)
+    cfg = TrainConfig(views_per_step=8, position_scale=side, decay_steps=300)
+    raw = raw_from_activated(g, cfg.n_features, np.random.default_rng(1))
+    tr = Trainer(raw, tr_v, torch.from_numpy(tr_t).cuda(), cfg, FrameConfig(16, 16))
+    te = torch.from_numpy(te_t).cuda()
+    before = tr.psnr(te_v, te).mean()
+    tr.capture()
+    tr.train(300, check_every=100)
+    torch.cuda.synchronize()
+    after = tr.psnr(te_v, te).mean()
+    assert math.isfinite(after) and after > before + 1.0, (before, after)
