@@ -10,6 +10,10 @@ backward pass to every Gaussian parameter.  Throughput = views processed per sec
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+``--workload scan360`` times forward projection of a 360-view scan (1,000,000 Gaussians,
+1024x1024 detector, views 1 degree apart), rendered a few views per pass through one
+workspace with every pass captured in one CUDA graph.
+
 Under torchrun (N > 1) each rank runs its own replica of the workload (weak scaling, no
 collective); rank 0 prints one JSON line.  ``--impl reference`` times the CPU oracle on
 the host cores on a bounded sample of the same workload.
@@ -38,7 +42,10 @@ WORKLOADS = {
     "train50k": dict(n=50_000, views=50, W=256, H=256, tile=(16, 16), cid=1),
     "fwd10k": dict(n=10_000, views=1, W=128, H=128, tile=(16, 16), cid=0),
     "batch100k": dict(n=100_000, views=100, W=256, H=256, tile=(16, 16), cid=2),
+    # forward only: a 360-view scan at 1 degree spacing, rendered in passes inside one graph
+    "scan360": dict(n=1_000_000, views=360, W=1024, H=1024, tile=(16, 16), cid=4, forward_only=True),
 }
+METRIC_SCAN = "X-ray projections/s fwd (1M Gaussians, 1024², 360 views) and % of roofline"
 METRIC = "X-ray projections/s fwd and fwd+bwd (50k Gaussians, 256²) and % of roofline"
 
 # FP32 lane instructions charged per evaluated (pixel, list entry) pair of the compositing
@@ -68,7 +75,8 @@ def _args():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the one-view-per-launch form")
     ap.add_argument("--config", default=None, help="tile and kernel shape TWxTH:batch:pixels_per_thread "
-                                                    "(e.g. 16x16:128:2) instead of autotuning")
+                                                    "(e.g. 16x16:128:2; scan workloads add :views_per_pass) "
+                                                    "instead of autotuning")
     return ap.parse_args()
 
 
@@ -92,6 +100,10 @@ def _workload(name: str):
 
 
 def _config(name: str, w: dict, n_gpus: int) -> dict:
+    if w.get("forward_only"):
+        return {"workload": name, "gaussians": w["n"], "views": w["views"], "detector": [w["W"], w["H"]],
+                "tile": list(w["tile"]), "step": "forward projection of every view",
+                "l2": "inputs larger than L2 (pairs of each pass: several GB)", "parallelism": f"replicas x{n_gpus}"}
     return {"workload": name, "gaussians": w["n"], "views": w["views"], "detector": [w["W"], w["H"]],
             "tile": list(w["tile"]), "loss": "L1 vs FP64 ellipsoid-phantom projections",
             "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{n_gpus}"}
@@ -178,21 +190,25 @@ def _source_sha(kernel_file: str) -> str:
 # ------------------------------------------------------------------------------------------
 
 def cpu_oracle_rate(name: str, target_seconds: float = 12.0) -> dict:
-    """Oracle forward + gradient (FP64, all host cores) on a bounded sample of the workload:
-    whole views while one view takes under ``target_seconds``, else a random pixel sample
-    of one view; projections/s scaled from the sample."""
+    """Oracle forward + gradient (forward only for a forward-only workload; FP64, all host
+    cores) on a bounded sample of the workload: whole views while one view takes under
+    ``target_seconds``, else a random pixel sample of one view; projections/s scaled from
+    the sample."""
     import oracle
     from paper_2403_04116_gb300 import synth
     w, g, views, ph = _workload(name)
+    fwd_only = bool(w.get("forward_only"))
     npx = views[0].width * views[0].height
     gen = np.random.default_rng(7)
 
     def run(view_ids, pix=None) -> float:
-        tg = synth.phantom_targets(ph, [views[i] for i in view_ids])
+        tg = None if fwd_only else synth.phantom_targets(ph, [views[i] for i in view_ids])
         t0 = time.perf_counter()
         for k, i in enumerate(view_ids):
             v = views[i]
             r = oracle.render64(g, v, pixels=pix)
+            if fwd_only:
+                continue
             G = np.sign(np.nan_to_num(r["image"]) - tg[k]) / npx
             if pix is not None:
                 mask = np.zeros(npx, bool)
@@ -201,7 +217,11 @@ def cpu_oracle_rate(name: str, target_seconds: float = 12.0) -> dict:
             oracle.grad64(g, v, G, pixels=pix)
         return time.perf_counter() - t0
 
-    t1 = run([0])
+    if fwd_only:  # a view of the workload takes minutes: time a 64-pixel probe first
+        probe = np.sort(gen.choice(npx, size=64, replace=False)).astype(np.int32)
+        t1 = run([0], probe) * npx / 64
+    else:
+        t1 = run([0])
     if t1 >= target_seconds:
         p = max(256, int(npx * target_seconds / t1))
         pix = np.sort(gen.choice(npx, size=p, replace=False)).astype(np.int32)
@@ -213,8 +233,9 @@ def cpu_oracle_rate(name: str, target_seconds: float = 12.0) -> dict:
         t = run(ids)
         rate, sample = len(ids) / t, f"{len(ids)} of {w['views']} views, all pixels, {t:.1f} s"
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    what = "forward" if fwd_only else "forward + gradient (L1 vs phantom)"
     return {"value": rate, "unit": "projections/s", "cores": threads, "kind": "oracle",
-            "sample": f"FP64 oracle forward + gradient (L1 vs phantom), {sample}"}
+            "sample": f"FP64 oracle {what}, {sample}"}
 
 
 def run_reference(args) -> None:
@@ -227,7 +248,8 @@ def run_reference(args) -> None:
         cpu_oracle_rate(args.workload, target_seconds=0.5)
     rates = [cpu_oracle_rate(args.workload, target_seconds=per_step) for _ in range(args.steps)]
     value = statistics.median(r["value"] for r in rates)
-    line = {"metric": METRIC, "value": value, "unit": "projections/s", "n_gpus": args.gpus, "steps": args.steps,
+    metric = METRIC_SCAN if w.get("forward_only") else METRIC
+    line = {"metric": metric, "value": value, "unit": "projections/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * w["views"] / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(args.workload, w, 1), "impl": "reference",
@@ -446,10 +468,171 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def _algo_bytes(kernel: str, n: int, VN: int, M: int, entry_passes: int, tile_passes: int) -> float:
+    """Algorithmic DRAM bytes of one step's launches of a memory-bound kernel (each input
+    read once, each output written once)."""
+    return {"k_radix_scatter": 24 * VN * entry_passes + 16 * M * tile_passes, "k_project": 48 * n + 72 * VN,
+            "k_emit": 20 * VN + 8 * M, "k_project_bwd": 32 * VN + 56 * n, "k_ranges": 4 * M,
+            "k_radix_hist": 4 * VN * entry_passes + 4 * M * tile_passes}.get(kernel, 0)
+
+
+def run_scan(args) -> None:
+    """Forward projection of every view of the scan workload, captured in one graph."""
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_2403_04116_gb300 import binding as B
+    from paper_2403_04116_gb300.batch import autotune_scan, build_scan
+    from paper_2403_04116_gb300.render import FrameConfig
+
+    B.lib(build_if_missing=True)
+    w, g, views, _ = _workload(args.workload)
+    V, H, W, n = w["views"], w["H"], w["W"], w["n"]
+    names = ("mean", "scale", "quat", "opacity", "intensity")
+    dev = tuple(torch.from_numpy(g[k]).cuda() for k in names)
+    if args.config:
+        parts = args.config.split(":")
+        tw_s, th_s = parts[0].split("x")
+        cfg = FrameConfig(int(tw_s), int(th_s), batch=int(parts[1]), pixels_per_thread=int(parts[2]))
+        vpp = int(parts[3]) if len(parts) > 3 else 16
+    elif args.autotune:
+        cfg, vpp, _ = autotune_scan(n, views, dev)
+    else:
+        cfg, vpp = FrameConfig(16, 16, batch=128, pixels_per_thread=2), 16
+    scan = build_scan(n, views, cfg, vpp, dev)
+    frame = scan.frame
+
+    def timed(fn, k: int) -> float:
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        barrier()
+        torch.cuda.synchronize()
+        for i in range(k):
+            starts[i].record()
+            fn()
+            ends[i].record()
+        torch.cuda.synchronize()
+        barrier()
+        return sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+    for _ in range(args.warmup):
+        scan.replay()
+    torch.cuda.synchronize()
+    stats = scan.statuses()
+    if any(c != B.XG_OK for c, _, _, _ in stats):
+        raise RuntimeError(f"pass status {[B.xg_status_str(c) for c, _, _, _ in stats]}")
+    with ClockSampler(local) as clocks:
+        ms_total = timed(scan.replay, args.steps)
+    clock_info = clocks.summary()
+
+    # per-kernel times: the same passes launched on the stream with event timing on
+    timing_steps = 1  # the library keeps up to 2048 timed launches between reads
+    frame.read_timing()
+    frame.set_timing(True)
+    ms_stream = timed(scan._run, timing_steps)
+    frame.set_timing(False)
+    kernels = frame.read_timing()
+    stats = scan.statuses()
+    M = sum(p for _, p, _, _ in stats)
+    f_eval = sum(e for _, _, e, _ in stats)
+    f_contrib = sum(c for _, _, _, c in stats)
+
+    ms_total, ms_stream = reduce_max([ms_total, ms_stream], device="cuda")
+    value = throughput(V, args.steps, world, ms_total)
+    peaks = _peaks()
+    alu_peak = SMS * FP32_LANES * peaks["sm_max_mhz"] * 1e6 / 1e12
+    VN = V * n
+    entry_passes = 4 + ((max(1, vpp - 1).bit_length() + 7) // 8)
+    tile_passes = frame.layout.sort_passes - entry_passes
+    stages = {}
+    for k, (nl, ms) in sorted(kernels.items()):
+        if k == "memset":
+            continue
+        ms /= timing_steps
+        if k == "k_render_fwd":
+            ach = (FWD_OPS_EVAL * f_eval + FWD_OPS_CONTRIB * f_contrib) / (ms * 1e-3) / 1e12
+            stages[k] = {"bound": "alu", "ms": ms, "achieved": ach, "unit": "TFP32op/s", "frac": ach / alu_peak}
+        else:
+            b = _algo_bytes(k, n * len(scan.starts), VN, M, entry_passes, tile_passes)
+            if b:
+                ach = b / (ms * 1e-3) / 1e9
+                stages[k] = {"bound": "hbm", "ms": ms, "achieved": ach, "unit": "GB/s", "frac": ach / peaks["hbm_gbs"]}
+            else:
+                stages[k] = {"ms": ms}
+    dom = max((k for k in stages if "frac" in stages[k]), key=lambda k: stages[k]["ms"])
+    launches = kernels[dom][0] / timing_steps
+    d = stages[dom]
+    roof = {"bound": d["bound"], "achieved": d["achieved"],
+            "peak": alu_peak if d["bound"] == "alu" else peaks["hbm_gbs"], "unit": d["unit"], "frac": d["frac"],
+            "traffic": None, "kernel": dom, "avg_launch_ms": d["ms"] / launches,
+            "peak_source": (f"{SMS} SMs x {FP32_LANES} FP32 lanes x {peaks['sm_max_mhz']:.0f} MHz"
+                            if d["bound"] == "alu" else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")}
+    gpu_launches = int(round(sum(nl for k, (nl, _) in kernels.items() if k != "memset") / timing_steps
+                             + len(scan.starts))) * args.steps  # + one status copy per pass
+
+    # end to end: pinned host Gaussians in, every projection back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = tuple(torch.from_numpy(g[k]).pin_memory() for k in names)
+        out = torch.empty(scan.image.shape, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            scan.load(tuple(t.cuda(non_blocking=True) for t in host))
+            scan.replay()
+            out.copy_(scan.image, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        k = max(1, min(args.steps, 5))
+        for _ in range(k):
+            e2e_step()
+        barrier()
+        (el,) = reduce_max([time.perf_counter() - t0], device="cuda")
+        e2e = {"value": throughput(V, k, world, 1000.0 * el), "unit": "projections/s",
+               "h2d_bytes_per_step": sum(t.numel() * 4 for t in host), "d2h_bytes_per_step": out.numel() * 4,
+               "steps": k, "path": "GraphedScan.load + replay, images copied to pinned host memory"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate(args.workload)
+    if rank == 0:
+        cfg_line = _config(args.workload, w, world)
+        cfg_line.update({"tile": [cfg.tile_w, cfg.tile_h], "staging_batch": cfg.batch,
+                         "pixels_per_thread": cfg.pixels_per_thread, "views_per_pass": vpp,
+                         "passes": len(scan.starts), "graph": "every pass in one CUDA graph",
+                         "autotuned": bool(args.autotune and not args.config)})
+        line = {"metric": METRIC_SCAN, "value": value, "unit": "projections/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": cfg_line, "stream_launched": {"ms_per_step": ms_stream / timing_steps},
+                "clocks": clock_info, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
+                "cpu_baseline": cpu, "pairs": int(M), "pairs_per_pass_max": int(max(p for _, p, _, _ in stats)),
+                "work": {"fwd_evaluated": int(f_eval), "fwd_contrib": int(f_contrib)}, "stages": stages,
+                "kernels_ms_per_step": {k: round(v[1] / timing_steps, 4) for k, v in sorted(kernels.items())}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif WORKLOADS[args.workload].get("forward_only"):
+        run_scan(args)
     else:
         run_ours(args)
 

@@ -90,8 +90,12 @@ typedef struct {
  * compositing thread owns, 1, 2 or 4 (0 selects 2), with tile_h a multiple of
  * 4 * pixels_per_thread and tile_w * tile_h <= 512 * pixels_per_thread; near_mm > 0;
  * batch: Gaussians staged in shared memory per round of the compositing kernels, one of
- * 64, 128, 256 (0 selects 256); 1 <= pair_capacity < 2^31.  Tile shape, batch and pixels
- * per thread change speed only: images and gradients do not depend on them. */
+ * 64, 128, 256 (0 selects 256); 1 <= pair_capacity < 2^31 (pairs of one pass).
+ * views_per_pass >= 0: views the per-pass arrays hold; 0, or a value >= the frame's view
+ * count, renders every view in one pass.  A smaller value renders a long scan in passes
+ * through one workspace (see xg_frame_select_views).  Tile shape, batch, pixels per thread
+ * and views per pass change speed and memory only: images and gradients do not depend on
+ * them. */
 typedef struct {
   int32_t tile_w;
   int32_t tile_h;
@@ -99,7 +103,7 @@ typedef struct {
   int32_t batch;
   int64_t pair_capacity;
   int32_t pixels_per_thread;
-  int32_t reserved; /* set to 0 */
+  int32_t views_per_pass;
 } xg_config;
 
 /* Device-side status of a frame, read back by xg_frame_read_status. */
@@ -115,7 +119,8 @@ typedef struct {
 } xg_device_status;
 
 /* Byte offsets, inside the workspace, of the frame's intermediate arrays (for inspection).
- * V views, n Gaussians, T tiles per view, cap = pair_capacity:
+ * V views of the current pass, n Gaussians, T tiles per view, cap = pair_capacity; the
+ * camera table (at `cameras`) holds every view of the frame:
  *   records    float[V*n][8]  (u_x, u_y, conic a, b, c, opacity, intensity, 0); u centred
  *                             on the principal point; zero where the Gaussian touches no tile
  *   depth      float[V*n]     t_z (0 where it touches no tile)
@@ -155,6 +160,15 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
                           void* workspace, size_t workspace_bytes, void* stream);
 void xg_frame_destroy(xg_frame* frame);
 
+/* Select the views of the next pass: views first_view .. first_view + V - 1 of the frame,
+ * V = min(views_per_pass, n_views - first_view), written to *n_selected (may be NULL).
+ * A new frame has views 0 .. views_per_pass - 1 selected.  The selection is host state
+ * only: it enqueues nothing, so it can sit between graph-captured calls, and it governs
+ * the calls made after it (their view index v, image planes and arrays run over the V
+ * selected views; xg_render_bwd sums over them only).  Calls already enqueued are not
+ * affected.  Errors: XG_ERR_INVALID_ARG (first_view outside [0, n_views)). */
+xg_status xg_frame_select_views(xg_frame* frame, int32_t first_view, int32_t* n_selected);
+
 /* Project every Gaussian into every view of the frame (Eq. 7-9 and the 2-D covariance of
  * Sec. 3.2: t = M_ext mu, u = M_int t, Sigma' = J W Sigma W^T J^T, Sigma'' its top-left
  * block, Sigma = R S S^T R^T of Sec. 3.1) and find the tiles its footprint touches.  Writes
@@ -187,6 +201,12 @@ xg_status xg_render_bwd(xg_frame* frame, const xg_gaussians* g, const float* gra
 /* Wait for `stream`, then copy the frame's device status to *out.  Returns XG_OK if the
  * copy worked (the device-side code is in out->code), else XG_ERR_CUDA. */
 xg_status xg_frame_read_status(const xg_frame* frame, xg_device_status* out, void* stream);
+
+/* Enqueue on `stream` a copy of the frame's device status, in the xg_device_status layout,
+ * to device memory `out` (8-byte aligned, caller-owned).  It does not synchronise, so it
+ * can be graph-captured, e.g. to keep the status of every pass of a scan rendered in
+ * passes.  Errors: XG_ERR_INVALID_ARG, XG_ERR_CUDA. */
+xg_status xg_frame_copy_status(const xg_frame* frame, xg_device_status* out, void* stream);
 
 /* Byte offsets of the frame's arrays inside its workspace. */
 xg_status xg_frame_layout(const xg_frame* frame, xg_layout* out);

@@ -3,7 +3,9 @@ CUDA graph, plus the tile-shape / staging-batch autotuner.
 
 ``GraphedStep`` captures project -> bin + sort -> composite -> L1 loss -> backward for all
 views of a frame once, then replays it; only tensor contents change between replays (the
-Gaussian parameters and the targets are copied into its input buffers).  ``PlainSteps``
+Gaussian parameters and the targets are copied into its input buffers).  ``GraphedScan``
+renders a scan too large for one pass (hundreds of views of a dense scene) in passes of a
+few views through one workspace, every pass recorded in the same graph.  ``PlainSteps``
 is the reference form: one frame per view and one launch sequence per view, no graph.
 Both run the same kernels, so their images and gradients agree (gradients up to the order
 of float atomics).
@@ -85,6 +87,69 @@ class GraphedStep:
         self.graph.replay()
 
 
+class GraphedScan:
+    """Forward projections of every view of a scan, ``views_per_pass`` views at a time
+    through one frame, all passes captured in one CUDA graph.
+
+    The device status word of each pass (pair count, capacity overflow, work counters) is
+    copied into ``pass_status`` inside the graph, so one read after a replay covers them all.
+    """
+
+    def __init__(self, n: int, views, cfg: FrameConfig, pair_capacity: int, views_per_pass: int, device="cuda"):
+        self.frame = Frame(n, views, cfg, pair_capacity, device, views_per_pass=views_per_pass)
+        f = self.frame
+        self.starts = list(range(0, f.n_scan, f.views_per_pass))
+        self.inputs = (torch.zeros(3, n, device=device), torch.ones(3, n, device=device),
+                       torch.zeros(4, n, device=device), torch.zeros(n, device=device), torch.zeros(n, device=device))
+        self.inputs[2][0] = 1.0
+        self.image = torch.empty(f.n_scan, f.H, f.W, device=device)
+        self.pass_status = torch.zeros(len(self.starts), 7, dtype=torch.int64, device=device)
+        self.graph = None
+
+    def _run(self) -> None:
+        f = self.frame
+        for i, first in enumerate(self.starts):
+            V = f.select(first)
+            f.project(*self.inputs)
+            f.bin_sort()
+            f.render_fwd(self.image[first:first + V])
+            f.copy_status(self.pass_status[i])
+        f.select(0)
+
+    def load(self, gaussians: tuple) -> None:
+        for dst, src in zip(self.inputs, gaussians):
+            dst.copy_(src, non_blocking=True)
+
+    def statuses(self) -> list:
+        """Per-pass (code, pairs, fwd_evaluated, fwd_contrib) of the latest run (synchronises)."""
+        out = []
+        for row in self.pass_status.cpu().numpy():
+            st = B.XgDeviceStatus.from_buffer_copy(row.tobytes())
+            out.append((st.code, st.pairs, st.fwd_evaluated, st.fwd_contrib))
+        return out
+
+    def max_pairs(self) -> int:
+        """Largest pass of one uncaptured run (synchronises); for sizing the capacity."""
+        self._run()
+        return max(p for _, p, _, _ in self.statuses())
+
+    def capture(self) -> None:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self._run()
+        torch.cuda.current_stream().wait_stream(side)
+        bad = [c for c, _, _, _ in self.statuses() if c != B.XG_OK]
+        if bad:
+            raise B.XgError(bad[0], "graph warm-up")
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._run()
+
+    def replay(self) -> None:
+        self.graph.replay()
+
+
 class PlainSteps:
     """The same step as one frame and one launch sequence per view (no graph)."""
 
@@ -122,6 +187,64 @@ class TuneResult:
 
     def config(self) -> FrameConfig:
         return FrameConfig(self.tile_w, self.tile_h, batch=self.batch, pixels_per_thread=self.pixels_per_thread)
+
+
+def build_scan(n: int, views, cfg: FrameConfig, views_per_pass: int, gaussians: tuple,
+               margin: float = 1.05) -> GraphedScan:
+    """A GraphedScan whose pair capacity fits the largest pass of these Gaussians (sized by
+    uncaptured runs, which synchronise), loaded with them and captured."""
+    cap = size_pairs(n, views[:views_per_pass], cfg, gaussians, margin=1.25)
+    while True:
+        scan = GraphedScan(n, views, cfg, cap, views_per_pass)
+        scan.load(gaussians)
+        need = scan.max_pairs()
+        if need <= cap:
+            break
+        cap = int(need * margin) + 4096
+        del scan
+    scan.capture()
+    return scan
+
+
+def autotune_scan(n: int, views, gaussians: tuple, tiles=((16, 16), (32, 16)), passes=(8, 16, 30),
+                  shapes=((128, 2), (256, 2), (256, 1)), reps: int = 3) -> tuple:
+    """Tile shape and views per pass, then staging batch and pixels per thread, with the
+    fastest replay of the captured scan; returns (FrameConfig, views_per_pass, ms)."""
+    def time_scan(cfg, vpp):
+        scan = build_scan(n, views, cfg, vpp, gaussians)
+        scan.replay()
+        times = []
+        for _ in range(reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            scan.replay()
+            e.record()
+            torch.cuda.synchronize()
+            times.append(s.elapsed_time(e))
+        del scan
+        torch.cuda.empty_cache()
+        return statistics.median(times)
+
+    best = None
+    b0, p0 = shapes[0]
+    for tw, th in tiles:
+        for vpp in passes:
+            tiles_per_view = -(-views[0].width // tw) * -(-views[0].height // th)
+            if vpp * tiles_per_view > (1 << 16) and vpp != passes[0]:
+                continue  # a third stage-3 radix pass
+            cfg = FrameConfig(tw, th, batch=b0, pixels_per_thread=p0)
+            ms = time_scan(cfg, vpp)
+            if best is None or ms < best[2]:
+                best = (cfg, vpp, ms)
+    cfg0, vpp, _ = best
+    for b, p in shapes[1:]:
+        if cfg0.tile_h % (4 * p):
+            continue
+        cfg = FrameConfig(cfg0.tile_w, cfg0.tile_h, batch=b, pixels_per_thread=p)
+        ms = time_scan(cfg, vpp)
+        if ms < best[2]:
+            best = (cfg, vpp, ms)
+    return best
 
 
 def _key(n: int, views) -> str:

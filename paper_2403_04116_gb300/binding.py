@@ -18,7 +18,8 @@ XG_ERR_WORKSPACE = 4
 XG_ERR_CHECK = 5
 
 # Every symbol include/xg.h declares.
-EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_project", "xg_bin_sort",
+EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_frame_select_views", "xg_frame_copy_status", "xg_project",
+           "xg_bin_sort",
            "xg_render_fwd", "xg_render_bwd", "xg_frame_read_status", "xg_frame_layout", "xg_loss_l1",
            "xg_frame_set_timing", "xg_frame_read_timing", "xg_activate", "xg_activate_bwd",
            "xg_loss_workspace_bytes", "xg_loss_l1_ssim", "xg_adam_step", "xg_psnr", "xg_sort_pairs_noalloc",
@@ -46,7 +47,7 @@ class XgGrads(ctypes.Structure):
 class XgConfig(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("near_mm", ctypes.c_float),
                 ("batch", ctypes.c_int32), ("pair_capacity", ctypes.c_int64), ("pixels_per_thread", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("views_per_pass", ctypes.c_int32)]
 
 
 class XgDeviceStatus(ctypes.Structure):
@@ -110,6 +111,10 @@ def lib(build_if_missing: bool = False):
     L.xg_frame_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(XgConfig), ctypes.c_int64,
                                   ctypes.POINTER(XgView), ctypes.c_int32, P, ctypes.c_size_t, P]
     L.xg_frame_create.restype = ctypes.c_int
+    L.xg_frame_copy_status.argtypes = [P, P, P]
+    L.xg_frame_copy_status.restype = ctypes.c_int
+    L.xg_frame_select_views.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    L.xg_frame_select_views.restype = ctypes.c_int
     L.xg_frame_destroy.argtypes = [P]
     L.xg_frame_destroy.restype = None
     L.xg_project.argtypes = [P, ctypes.POINTER(XgGaussians), P]
@@ -173,6 +178,16 @@ def xg_frame_create(cfg: XgConfig, n: int, views, workspace: int, workspace_byte
     _check(lib().xg_frame_create(ctypes.byref(out), ctypes.byref(cfg), n, arr, len(views), workspace,
                                  workspace_bytes, stream), "xg_frame_create")
     return out.value
+
+
+def xg_frame_copy_status(frame: int, out_ptr: int, stream: int) -> None:
+    _check(lib().xg_frame_copy_status(frame, out_ptr, stream), "xg_frame_copy_status")
+
+
+def xg_frame_select_views(frame: int, first_view: int) -> int:
+    got = ctypes.c_int32(0)
+    _check(lib().xg_frame_select_views(frame, first_view, ctypes.byref(got)), "xg_frame_select_views")
+    return got.value
 
 
 def xg_frame_destroy(frame: int) -> None:

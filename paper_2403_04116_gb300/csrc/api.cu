@@ -23,12 +23,17 @@ bool valid_config(const xg_config* cfg) {
   return (ppt == 1 || ppt == 2 || ppt == 4) && valid_tile(cfg->tile_w) && valid_tile(cfg->tile_h) &&
          cfg->tile_h % (4 * ppt) == 0 && cfg->tile_w * cfg->tile_h <= 512 * ppt && valid_batch(cfg->batch) &&
          isfinite(cfg->near_mm) && cfg->near_mm > 0.f && cfg->pair_capacity >= 1 &&
-         cfg->pair_capacity < ((int64_t)1 << 31);
+         cfg->pair_capacity < ((int64_t)1 << 31) && cfg->views_per_pass >= 0;
 }
 
-bool valid_sizes(int64_t n, int32_t n_views, int32_t W, int32_t H) {
+// Views rendered per pass: all of them unless the configuration asks for fewer.
+int32_t pass_views(const xg_config* cfg, int32_t n_views) {
+  return cfg->views_per_pass > 0 && cfg->views_per_pass < n_views ? cfg->views_per_pass : n_views;
+}
+
+bool valid_sizes(int64_t n, int32_t n_views, int32_t per_pass, int32_t W, int32_t H) {
   return n >= 1 && n < ((int64_t)1 << 31) && n_views >= 1 && n_views <= xg::kMaxViews && W >= 1 && W <= 4096 &&
-         H >= 1 && H <= 4096 && (int64_t)n_views * n < ((int64_t)1 << 40);
+         H >= 1 && H <= 4096 && (int64_t)per_pass * n < ((int64_t)1 << 40);
 }
 
 struct Sizes {
@@ -60,7 +65,9 @@ struct Offsets {
   size_t total;
 };
 
-bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t W, int32_t H, Sizes* s, Offsets* o) {
+// Per-pass arrays are sized for V views; the camera table holds all n_scan views.
+bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t n_scan, int32_t W, int32_t H, Sizes* s,
+                  Offsets* o) {
   if (!sizes_of(cfg, V, W, H, s)) return false;
   const size_t VN = (size_t)V * (size_t)n;
   const size_t cap = (size_t)cfg->pair_capacity;
@@ -72,7 +79,7 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t W, int32_t
     return at;
   };
   o->status = take(sizeof(xg::DevStatus));
-  o->cameras = take(sizeof(xg::Camera) * (size_t)V);
+  o->cameras = take(sizeof(xg::Camera) * (size_t)n_scan);
   o->records = take(32 * VN);
   o->depth = take(4 * VN);
   o->rect = take(8 * VN);
@@ -91,6 +98,44 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t W, int32_t
   o->grad2d = take(4 * 8 * VN);
   o->total = off;
   return true;
+}
+
+bool valid_view(const xg_view& w) {
+  return isfinite(w.sod_mm) && w.sod_mm > 0 && isfinite(w.sdd_mm) && w.sdd_mm > 0 && isfinite(w.pitch_u_mm) &&
+         w.pitch_u_mm > 0 && isfinite(w.pitch_v_mm) && w.pitch_v_mm > 0 && isfinite(w.angle_rad);
+}
+
+// Camera table of the frame's views (trigonometry in FP64, rounded once to FP32), copied to
+// the workspace on `st`; the host staging buffer may be freed when the copy call returns.
+cudaError_t upload_cameras(const xg_frame* f, const xg_view* views, cudaStream_t st) {
+  xg::Camera* cams = (xg::Camera*)calloc((size_t)f->n_scan, sizeof(xg::Camera));
+  if (!cams) return cudaErrorMemoryAllocation;
+  for (int32_t v = 0; v < f->n_scan; ++v) {
+    const xg_view& w = views[v];
+    xg::Camera& c = cams[v];
+    c.c = (float)cos(w.angle_rad);
+    c.s = (float)sin(w.angle_rad);
+    c.L = (float)w.sod_mm;
+    c.fu = (float)(w.sdd_mm / w.pitch_u_mm);
+    c.fv = (float)(w.sdd_mm / w.pitch_v_mm);
+    c.hw = (float)f->width * 0.5f - 0.5f;
+    c.hh = (float)f->height * 0.5f - 0.5f;
+  }
+  const cudaError_t e =
+      cudaMemcpyAsync(f->cam_all, cams, sizeof(xg::Camera) * (size_t)f->n_scan, cudaMemcpyHostToDevice, st);
+  free(cams);  // pageable source: the copy has been staged when cudaMemcpyAsync returns
+  return e;
+}
+
+__global__ void k_copy_status(const xg::DevStatus* __restrict__ s, xg_device_status* __restrict__ out) {
+  out->code = s->code;
+  out->reserved = 0;
+  out->pairs = s->pairs;
+  out->nonfinite = (int64_t)s->nonfinite;
+  out->fwd_evaluated = (int64_t)s->fwd_evaluated;
+  out->fwd_contrib = (int64_t)s->fwd_contrib;
+  out->bwd_evaluated = (int64_t)s->bwd_evaluated;
+  out->bwd_contrib = (int64_t)s->bwd_contrib;
 }
 
 }  // namespace
@@ -114,10 +159,12 @@ Timed::~Timed() {
 extern "C" {
 
 size_t xg_workspace_bytes(const xg_config* cfg, int64_t n, int32_t n_views, int32_t width, int32_t height) {
-  if (!valid_config(cfg) || !valid_sizes(n, n_views, width, height)) return 0;
+  if (!valid_config(cfg) || n_views < 1) return 0;
+  const int32_t per_pass = pass_views(cfg, n_views);
+  if (!valid_sizes(n, n_views, per_pass, width, height)) return 0;
   Sizes s;
   Offsets o;
-  return make_offsets(cfg, n, n_views, width, height, &s, &o) ? o.total : 0;
+  return make_offsets(cfg, n, per_pass, n_views, width, height, &s, &o) ? o.total : 0;
 }
 
 xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const xg_view* views, int32_t n_views,
@@ -126,17 +173,15 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   *out = nullptr;
   if (!valid_config(cfg) || !views || n_views < 1) return XG_ERR_INVALID_ARG;
   const int32_t W = views[0].width, H = views[0].height;
-  if (!valid_sizes(n, n_views, W, H)) return XG_ERR_INVALID_ARG;
+  const int32_t per_pass = pass_views(cfg, n_views);
+  if (!valid_sizes(n, n_views, per_pass, W, H)) return XG_ERR_INVALID_ARG;
   for (int32_t v = 0; v < n_views; ++v) {
     const xg_view& w = views[v];
-    if (w.width != W || w.height != H) return XG_ERR_INVALID_ARG;
-    if (!(isfinite(w.sod_mm) && w.sod_mm > 0 && isfinite(w.sdd_mm) && w.sdd_mm > 0 && isfinite(w.pitch_u_mm) &&
-          w.pitch_u_mm > 0 && isfinite(w.pitch_v_mm) && w.pitch_v_mm > 0 && isfinite(w.angle_rad)))
-      return XG_ERR_INVALID_ARG;
+    if (w.width != W || w.height != H || !valid_view(w)) return XG_ERR_INVALID_ARG;
   }
   Sizes s;
   Offsets o;
-  if (!make_offsets(cfg, n, n_views, W, H, &s, &o)) return XG_ERR_INVALID_ARG;
+  if (!make_offsets(cfg, n, per_pass, n_views, W, H, &s, &o)) return XG_ERR_INVALID_ARG;
   if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < o.total) return XG_ERR_WORKSPACE;
 
   xg_frame* f = (xg_frame*)calloc(1, sizeof(xg_frame));
@@ -144,8 +189,12 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   f->cfg = *cfg;
   if (f->cfg.batch == 0) f->cfg.batch = 256;
   if (f->cfg.pixels_per_thread == 0) f->cfg.pixels_per_thread = 2;
+  f->cfg.views_per_pass = per_pass;
   f->n = n;
-  f->n_views = n_views;
+  f->n_scan = n_views;
+  f->views_per_pass = per_pass;
+  f->first_view = 0;
+  f->n_views = per_pass;
   f->width = W;
   f->height = H;
   f->tiles_x = s.tiles_x;
@@ -161,7 +210,8 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   char* base = (char*)workspace;
   xg::FramePtrs& p = f->p;
   p.status = (xg::DevStatus*)(base + o.status);
-  p.cam = (xg::Camera*)(base + o.cameras);
+  f->cam_all = (xg::Camera*)(base + o.cameras);
+  p.cam = f->cam_all;
   p.rec = (float4*)(base + o.records);
   p.depth = (float*)(base + o.depth);
   p.rect = (ushort4*)(base + o.rect);
@@ -200,32 +250,24 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   L.tiles_y = s.tiles_y;
   L.sort_passes = s.entry_passes + s.tile_passes;
 
-  // camera table: trigonometry in FP64, rounded once to FP32
-  xg::Camera* cams = (xg::Camera*)calloc((size_t)n_views, sizeof(xg::Camera));
-  if (!cams) {
-    free(f);
-    return XG_ERR_INVALID_ARG;
-  }
-  for (int32_t v = 0; v < n_views; ++v) {
-    const xg_view& w = views[v];
-    xg::Camera& c = cams[v];
-    c.c = (float)cos(w.angle_rad);
-    c.s = (float)sin(w.angle_rad);
-    c.L = (float)w.sod_mm;
-    c.fu = (float)(w.sdd_mm / w.pitch_u_mm);
-    c.fv = (float)(w.sdd_mm / w.pitch_v_mm);
-    c.hw = (float)W * 0.5f - 0.5f;
-    c.hh = (float)H * 0.5f - 0.5f;
-  }
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(p.cam, cams, sizeof(xg::Camera) * (size_t)n_views, cudaMemcpyHostToDevice, st);
-  free(cams);  // pageable source: the copy has been staged when cudaMemcpyAsync returns
+  cudaError_t e = upload_cameras(f, views, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.status, 0, sizeof(xg::DevStatus), st);
   if (e != cudaSuccess) {
     free(f);
     return XG_ERR_CUDA;
   }
   *out = f;
+  return XG_OK;
+}
+
+xg_status xg_frame_select_views(xg_frame* frame, int32_t first_view, int32_t* n_selected) {
+  if (!frame || first_view < 0 || first_view >= frame->n_scan) return XG_ERR_INVALID_ARG;
+  const int32_t left = frame->n_scan - first_view;
+  frame->first_view = first_view;
+  frame->n_views = left < frame->views_per_pass ? left : frame->views_per_pass;
+  frame->p.cam = frame->cam_all + first_view;
+  if (n_selected) *n_selected = frame->n_views;
   return XG_OK;
 }
 
@@ -347,6 +389,12 @@ xg_status xg_frame_read_status(const xg_frame* frame, xg_device_status* out, voi
   out->bwd_evaluated = (int64_t)s.bwd_evaluated;
   out->bwd_contrib = (int64_t)s.bwd_contrib;
   return XG_OK;
+}
+
+xg_status xg_frame_copy_status(const xg_frame* frame, xg_device_status* out, void* stream) {
+  if (!frame || !out || ((uintptr_t)out % 8) != 0) return XG_ERR_INVALID_ARG;
+  k_copy_status<<<1, 1, 0, (cudaStream_t)stream>>>(frame->p.status, out);
+  return cudaGetLastError() == cudaSuccess ? XG_OK : XG_ERR_CUDA;
 }
 
 xg_status xg_frame_layout(const xg_frame* frame, xg_layout* out) {

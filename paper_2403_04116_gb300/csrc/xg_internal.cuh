@@ -156,7 +156,11 @@ constexpr int kMaxTimingRecs = 2048;
 struct xg_frame {
   xg_config cfg;
   int64_t n;
-  int32_t n_views, width, height;
+  int32_t n_views;         // views of the current pass (the kernels' V)
+  int32_t n_scan;          // views in the camera table
+  int32_t views_per_pass;  // capacity of the per-pass arrays
+  int32_t first_view;      // camera-table index of the current pass's view 0
+  int32_t width, height;
   int32_t tiles_x, tiles_y;
   int64_t tiles_per_view;
   int32_t tile_bits;     // bits of view * T + tile
@@ -166,6 +170,7 @@ struct xg_frame {
   void* workspace;
   size_t workspace_bytes;
   xg_layout layout;
+  xg::Camera* cam_all;  // camera table of all n_scan views; p.cam = cam_all + first_view
   xg::FramePtrs p;
   // optional per-kernel timing with CUDA events on the launch stream
   int timing;

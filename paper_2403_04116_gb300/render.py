@@ -44,22 +44,29 @@ class FrameConfig:
 class Frame:
     """One batch of views sharing a detector size, with its device workspace.
 
-    ``pair_capacity`` bounds the (view, tile, Gaussian) pairs; the workspace is allocated
-    once here and reused by every call, so a sequence of calls can be graph-captured.
+    ``pair_capacity`` bounds the (view, tile, Gaussian) pairs of one pass; the workspace is
+    allocated once here and reused by every call, so a sequence of calls can be
+    graph-captured.  With ``views_per_pass`` below the view count the per-pass arrays hold
+    that many views, and :meth:`select` picks the window the next calls render; ``V`` is
+    the number of views of the current pass.
     """
 
     def __init__(self, n: int, views, cfg: FrameConfig | None = None, pair_capacity: int = 1 << 22,
-                 device: torch.device | str | None = None, stream: torch.cuda.Stream | None = None):
+                 device: torch.device | str | None = None, stream: torch.cuda.Stream | None = None,
+                 views_per_pass: int = 0):
         self.cfg = cfg or FrameConfig()
         self.views = list(views)
         self.n = int(n)
-        self.V = len(self.views)
+        self.n_scan = len(self.views)
+        self.views_per_pass = min(views_per_pass, self.n_scan) if views_per_pass > 0 else self.n_scan
+        self.V = self.views_per_pass
+        self.first = 0
         self.W, self.H = self.views[0].width, self.views[0].height
         self.pair_capacity = int(pair_capacity)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self._c = B.XgConfig(self.cfg.tile_w, self.cfg.tile_h, self.cfg.near_mm, self.cfg.batch, self.pair_capacity,
-                             self.cfg.pixels_per_thread, 0)
-        nbytes = B.xg_workspace_bytes(self._c, self.n, self.V, self.W, self.H)
+                             self.cfg.pixels_per_thread, self.views_per_pass)
+        nbytes = B.xg_workspace_bytes(self._c, self.n, self.n_scan, self.W, self.H)
         if nbytes == 0:
             raise ValueError("invalid frame configuration")
         raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
@@ -101,8 +108,21 @@ class Frame:
         out = B.XgGrads(*[t.data_ptr() for t in grads])
         B.xg_render_bwd(self.handle, g, grad_image.data_ptr(), out, _stream_handle(stream))
 
+    def select(self, first_view: int) -> int:
+        """Render views first_view .. first_view + V - 1 in the calls that follow; returns V."""
+        self.V = B.xg_frame_select_views(self.handle, first_view)
+        self.first = first_view
+        return self.V
+
     def status(self, stream=None) -> B.XgDeviceStatus:
         return B.xg_frame_read_status(self.handle, _stream_handle(stream))
+
+    def copy_status(self, out: torch.Tensor, stream=None) -> None:
+        """Enqueue a copy of the device status into ``out`` (CUDA int64 tensor of 7 entries:
+        code and reserved packed in the first, then the fields of ``xg_device_status``)."""
+        if out.dtype != torch.int64 or not out.is_cuda or out.numel() < 7 or not out.is_contiguous():
+            raise ValueError("expected a contiguous CUDA int64 tensor of at least 7 entries")
+        B.xg_frame_copy_status(self.handle, out.data_ptr(), _stream_handle(stream))
 
     def set_timing(self, enable: bool) -> None:
         B.xg_frame_set_timing(self.handle, enable)

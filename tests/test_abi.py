@@ -49,6 +49,23 @@ def test_workspace_bytes_host_checks(lib):
         assert B.xg_workspace_bytes(bad, 10, 1, 64, 64) == 0
 
 
+def test_workspace_of_a_scan_rendered_in_passes(lib):
+    def ws(V, per_pass):
+        return B.xg_workspace_bytes(B.XgConfig(16, 16, 0.2, 0, 1 << 20, 2, per_pass), 1000, V, 64, 64)
+    # per-pass arrays follow the views of one pass; only the 64-byte camera table grows
+    one_pass = ws(8, 0)
+    assert ws(8, 8) == ws(8, 100) == one_pass
+    assert ws(360, 8) - one_pass == pytest.approx(64 * 352, abs=512)
+    assert ws(360, 8) < ws(360, 16) < ws(360, 0)
+    assert ws(8, -1) == 0
+
+
+def test_select_views_rejects_a_null_frame(lib):
+    with pytest.raises(B.XgError) as e:
+        B.xg_frame_select_views(None, 0)
+    assert e.value.code == B.XG_ERR_INVALID_ARG
+
+
 def test_frame_create_rejects_bad_arguments_before_touching_the_device(lib):
     from paper_2403_04116_gb300.synth import View
     cfg = B.XgConfig(16, 16, 0.2, 0, 1000)
