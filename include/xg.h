@@ -51,7 +51,8 @@ typedef enum {
   XG_ERR_CAPACITY = 2,    /* the frame's (view, tile, Gaussian) pairs exceed pair_capacity */
   XG_ERR_CUDA = 3,        /* a CUDA launch or copy failed; see cudaGetLastError */
   XG_ERR_WORKSPACE = 4,   /* the workspace is too small or misaligned */
-  XG_ERR_CHECK = 5        /* a device-side bounds check failed (a library defect); outputs invalid */
+  XG_ERR_CHECK = 5        /* a device-side bounds check failed, or a bounded wait in a kernel expired
+                             (a library or device defect); outputs invalid */
 } xg_status;
 
 /* One cone-beam projection (Sec. 3.3, Eq. 12).  The source orbits at distance sod_mm from

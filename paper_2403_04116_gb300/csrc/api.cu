@@ -251,7 +251,8 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   L.sort_passes = s.entry_passes + s.tile_passes;
 
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = upload_cameras(f, views, st);
+  cudaError_t e = xg::radix_prepare();  // kernel attributes, set outside any stream capture
+  if (e == cudaSuccess) e = upload_cameras(f, views, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.status, 0, sizeof(xg::DevStatus), st);
   if (e != cudaSuccess) {
     free(f);

@@ -244,17 +244,66 @@ __global__ void __launch_bounds__(256) k_radix_colscan(uint32_t* __restrict__ hi
   if (threadIdx.x == 0) hist[kSortBlocks * 256 + d] = total;
 }
 
+// ---- bulk asynchronous copies into shared memory, completed on an mbarrier ----------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t arrivals) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(arrivals) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the phase with this parity; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t spin = 0; spin < kSpinLimit; ++spin)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// global -> shared copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// orders this thread's earlier generic-proxy shared-memory accesses before later bulk copies
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Stable scatter of one digit.  Each CTA walks its chunk in tiles of kSortTile items; in a
-// tile, warp w owns items [w*256, w*256+256) in 8 rounds of 32, ranks them with
-// match_any, the tile is reordered by digit in shared memory and written out in digit runs.
-template <int WORDS>
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(SortArrays<WORDS> arr, int digit_word, int shift,
+// tile, warp w owns items [w*256, w*256+256) in 8 rounds of 32 and ranks them with
+// match_any against per-warp digit counts; the tile is reordered by digit in shared memory
+// and written out in digit runs.
+// Two tile buffers alternate: while tile j is ranked and reordered in one, a bulk
+// asynchronous copy brings tile j+1 into the other, so every CTA keeps a tile of loads in
+// flight through its whole chunk.  Full tiles of 16-byte aligned arrays take that path;
+// the rest (a chunk's ragged last tile, unaligned caller arrays) are loaded directly.
+template <int WORDS, int DW>
+__global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(SortArrays<WORDS> arr, int shift,
                                                                 DevStatus* __restrict__ st, int64_t fixed_count,
                                                                 const uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s_w[WORDS][kSortTile];
-  __shared__ uint32_t s_wcnt[kWarps][256];
-  __shared__ uint32_t s_bofs[256], s_tofs[256], s_tcnt[256];
+  extern __shared__ __align__(128) uint32_t s_dyn[];  // [2][WORDS][kSortTile]
+  // per warp and digit: the tile's count, then the digit's first slot in the reordered tile
+  // (16 bits each, two digits per word so that one 32-bit shared atomic adds to a count)
+  __shared__ uint32_t s_wcnt[kWarps][128];
+  __shared__ uint32_t s_delta[256];  // output position minus tile slot, per digit
   __shared__ uint32_t s_warp[kWarps];
+  __shared__ __align__(8) uint64_t s_bar;
+  uint16_t* const s_wc16 = reinterpret_cast<uint16_t*>(&s_wcnt[0][0]);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -262,97 +311,153 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(SortArrays<WORDS
   const int64_t chunk = chunk_of(total);
   const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
   if (beg >= end) return;
+  bool aligned = true;
+#pragma unroll
+  for (int w = 0; w < WORDS; ++w) aligned &= ((uintptr_t)arr.in[w] & 15u) == 0;
+#define BULK_TILE(b) (aligned && end - (b) >= kSortTile)
+#define BUF(j, w) (s_dyn + (((j) & 1) * WORDS + (w)) * kSortTile)
+  constexpr uint32_t kTileBytes = (uint32_t)(WORDS * kSortTile * sizeof(uint32_t));
+  // thread `tid` owns digit `tid`: its next output position for this CTA
+  uint32_t bofs;
   {
     uint32_t all;
     const uint32_t digit_base = block_exclusive_scan<kSortThreads>(hist[kSortBlocks * 256 + tid], s_warp, all);
-    s_bofs[tid] = digit_base + hist[blockIdx.x * 256 + tid];
+    bofs = digit_base + hist[blockIdx.x * 256 + tid];
   }
+  for (int i = tid; i < kWarps * 128; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    if (BULK_TILE(beg)) {
+      mbar_expect_tx(&s_bar, kTileBytes);
 #pragma unroll
-  for (int w = 0; w < kWarps; ++w) s_wcnt[w][tid] = 0;
+      for (int w = 0; w < WORDS; ++w) bulk_load(BUF(0, w), arr.in[w] + beg, kSortTile * 4u, &s_bar);
+    }
+  }
   __syncthreads();
 
-  for (int64_t base = beg; base < end; base += kSortTile) {
+  int j = 0;
+  for (int64_t base = beg; base < end; base += kSortTile, ++j) {
     uint32_t item[kSortItems][WORDS], dig[kSortItems], rank[kSortItems];
-    // all loads of the tile first, so that kSortItems * WORDS of them are in flight
+    if (BULK_TILE(base)) {
+      // every tile before j was a full bulk tile, so tile j completes phase j
+      const bool ok = mbar_wait_bounded(&s_bar, (uint32_t)(j & 1));
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) st->code = XG_ERR_CHECK;
+        mbar_wait_bounded(&s_bar, (uint32_t)(j & 1));  // let the copy in flight land first
+        return;
+      }
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-      const int64_t i = base + warp * (32 * kSortItems) + k * 32 + lane;
+      for (int k = 0; k < kSortItems; ++k)
 #pragma unroll
-      for (int w = 0; w < WORDS; ++w) item[k][w] = i < end ? __ldg(arr.in[w] + i) : 0u;
+        for (int w = 0; w < WORDS; ++w) item[k][w] = BUF(j, w)[warp * (32 * kSortItems) + k * 32 + lane];
+    } else {
+#pragma unroll
+      for (int k = 0; k < kSortItems; ++k) {
+        const int64_t i = base + warp * (32 * kSortItems) + k * 32 + lane;
+#pragma unroll
+        for (int w = 0; w < WORDS; ++w) item[k][w] = i < end ? __ldg(arr.in[w] + i) : 0u;
+      }
     }
+    __syncthreads();  // tile j is in registers: its buffer becomes the reorder buffer
+    if (tid == 0 && BULK_TILE(base + kSortTile)) {
+      mbar_expect_tx(&s_bar, kTileBytes);
+#pragma unroll
+      for (int w = 0; w < WORDS; ++w) bulk_load(BUF(j + 1, w), arr.in[w] + base + kSortTile, kSortTile * 4u, &s_bar);
+    }
+    // rank within the warp: the leader of each digit group adds the group to the warp's
+    // count and hands the previous count to the group
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
       const int64_t i = base + warp * (32 * kSortItems) + k * 32 + lane;
       const bool valid = i < end;
-      uint32_t dw = 0;
-#pragma unroll
-      for (int w = 0; w < WORDS; ++w)
-        if (w == digit_word) dw = item[k][w];
-      dig[k] = valid ? ((dw >> shift) & 255u) : 256u;
+      dig[k] = valid ? ((item[k][DW] >> shift) & 255u) : 256u;
       const uint32_t peers = __match_any_sync(0xffffffffu, dig[k]);
-      rank[k] = valid ? s_wcnt[warp][dig[k]] + __popc(peers & lt_mask) : 0u;
-      __syncwarp();
-      if (valid && lane == __ffs(peers) - 1) s_wcnt[warp][dig[k]] += __popc(peers);
-      __syncwarp();
+      const int leader = __ffs(peers) - 1;
+      if constexpr (WORDS == 2) {
+        const uint32_t half = (dig[k] & 1u) * 16u;
+        uint32_t old = 0;
+        if (valid && lane == leader) old = atomicAdd(&s_wcnt[warp][dig[k] >> 1], (uint32_t)__popc(peers) << half);
+        old = __shfl_sync(0xffffffffu, old, leader);
+        rank[k] = ((old >> half) & 0xffffu) + __popc(peers & lt_mask);
+      } else {  // fewer live registers: read the count, then the leader writes it back
+        rank[k] = valid ? s_wc16[warp * 256 + dig[k]] + __popc(peers & lt_mask) : 0u;
+        __syncwarp();
+        if (valid && lane == leader) s_wc16[warp * 256 + dig[k]] += (uint16_t)__popc(peers);
+        __syncwarp();
+      }
     }
     __syncthreads();
-    // digit `tid`: warp-exclusive prefixes and the tile's count
-    uint32_t run = 0;
+    // digit `tid`: the tile's count, its first slot, and each warp's first slot
+    uint32_t tile_count = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) tile_count += s_wc16[w * 256 + tid];
+    uint32_t tile_total;
+    uint32_t slot = block_exclusive_scan<kSortThreads>(tile_count, s_warp, tile_total);
+    s_delta[tid] = bofs - slot;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
-      const uint32_t c = s_wcnt[w][tid];
-      s_wcnt[w][tid] = run;
-      run += c;
+      const uint32_t c = s_wc16[w * 256 + tid];
+      s_wc16[w * 256 + tid] = (uint16_t)slot;
+      slot += c;
     }
-    s_tcnt[tid] = run;
-    uint32_t tile_total;
-    s_tofs[tid] = block_exclusive_scan<kSortThreads>(run, s_warp, tile_total);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
       if (dig[k] < 256u) {
-        const uint32_t loc = s_tofs[dig[k]] + s_wcnt[warp][dig[k]] + rank[k];
+        const uint32_t loc = s_wc16[warp * 256 + dig[k]] + rank[k];
 #pragma unroll
-        for (int w = 0; w < WORDS; ++w) s_w[w][loc] = item[k][w];
+        for (int w = 0; w < WORDS; ++w) BUF(j, w)[loc] = item[k][w];
       }
     }
     __syncthreads();
     const int n_tile = (int)min((int64_t)kSortTile, end - base);
     for (int i = tid; i < n_tile; i += kSortThreads) {
-      const uint32_t d = (s_w[digit_word][i] >> shift) & 255u;
-      const uint32_t pos = s_bofs[d] + (uint32_t)i - s_tofs[d];
+      const uint32_t d = (BUF(j, DW)[i] >> shift) & 255u;
+      const uint32_t pos = s_delta[d] + (uint32_t)i;
       if ((int64_t)pos >= total) {  // cannot happen when the histograms are right
         st->code = XG_ERR_CHECK;
         continue;
       }
 #pragma unroll
-      for (int w = 0; w < WORDS; ++w) arr.out[w][pos] = s_w[w][i];
+      for (int w = 0; w < WORDS; ++w) arr.out[w][pos] = BUF(j, w)[i];
     }
-    __syncthreads();
-    s_bofs[tid] += s_tcnt[tid];
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) s_wcnt[w][tid] = 0;
+    fence_proxy_async_smem();  // this buffer receives tile j+2 by bulk copy
+    bofs += tile_count;
+    for (int i = tid; i < kWarps * 128; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
   }
+#undef BULK_TILE
+#undef BUF
 }
 
-template __global__ void k_radix_scatter<2>(SortArrays<2>, int, int, DevStatus*, int64_t, const uint32_t*);
-template __global__ void k_radix_scatter<3>(SortArrays<3>, int, int, DevStatus*, int64_t, const uint32_t*);
 
 // ------------------------------------------------------------------------------------------
 // tile ranges in the sorted pairs
 // ------------------------------------------------------------------------------------------
+// One thread per 4 consecutive sorted pairs (one 16-byte load); the keys just outside its
+// four come from the neighbouring loads through L1.  The key array is 16-byte aligned and
+// padded to a multiple of 16 bytes, so the last load stays inside it.
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key_tile, int64_t n_keys,
                                                 DevStatus* __restrict__ st, uint2* __restrict__ range) {
   const int64_t total = items_of(st, -1);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t t = key_tile[i];
-    if ((int64_t)t >= n_keys) {  // cannot happen when emit and sort are right
-      st->code = XG_ERR_CHECK;
-      continue;
+  const int64_t quads = (total + 3) / 4;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < quads; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = 4 * q;
+    const uint4 k4 = __ldg(reinterpret_cast<const uint4*>(key_tile) + q);
+    const uint32_t k[6] = {i0 > 0 ? __ldg(key_tile + i0 - 1) : 0xffffffffu, k4.x, k4.y, k4.z, k4.w,
+                           i0 + 4 < total ? __ldg(key_tile + i0 + 4) : 0xffffffffu};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t i = i0 + e;
+      if (i >= total) break;
+      const uint32_t t = k[e + 1];
+      if ((int64_t)t >= n_keys) {  // cannot happen when emit and sort are right
+        st->code = XG_ERR_CHECK;
+        continue;
+      }
+      if (i == 0 || k[e] != t) range[t].x = (uint32_t)i;
+      if (i == total - 1 || k[e + 2] != t) range[t].y = (uint32_t)(i + 1);
     }
-    if (i == 0 || key_tile[i - 1] != t) range[t].x = (uint32_t)i;
-    if (i == total - 1 || key_tile[i + 1] != t) range[t].y = (uint32_t)(i + 1);
   }
 }
 
@@ -360,8 +465,38 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
 // host side
 // ------------------------------------------------------------------------------------------
 template <int WORDS>
-void radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, int64_t fixed_count,
-                DevStatus* status, uint32_t* hist, cudaStream_t st) {
+constexpr size_t scatter_smem() {
+  return 2 * WORDS * kSortTile * sizeof(uint32_t);
+}
+
+template <int WORDS, int DW>
+cudaError_t scatter_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<WORDS, DW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)scatter_smem<WORDS>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_radix_scatter<WORDS, DW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
+// Dynamic shared memory of the scatter kernels, set once per process (the first call must
+// not be inside a stream capture; frame creation makes it).
+cudaError_t radix_prepare() {
+  static cudaError_t once = [] {
+    cudaError_t e = scatter_attrs<2, 0>();
+    if (e == cudaSuccess) e = scatter_attrs<2, 1>();
+    if (e == cudaSuccess) e = scatter_attrs<3, 0>();
+    if (e == cudaSuccess) e = scatter_attrs<3, 1>();
+    return e;
+  }();
+  return once;
+}
+
+template <int WORDS>
+cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, int64_t fixed_count,
+                       DevStatus* status, uint32_t* hist, cudaStream_t st) {
+  const cudaError_t prep = radix_prepare();
+  if (prep != cudaSuccess) return prep;
   {
     Timed t(f, kRadixHist, st);
     k_radix_hist<<<kSortBlocks, kSortThreads, 0, st>>>(arr.in[digit_word], shift, status, fixed_count, hist);
@@ -372,12 +507,19 @@ void radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int s
   }
   {
     Timed t(f, kRadixScatter, st);
-    k_radix_scatter<WORDS><<<kSortBlocks, kSortThreads, 0, st>>>(arr, digit_word, shift, status, fixed_count, hist);
+    constexpr size_t smem = scatter_smem<WORDS>();
+    if (digit_word == 0)
+      k_radix_scatter<WORDS, 0><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, status, fixed_count, hist);
+    else
+      k_radix_scatter<WORDS, 1><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, status, fixed_count, hist);
   }
+  return cudaGetLastError();
 }
 
-template void radix_pass<2>(xg_frame*, const SortArrays<2>&, int, int, int64_t, DevStatus*, uint32_t*, cudaStream_t);
-template void radix_pass<3>(xg_frame*, const SortArrays<3>&, int, int, int64_t, DevStatus*, uint32_t*, cudaStream_t);
+template cudaError_t radix_pass<2>(xg_frame*, const SortArrays<2>&, int, int, int64_t, DevStatus*, uint32_t*,
+                                    cudaStream_t);
+template cudaError_t radix_pass<3>(xg_frame*, const SortArrays<3>&, int, int, int64_t, DevStatus*, uint32_t*,
+                                    cudaStream_t);
 
 cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   const FramePtrs& p = f->p;
@@ -390,7 +532,8 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     SortArrays<3> arr;
     arr.in[0] = p.ent_view[cur], arr.in[1] = p.ent_depth[cur], arr.in[2] = p.ent_gid[cur];
     arr.out[0] = p.ent_view[cur ^ 1], arr.out[1] = p.ent_depth[cur ^ 1], arr.out[2] = p.ent_gid[cur ^ 1];
-    radix_pass<3>(f, arr, digit_word, shift, VN, p.status, p.hist, st);
+    const cudaError_t e = radix_pass<3>(f, arr, digit_word, shift, VN, p.status, p.hist, st);
+    if (e != cudaSuccess) return e;
     cur ^= 1;
   }
   const uint32_t* ent_view = p.ent_view[cur];
@@ -420,7 +563,8 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     SortArrays<2> arr;
     arr.in[0] = p.key_tile[pc], arr.in[1] = p.value[pc];
     arr.out[0] = p.key_tile[pc ^ 1], arr.out[1] = p.value[pc ^ 1];
-    radix_pass<2>(f, arr, 0, 8 * pass, -1, p.status, p.hist, st);
+    const cudaError_t e = radix_pass<2>(f, arr, 0, 8 * pass, -1, p.status, p.hist, st);
+    if (e != cudaSuccess) return e;
     pc ^= 1;
   }
   // stage 4: ranges

@@ -67,6 +67,7 @@ extern "C" xg_status xg_sort_pairs_noalloc(const uint32_t* key_tile, const uint3
   unsigned char* base = nullptr;
   const xg_status s = noalloc_scratch(&base);
   if (s != XG_OK) return s;
+  if (radix_prepare() != cudaSuccess) return XG_ERR_CUDA;
   if (count == 0) return XG_OK;
   cudaStream_t st = (cudaStream_t)stream;
   DevStatus* status = (DevStatus*)base;
@@ -91,7 +92,8 @@ extern "C" xg_status xg_sort_pairs_noalloc(const uint32_t* key_tile, const uint3
       arr.in[w] = src[w];
       arr.out[w] = dst[w];
     }
-    radix_pass<3>(nullptr, arr, digit_word ? 0 : 1, shift, count, status, hist, st);
+    if (radix_pass<3>(nullptr, arr, digit_word ? 0 : 1, shift, count, status, hist, st) != cudaSuccess)
+      return XG_ERR_CUDA;
     src[0] = dst[0];
     src[1] = dst[1];
     src[2] = dst[2];

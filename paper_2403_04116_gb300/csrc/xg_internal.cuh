@@ -16,10 +16,15 @@
 namespace xg {
 
 constexpr int kMaxViews = 1 << 16;
-constexpr int kSortBlocks = 608;      // 4 x 152 SMs: grid of the scan and radix-sort passes
+constexpr int kNumSMs = 152;
+constexpr int kSortCtasPerSM = 4;
+constexpr int kSortBlocks = kSortCtasPerSM * kNumSMs;  // grid of the scan and radix-sort passes
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;         // keys per thread per radix tile
 constexpr int kSortTile = kSortThreads * kSortItems;
+// iteration limit of every spin-wait in a kernel; on expiry the kernel records
+// XG_ERR_CHECK in the status word and returns
+constexpr uint32_t kSpinLimit = 1u << 22;
 
 // Decision constants (float roundings of the paper-level values).
 constexpr double kLn2D = 0.69314718055994530942;
@@ -204,6 +209,9 @@ cudaError_t launch_loss_l1(const float* image, const float* target, int64_t coun
 // the digit taken from arr.in[digit_word] >> shift.  The item count is `fixed_count` when it
 // is >= 0, else the pair count in the status word.  `f` may be NULL (no timing).
 template <int WORDS>
-void radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, int64_t fixed_count,
-                DevStatus* status, uint32_t* hist, cudaStream_t st);
+cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, int64_t fixed_count,
+                       DevStatus* status, uint32_t* hist, cudaStream_t st);
+// Sets the scatter kernels' shared-memory attributes (once per process); call outside
+// stream capture before the first radix_pass.
+cudaError_t radix_prepare();
 }  // namespace xg
