@@ -145,3 +145,13 @@ def phantom_targets(ph: dict, views: list[View]) -> np.ndarray:
     imgs = np.stack([phantom_line_integrals(ph, v) for v in views])
     m = imgs.max()
     return (imgs / m if m > 0 else imgs).astype(np.float32)
+
+
+def projection_noise(images: np.ndarray, level: float, gen: np.random.Generator) -> np.ndarray:
+    """Targets with additive zero-mean Gaussian noise of standard deviation ``level`` times
+    each view's value range: the paper's measured projections carry 3 % noise (Sec. 4.1),
+    whose model it does not state; this is the reading."""
+    images = np.asarray(images, np.float64)
+    flat = images.reshape(images.shape[0], -1)
+    span = (flat.max(axis=1) - flat.min(axis=1)).reshape(-1, *([1] * (images.ndim - 1)))
+    return images + gen.normal(0.0, 1.0, size=images.shape) * level * span
