@@ -305,6 +305,24 @@ xg_status xg_adam_step(const xg_adam_group* groups, int32_t n_groups, int32_t* s
 xg_status xg_psnr(const float* image, const float* target, int32_t n_views, int64_t pixels_per_view, float* psnr,
                   void* stream);
 
+/* ACUI initialisation of the Gaussian centres (Sec. 3.3, Eq. 13).  A cuboid of
+ * size_mm[0] x size_mm[1] x size_mm[2] mm centred on the origin is divided into
+ * grid[0] x grid[1] x grid[2] voxels; the centres are the points
+ * (n_1 S_1 d / M_1, n_2 S_2 d / M_2, n_3 S_3 d / M_3) for integers n_i with
+ * |n_i| <= floor(M_i / (2 d)) + 1 (the bracket of Eq. 13 read as the floor), d = interval
+ * in voxels (the paper takes d = 8).
+ *
+ * xg_acui_count returns the number of points (0 for invalid arguments: sizes not finite
+ * and positive, grid < 1, interval not finite and positive, or 2^31 points or more). */
+int64_t xg_acui_count(const double size_mm[3], const int32_t grid[3], double interval);
+
+/* Writes the points to `mean` (device, float[3][count], rows x, y, z), n_1 slowest and
+ * n_3 fastest, each ascending; every coordinate is ((n S) d) / M in FP64 rounded once to
+ * FP32.  size_mm and grid are host arrays.  Enqueued on `stream`.  Errors:
+ * XG_ERR_INVALID_ARG, XG_ERR_CAPACITY (count > capacity floats per row), XG_ERR_CUDA. */
+xg_status xg_acui_points(const double size_mm[3], const int32_t grid[3], double interval, float* mean,
+                         int64_t capacity, void* stream);
+
 /* Largest pair count xg_sort_pairs_noalloc accepts. */
 #define XG_NOALLOC_MAX_PAIRS (1 << 20)
 

@@ -18,7 +18,7 @@ XG_ERR_WORKSPACE = 4
 XG_ERR_CHECK = 5
 
 # Every symbol include/xg.h declares.
-EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_frame_select_views", "xg_frame_copy_status", "xg_project",
+EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_frame_select_views", "xg_acui_count", "xg_acui_points", "xg_frame_copy_status", "xg_project",
            "xg_bin_sort",
            "xg_render_fwd", "xg_render_bwd", "xg_frame_read_status", "xg_frame_layout", "xg_loss_l1",
            "xg_frame_set_timing", "xg_frame_read_timing", "xg_activate", "xg_activate_bwd",
@@ -111,6 +111,11 @@ def lib(build_if_missing: bool = False):
     L.xg_frame_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(XgConfig), ctypes.c_int64,
                                   ctypes.POINTER(XgView), ctypes.c_int32, P, ctypes.c_size_t, P]
     L.xg_frame_create.restype = ctypes.c_int
+    L.xg_acui_count.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), ctypes.c_double]
+    L.xg_acui_count.restype = ctypes.c_int64
+    L.xg_acui_points.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), ctypes.c_double, P,
+                                 ctypes.c_int64, P]
+    L.xg_acui_points.restype = ctypes.c_int
     L.xg_frame_copy_status.argtypes = [P, P, P]
     L.xg_frame_copy_status.restype = ctypes.c_int
     L.xg_frame_select_views.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
@@ -178,6 +183,19 @@ def xg_frame_create(cfg: XgConfig, n: int, views, workspace: int, workspace_byte
     _check(lib().xg_frame_create(ctypes.byref(out), ctypes.byref(cfg), n, arr, len(views), workspace,
                                  workspace_bytes, stream), "xg_frame_create")
     return out.value
+
+
+def _acui_args(size_mm, grid):
+    return (ctypes.c_double * 3)(*[float(x) for x in size_mm]), (ctypes.c_int32 * 3)(*[int(m) for m in grid])
+
+
+def xg_acui_count(size_mm, grid, interval: float) -> int:
+    return int(lib().xg_acui_count(*_acui_args(size_mm, grid), float(interval)))
+
+
+def xg_acui_points(size_mm, grid, interval: float, mean_ptr: int, capacity: int, stream: int) -> None:
+    _check(lib().xg_acui_points(*_acui_args(size_mm, grid), float(interval), mean_ptr, int(capacity), stream),
+           "xg_acui_points")
 
 
 def xg_frame_copy_status(frame: int, out_ptr: int, stream: int) -> None:

@@ -1,4 +1,5 @@
-"""Pins of the FP64 ACUI oracle (Eq. 13) against facts outside it."""
+"""Pins of the FP64 ACUI oracle (Eq. 13) against facts outside it, and the host-side point
+count of the C ABI against it (no device calls)."""
 import itertools
 
 import numpy as np
@@ -49,6 +50,17 @@ def test_ordering_n1_slowest():
     assert (np.diff(P[2][:7]) > 0).all() and (P[0][:49] == P[0][0]).all()
     assert P[0][0] < P[0][49] and P[1][0] < P[1][7]
     np.testing.assert_allclose(P[:, 0], [-7.5, -7.5, -7.5])  # -3 * 10 * 2 / 8
+
+
+def test_host_count_of_the_library_matches_the_oracle():
+    from paper_2403_04116_gb300 import binding as B
+    B.lib(build_if_missing=True)
+    for S, M, d in [((200.0,) * 3, (256,) * 3, 8), ((1.0, 2.0, 3.0), (100, 10, 1), 3.5), ((5.0,) * 3, (1, 1, 1), 0.25),
+                    ((7.0, 9.0, 11.0), (13, 17, 19), 1.0)]:
+        assert B.xg_acui_count(S, M, d) == A.acui_count(S, M, d)
+    for bad in [((0.0, 1.0, 1.0), (8, 8, 8), 2), ((1.0,) * 3, (0, 8, 8), 2), ((1.0,) * 3, (8, 8, 8), 0.0),
+                ((1.0,) * 3, (8, 8, 8), float("nan")), ((1.0,) * 3, (1 << 30,) * 3, 1.0)]:
+        assert B.xg_acui_count(*bad) == 0
 
 
 def test_projection_noise_level():
