@@ -44,8 +44,12 @@ WORKLOADS = {
     "batch100k": dict(n=100_000, views=100, W=256, H=256, tile=(16, 16), cid=2),
     # forward only: a 360-view scan at 1 degree spacing, rendered in passes inside one graph
     "scan360": dict(n=1_000_000, views=360, W=1024, H=1024, tile=(16, 16), cid=4, forward_only=True),
+    # the same scene and detector with two views: a small case for profiler captures
+    "dense2": dict(n=1_000_000, views=2, W=1024, H=1024, tile=(16, 16), cid=4, forward_only=True),
 }
-METRIC_SCAN = "X-ray projections/s fwd (1M Gaussians, 1024², 360 views) and % of roofline"
+def metric_scan(w: dict) -> str:
+    return (f"X-ray projections/s fwd ({w['n'] / 1e6:g}M Gaussians, {w['W']}², {w['views']} views) "
+            "and % of roofline")
 METRIC = "X-ray projections/s fwd and fwd+bwd (50k Gaussians, 256²) and % of roofline"
 
 # FP32 lane instructions charged per evaluated (pixel, list entry) pair of the compositing
@@ -248,7 +252,7 @@ def run_reference(args) -> None:
         cpu_oracle_rate(args.workload, target_seconds=0.5)
     rates = [cpu_oracle_rate(args.workload, target_seconds=per_step) for _ in range(args.steps)]
     value = statistics.median(r["value"] for r in rates)
-    metric = METRIC_SCAN if w.get("forward_only") else METRIC
+    metric = metric_scan(w) if w.get("forward_only") else METRIC
     line = {"metric": metric, "value": value, "unit": "projections/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * w["views"] / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -614,7 +618,7 @@ def run_scan(args) -> None:
                          "pixels_per_thread": cfg.pixels_per_thread, "views_per_pass": vpp,
                          "passes": len(scan.starts), "graph": "every pass in one CUDA graph",
                          "autotuned": bool(args.autotune and not args.config)})
-        line = {"metric": METRIC_SCAN, "value": value, "unit": "projections/s", "n_gpus": world,
+        line = {"metric": metric_scan(w), "value": value, "unit": "projections/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": cfg_line, "stream_launched": {"ms_per_step": ms_stream / timing_steps},

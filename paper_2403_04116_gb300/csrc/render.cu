@@ -6,7 +6,14 @@
 // memory in batches (the record of each Gaussian read once per CTA and broadcast to all its
 // pixels); a CTA stops fetching as soon as every pixel's transmittance has hit the floor
 // (__syncthreads_count).  Per batch, each warp compacts the staged entries whose footprint
-// box meets its block (ballot) and walks only those.
+// can reach its block (box test, then the largest exponent over the block) and walks only
+// those.
+//
+// A thread's pixels are processed in pairs with the packed two-lane FP32 instructions of
+// sm_100+ (f32x2 add / mul / fma): both pixels of a pair see the same list entry, so the
+// exponent, exp, opacity, transmittance and colour (forward) or gradient terms (backward)
+// of the two run as one instruction stream.  Each lane rounds as the scalar operation
+// would, so results are those of the documented scalar FP32 sequence.
 //
 // Most (pixel, list entry) pairs lie outside the Gaussian's footprint.  Each staged record
 // carries a conservative exponent threshold ln(1/(255 o)) - 1e-4: below it the opacity
@@ -18,8 +25,8 @@
 // recovering the transmittance by division instead of storing it.  Per list entry, a warp
 // with contributing pixels sums its 7 per-pixel terms (six moments of dL/dpower and the
 // intensity term) with an 8-value reduce-scatter butterfly (9 shuffles; lane 4k ends with
-// the sum of term k) into shared memory.  After the batch each Gaussian's sums are turned into dL/du, dL/dconic and
-// dL/dopacity and added to global memory with two float4 atomics.
+// the sum of term k) into shared memory.  After the batch each Gaussian's sums are turned
+// into dL/du, dL/dconic and dL/dopacity and added to global memory with two float4 atomics.
 #include "xg_internal.cuh"
 
 namespace xg {
@@ -27,39 +34,71 @@ namespace xg {
 
 constexpr int kMaxWarps = 16;  // 512-thread tiles
 
-// Stage list entries [first, first + cnt) of a tile: records rescaled for the exponent,
-// the exponent threshold, and a conservative pixel box of each footprint.
-__device__ __forceinline__ void stage_batch(const uint32_t* __restrict__ value, const float4* __restrict__ rec,
-                                            int64_t vn_base, uint32_t first, int cnt, const Camera& cam, float4* s_a,
-                                            float4* s_b, float4* s_box, uint32_t* s_g) {
+// Packed staging for the pixel-pair kernels: every field duplicated so that one broadcast
+// shared load yields both lanes of a packed operand.  s_q[0..3][j] = (u_x u_x u_y u_y),
+// (na na nb nb), (nc nc o o), (i i thr thr) with na, nb, nc = -a/2, -b, -c/2 and thr the
+// exponent threshold; s_box as in stage_batch.
+template <int kBatch>
+__device__ __forceinline__ void stage_batch_pairs(const uint32_t* __restrict__ value, const float4* __restrict__ rec,
+                                                  int64_t vn_base, uint32_t first, int cnt, const Camera& cam,
+                                                  float4 (*s_q)[kBatch], float4* s_box, uint32_t* s_g) {
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     const uint32_t g = value[first + j];
     const float4 a = rec[2 * (vn_base + g)];
     const float4 b = rec[2 * (vn_base + g) + 1];
-    // (u_x, u_y, -a/2, -b) and (-c/2, opacity, intensity): exact rescalings of the conic;
-    // w: exponent below which the opacity cannot reach 1/255
-    s_a[j] = make_float4(a.x, a.y, -0.5f * a.z, -a.w);
-    s_b[j] = make_float4(-0.5f * b.x, b.y, b.z, logf(kAlphaMin / b.y) - 1e-4f);
-    // Pixels where the opacity can reach 1/255 satisfy d^T K d <= 2 ln(255 o); their x
-    // offsets lie within sqrt(2 ln(255 o) (K^-1)_xx), and likewise for y.  Widened by 0.1 %
-    // and 0.01 px, far beyond FP32 rounding, so the box never drops a contributing pixel.
-    const float two_l = 2.f * fmaxf(logf(255.f * b.y), 0.f);
+    const float na = -0.5f * a.z, nb = -a.w, nc = -0.5f * b.x;
+    // ln(255 o) with the fast hardware log (absolute error below 1e-5 here): the threshold
+    // keeps a 1e-4 margin and the box 0.1 % + 0.01 px, so both stay conservative
+    const float l255o = __logf(255.f * b.y);
+    const float thr = -l255o - 1e-4f;
+    s_q[0][j] = make_float4(a.x, a.x, a.y, a.y);
+    s_q[1][j] = make_float4(na, na, nb, nb);
+    s_q[2][j] = make_float4(nc, nc, b.y, b.y);
+    s_q[3][j] = make_float4(b.z, b.z, thr, thr);
+    const float two_l = 2.f * fmaxf(l255o, 0.f);
     const float det = a.z * b.x - a.w * a.w;
     float ex = INFINITY, ey = INFINITY;
     if (det > 0.f) {
-      ex = sqrtf(two_l * b.x / det) * 1.001f + 0.01f;
-      ey = sqrtf(two_l * a.z / det) * 1.001f + 0.01f;
+      const float s = __fdividef(two_l, det);
+      ex = __fsqrt_rn(s * b.x) * 1.001f + 0.01f;
+      ey = __fsqrt_rn(s * a.z) * 1.001f + 0.01f;
     }
-    const float cx = a.x + cam.hw, cy = a.y + cam.hh;  // footprint centre in pixel indices
+    const float cx = a.x + cam.hw, cy = a.y + cam.hh;
     s_box[j] = make_float4(cx - ex, cx + ex, cy - ey, cy + ey);
     if (s_g) s_g[j] = g;
   }
 }
 
-// The staged entries whose box meets this warp's pixel block [bx0, bx0+7] x [by0, by1], in
-// list order; returns their count.
-__device__ __forceinline__ int warp_list(const float4* s_box, int cnt, float bx0, float by0, float by1,
-                                         uint16_t* list, int lane) {
+// Largest exponent na dx^2 + nb dx dy + nc dy^2 (na, nc < 0) over the offsets
+// d in [dx0, dx1] x [dy0, dy1]: 0 if the rectangle holds the centre, else the best point on
+// one of its edges (the concave quadratic restricted to an edge peaks at the clamped
+// stationary point).
+__device__ __forceinline__ float max_power_over_rect(float na, float nb, float nc, float dx0, float dx1, float dy0,
+                                                     float dy1) {
+  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
+  const float ky = __fdividef(-nb, 2.f * nc), kx = __fdividef(-nb, 2.f * na);
+  float best = -INFINITY;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float X = e ? dx1 : dx0;
+    const float dy = fminf(fmaxf(ky * X, dy0), dy1);
+    best = fmaxf(best, X * (na * X + nb * dy) + nc * dy * dy);
+    const float Y = e ? dy1 : dy0;
+    const float dx = fminf(fmaxf(kx * Y, dx0), dx1);
+    best = fmaxf(best, dx * (na * dx + nb * Y) + nc * Y * Y);
+  }
+  return best;
+}
+
+// The staged entries whose footprint can reach this warp's pixel block [bx0, bx0+7] x
+// [by0, by1] (pixel indices), in list order; returns their count.  An entry is kept when its
+// box meets the block and the largest exponent over the block's pixel centres is within a
+// margin (1e-2 + 1e-3 |thr|, far above FP32 rounding of these sums) of the threshold below
+// which no pixel can reach opacity 1/255: only entries that no pixel of the block could
+// take are dropped, so decisions are unchanged.
+template <int kBatch>
+__device__ __forceinline__ int warp_list(const float4 (*s_q)[kBatch], const float4* s_box, int cnt, float bx0,
+                                         float by0, float by1, const Camera& cam, uint16_t* list, int lane) {
   const uint32_t lt_mask = (1u << lane) - 1u;
   int m = 0;
   for (int j0 = 0; j0 < cnt; j0 += 32) {
@@ -68,6 +107,13 @@ __device__ __forceinline__ int warp_list(const float4* s_box, int cnt, float bx0
     if (j < cnt) {
       const float4 bx = s_box[j];
       hit = bx.x <= bx0 + 7.f && bx.y >= bx0 && bx.z <= by1 && bx.w >= by0;
+      if (hit) {
+        const float cx = s_q[0][j].x + cam.hw, cy = s_q[0][j].z + cam.hh;
+        const float thr = s_q[3][j].z;
+        const float best = max_power_over_rect(s_q[1][j].x, s_q[1][j].z, s_q[2][j].x, cx - (bx0 + 7.f), cx - bx0,
+                                               cy - by1, cy - by0);
+        hit = best >= thr - (1e-2f + 1e-3f * fabsf(thr));
+      }
     }
     const uint32_t mask = __ballot_sync(0xffffffffu, hit);
     if (hit) list[m + __popc(mask & lt_mask)] = (uint16_t)j;
@@ -130,6 +176,9 @@ __device__ __forceinline__ float power_of(const float4 a, const float nc, float 
   return ffma(dx, t, fmul(fmul(nc, dy), dy));
 }
 
+// Forward.  A thread's pixels are taken in pairs (4 rows apart; for one pixel per thread
+// the second of the pair is idle), and the exponent, exp, opacity, transmittance and colour
+// of both are computed with packed two-lane instructions; the decisions stay per pixel.
 template <int kBatch, int PPT>
 __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ range, const uint32_t* __restrict__ value,
                                                     const float4* __restrict__ rec, int64_t n, int W, int H,
@@ -137,7 +186,9 @@ __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ ra
                                                     const Camera* __restrict__ cams, DevStatus* __restrict__ st,
                                                     float* __restrict__ image, uint32_t* __restrict__ ncontrib,
                                                     float* __restrict__ tfinal, uint32_t* __restrict__ last) {
-  __shared__ float4 s_a[kBatch], s_b[kBatch], s_box[kBatch];
+  constexpr int NP = PPT > 1 ? PPT / 2 : 1;  // pixel pairs per thread
+  __shared__ float4 s_q[4][kBatch];
+  __shared__ float4 s_box[kBatch];
   __shared__ uint16_t s_list[kMaxWarps][kBatch];
   const int tile = blockIdx.x, v = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -148,76 +199,102 @@ __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ ra
   const float bx0 = (float)(tx0 + (lx & ~7)), by0 = (float)(ty0 + (ly & ~3));  // this warp's block
   const float by1 = by0 + (float)(4 * PPT - 1);
   const Camera cam = cams[v];
-  const float px = fsub((float)x, cam.hw);
+  const float2 npx = f2(-fsub((float)x, cam.hw));
   const uint2 r = st->code == XG_OK ? range[(int64_t)v * tiles_per_view + tile] : make_uint2(0u, 0u);
   const int nlist = (int)(r.y - r.x);
   const int64_t vn_base = (int64_t)v * n;
   uint16_t* my_list = s_list[warp];
 
-  float py[PPT], T[PPT], C[PPT];
-  uint32_t nc[PPT], lastp[PPT];
-  bool done[PPT];
+  float2 npy[NP], T[NP], C[NP];
+  uint32_t nc[NP][2], lastp[NP][2];
+  bool done[NP][2];
 #pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    const int y = ty0 + ly + 4 * q;
-    py[q] = fsub((float)y, cam.hh);
-    T[q] = 1.0f;
-    C[q] = 0.0f;
-    nc[q] = lastp[q] = 0;
-    done[q] = !(x < W && y < H);
+  for (int pr = 0; pr < NP; ++pr) {
+    float ny[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int y = ty0 + ly + 4 * (2 * pr + h);
+      ny[h] = -fsub((float)y, cam.hh);
+      nc[pr][h] = lastp[pr][h] = 0;
+      done[pr][h] = !((PPT > 1 || h == 0) && x < W && y < H);
+    }
+    npy[pr] = make_float2(ny[0], ny[1]);
+    T[pr] = f2(1.0f);
+    C[pr] = f2(0.0f);
   }
   uint32_t nev = 0;
   auto all_done = [&]() {
     bool d = true;
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) d = d && done[q];
+    for (int pr = 0; pr < NP; ++pr) d = d && done[pr][0] && done[pr][1];
     return d;
   };
   for (int base = 0; base < nlist; base += kBatch) {
     if (__syncthreads_count(all_done()) == (int)blockDim.x) break;
     const int cnt = min(kBatch, nlist - base);
-    stage_batch(value, rec, vn_base, r.x + base, cnt, cam, s_a, s_b, s_box, nullptr);
+    stage_batch_pairs<kBatch>(value, rec, vn_base, r.x + base, cnt, cam, s_q, s_box, nullptr);
     __syncthreads();
     if (__all_sync(0xffffffffu, all_done())) continue;
-    const int m = warp_list(s_box, cnt, bx0, by0, by1, my_list, lane);
+    const int m = warp_list<kBatch>(s_q, s_box, cnt, bx0, by0, by1, cam, my_list, lane);
 #pragma unroll 2
     for (int k = 0; k < m; ++k) {
       if (all_done()) break;
       const int j = my_list[k];
-      const float4 a = s_a[j];
-      const float4 b = s_b[j];
+      const float4 q0 = s_q[0][j], q1 = s_q[1][j], q2 = s_q[2][j], q3 = s_q[3][j];
+      const float2 dx = fadd2(make_float2(q0.x, q0.y), npx);
+      const uint32_t pos = (uint32_t)(base + j + 1);
 #pragma unroll
-      for (int q = 0; q < PPT; ++q) {
-        if (done[q]) continue;
-        float dx, dy;
-        const float p = power_of(a, b.x, px, py[q], dx, dy);
-        ++nev;
-        if (p < b.w) continue;  // opacity provably below 1/255
-        const float al = fminf(kAlphaMax, fmul(b.y, xg_exp(p)));
-        if (al < kAlphaMin) continue;
-        const float Tn = fmul(T[q], fsub(1.0f, al));
-        if (Tn < kTMin) {
-          done[q] = true;
-          continue;
+      for (int pr = 0; pr < NP; ++pr) {
+        if (done[pr][0] && done[pr][1]) continue;
+        // the exponent dx (na dx + nb dy) + (nc dy) dy of both pixels
+        const float2 dy = fadd2(make_float2(q0.z, q0.w), npy[pr]);
+        const float2 t = ffma2(make_float2(q1.x, q1.y), dx, fmul2(make_float2(q1.z, q1.w), dy));
+        const float2 p = ffma2(dx, t, fmul2(fmul2(make_float2(q2.x, q2.y), dy), dy));
+        nev += (uint32_t)!done[pr][0] + (uint32_t)!done[pr][1];
+        const bool in0 = !done[pr][0] && !(p.x < q3.z), in1 = !done[pr][1] && !(p.y < q3.z);
+        if (!(in0 || in1)) continue;  // opacity provably below 1/255 for both
+        const float2 oe = fmul2(make_float2(q2.z, q2.w), xg_exp2v(p));
+        const float2 al = make_float2(fminf(kAlphaMax, oe.x), fminf(kAlphaMax, oe.y));
+        const float2 Tn = fmul2(T[pr], ffma2(al, f2(-1.0f), f2(1.0f)));
+        const float2 Cn = ffma2(make_float2(q3.x, q3.y), fmul2(al, T[pr]), C[pr]);
+        if (in0 && !(al.x < kAlphaMin)) {
+          if (Tn.x < kTMin) {
+            done[pr][0] = true;
+          } else {
+            C[pr].x = Cn.x;
+            T[pr].x = Tn.x;
+            ++nc[pr][0];
+            lastp[pr][0] = pos;
+          }
         }
-        C[q] = ffma(b.z, fmul(al, T[q]), C[q]);
-        T[q] = Tn;
-        ++nc[q];
-        lastp[q] = (uint32_t)(base + j + 1);
+        if (in1 && !(al.y < kAlphaMin)) {
+          if (Tn.y < kTMin) {
+            done[pr][1] = true;
+          } else {
+            C[pr].y = Cn.y;
+            T[pr].y = Tn.y;
+            ++nc[pr][1];
+            lastp[pr][1] = pos;
+          }
+        }
       }
     }
   }
   uint32_t nct = 0;
 #pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    const int y = ty0 + ly + 4 * q;
-    nct += nc[q];
-    if (x < W && y < H) {
-      const int64_t pix = ((int64_t)v * H + y) * W + x;
-      image[pix] = C[q];
-      tfinal[pix] = T[q];
-      last[pix] = lastp[q];
-      if (ncontrib) ncontrib[pix] = nc[q];
+  for (int pr = 0; pr < NP; ++pr) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (PPT == 1 && h == 1) continue;
+      const int y = ty0 + ly + 4 * (2 * pr + h);
+      nct += nc[pr][h];
+      if (x < W && y < H) {
+        const int64_t pix = ((int64_t)v * H + y) * W + x;
+        image[pix] = h ? C[pr].y : C[pr].x;
+        tfinal[pix] = h ? T[pr].y : T[pr].x;
+        last[pix] = lastp[pr][h];
+        if (ncontrib) ncontrib[pix] = nc[pr][h];
+      }
     }
   }
   add_counts(nev, nct, &st->fwd_evaluated, &st->fwd_contrib);
@@ -252,6 +329,10 @@ cudaError_t launch_render_fwd(xg_frame* f, float* image, uint32_t* n_contrib, cu
 // ------------------------------------------------------------------------------------------
 // backward
 // ------------------------------------------------------------------------------------------
+// Backward.  Pixels are taken in pairs as in the forward kernel.  A pixel of the pair that
+// does not contribute to an entry takes alpha = 0 there, which leaves its transmittance,
+// its blended-behind intensity and every gradient term unchanged, so the pair's update is
+// one packed, branch-free sequence.
 template <int kBatch, int PPT>
 __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ range, const uint32_t* __restrict__ value,
                                                     const float4* __restrict__ rec, int64_t n, int n_views, int W,
@@ -260,7 +341,9 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
                                                     const float* __restrict__ grad_image,
                                                     const float* __restrict__ tfinal, const uint32_t* __restrict__ last,
                                                     float* __restrict__ g2d) {
-  __shared__ float4 s_a[kBatch], s_b[kBatch], s_box[kBatch];
+  constexpr int NP = PPT > 1 ? PPT / 2 : 1;
+  __shared__ float4 s_q[4][kBatch];
+  __shared__ float4 s_box[kBatch];
   __shared__ uint32_t s_g[kBatch];
   __shared__ __align__(16) float s_acc[kBatch * 8];
   __shared__ uint16_t s_list[kMaxWarps][kBatch];
@@ -275,29 +358,36 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
   const float bx0 = (float)(tx0 + (lx & ~7)), by0 = (float)(ty0 + (ly & ~3));
   const float by1 = by0 + (float)(4 * PPT - 1);
   const Camera cam = cams[v];
-  const float px = fsub((float)x, cam.hw);
+  const float2 npx = f2(-fsub((float)x, cam.hw));
   const uint2 r = range[(int64_t)v * tiles_per_view + tile];
   const int64_t vn_base = (int64_t)v * n;
   uint16_t* my_list = s_list[warp];
 
-  float py[PPT], G[PPT], Tc[PPT], A[PPT];
-  uint32_t L[PPT];
+  float2 npy[NP], G[NP], Tc[NP], A[NP];
+  uint32_t L[NP][2];
   uint32_t lmax = 0;
 #pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    const int y = ty0 + ly + 4 * q;
-    py[q] = fsub((float)y, cam.hh);
-    G[q] = 0.f;
-    Tc[q] = 1.f;
-    A[q] = 0.f;  // intensity blended behind the current position, per unit transmittance
-    L[q] = 0;
-    if (x < W && y < H) {
-      const int64_t pix = ((int64_t)v * H + y) * W + x;
-      G[q] = grad_image[pix];
-      Tc[q] = tfinal[pix];
-      L[q] = G[q] != 0.f ? last[pix] : 0u;
+  for (int pr = 0; pr < NP; ++pr) {
+    float ny[2], g[2], tc[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int y = ty0 + ly + 4 * (2 * pr + h);
+      ny[h] = -fsub((float)y, cam.hh);
+      g[h] = 0.f;
+      tc[h] = 1.f;
+      L[pr][h] = 0;
+      if ((PPT > 1 || h == 0) && x < W && y < H) {
+        const int64_t pix = ((int64_t)v * H + y) * W + x;
+        g[h] = grad_image[pix];
+        tc[h] = tfinal[pix];
+        L[pr][h] = g[h] != 0.f ? last[pix] : 0u;
+      }
+      lmax = max(lmax, L[pr][h]);
     }
-    lmax = max(lmax, L[q]);
+    npy[pr] = make_float2(ny[0], ny[1]);
+    G[pr] = make_float2(g[0], g[1]);
+    Tc[pr] = make_float2(tc[0], tc[1]);
+    A[pr] = f2(0.f);  // intensity blended behind the current position, per unit transmittance
   }
   if (threadIdx.x == 0) s_maxlast = 0;
   __syncthreads();
@@ -313,50 +403,62 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
   for (int end_pos = maxl; end_pos > 0; end_pos -= kBatch) {
     const int base = max(0, end_pos - kBatch);
     const int cnt = end_pos - base;
-    stage_batch(value, rec, vn_base, r.x + base, cnt, cam, s_a, s_b, s_box, s_g);
+    stage_batch_pairs<kBatch>(value, rec, vn_base, r.x + base, cnt, cam, s_q, s_box, s_g);
     for (int i = threadIdx.x; i < cnt * 8; i += blockDim.x) s_acc[i] = 0.f;
     __syncthreads();
     if ((uint32_t)base < wl) {
-      const int m = warp_list(s_box, min(cnt, (int)wl - base), bx0, by0, by1, my_list, lane);
+      const int m = warp_list<kBatch>(s_q, s_box, min(cnt, (int)wl - base), bx0, by0, by1, cam, my_list, lane);
       for (int k = m - 1; k >= 0; --k) {
         const int j = my_list[k];
-        const float4 a = s_a[j];
-        const float4 b = s_b[j];
-        float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float4 q0 = s_q[0][j], q1 = s_q[1][j], q2 = s_q[2][j], q3 = s_q[3][j];
+        const float2 dx = fadd2(make_float2(q0.x, q0.y), npx);
+        const uint32_t pos = (uint32_t)(base + j);
+        // packed sums over the thread's pixels: six moments of dp = dL/dpower (dp, dp d,
+        // dp d d^T) and dL/dintensity
+        float2 gm[7];
+#pragma unroll
+        for (int t = 0; t < 7; ++t) gm[t] = f2(0.f);
         bool contrib = false;
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-          if ((uint32_t)(base + j) >= L[q]) continue;
-          ++nev;
-          float dx, dy;
-          const float p = power_of(a, b.x, px, py[q], dx, dy);
-          if (p < b.w) continue;
-          const float e = xg_exp(p);
-          const float oe = fmul(b.y, e);
-          const float al = fminf(kAlphaMax, oe);
-          if (al < kAlphaMin) continue;
+        for (int pr = 0; pr < NP; ++pr) {
+          const bool act0 = pos < L[pr][0], act1 = pos < L[pr][1];
+          if (!(act0 || act1)) continue;
+          nev += (uint32_t)act0 + (uint32_t)act1;
+          const float2 dy = fadd2(make_float2(q0.z, q0.w), npy[pr]);
+          const float2 t = ffma2(make_float2(q1.x, q1.y), dx, fmul2(make_float2(q1.z, q1.w), dy));
+          const float2 p = ffma2(dx, t, fmul2(fmul2(make_float2(q2.x, q2.y), dy), dy));
+          const bool in0 = act0 && !(p.x < q3.z), in1 = act1 && !(p.y < q3.z);
+          if (!(in0 || in1)) continue;
+          const float2 oe = fmul2(make_float2(q2.z, q2.w), xg_exp2v(p));
+          const float2 al = make_float2(fminf(kAlphaMax, oe.x), fminf(kAlphaMax, oe.y));
+          const bool ok0 = in0 && !(al.x < kAlphaMin), ok1 = in1 && !(al.y < kAlphaMin);
+          if (!(ok0 || ok1)) continue;
           contrib = true;
-          ++ncon;
-          Tc[q] = __fdividef(Tc[q], 1.f - al);
-          const float in = b.z;
-          gv[6] += G[q] * al * Tc[q];                 // dL/d intensity
-          const float dL_dal = G[q] * Tc[q] * (in - A[q]);
-          A[q] = al * in + (1.f - al) * A[q];
-          if (oe < kAlphaMax) {
-            // moments of dp = dL/d power: sum dp (dL/d opacity = sum dp / opacity, as
-            // d sigma / d opacity = e^p = sigma / opacity) and sum dp d, dp d d^T; the
-            // conic and the opacity enter once per Gaussian at the flush
-            const float dp = dL_dal * al;
-            const float sx = dp * dx, sy = dp * dy;
-            gv[0] += sx;
-            gv[1] += sy;
-            gv[2] += sx * dx;
-            gv[3] += sx * dy;
-            gv[4] += sy * dy;
-            gv[5] += dp;
-          }
+          ncon += (uint32_t)ok0 + (uint32_t)ok1;
+          // alpha of the pixels that contribute, 0 for the other one
+          const float2 alm = make_float2(ok0 ? al.x : 0.f, ok1 ? al.y : 0.f);
+          const float2 omal = ffma2(alm, f2(-1.0f), f2(1.0f));
+          Tc[pr] = make_float2(__fdividef(Tc[pr].x, omal.x), __fdividef(Tc[pr].y, omal.y));
+          const float2 gw = fmul2(G[pr], Tc[pr]);                           // dL/dC T
+          gm[6] = ffma2(gw, alm, gm[6]);                                    // dL/d intensity
+          const float2 dl_dal = fmul2(gw, ffma2(A[pr], f2(-1.0f), make_float2(q3.x, q3.y)));
+          A[pr] = ffma2(alm, make_float2(q3.x, q3.y), fmul2(omal, A[pr]));
+          // dp = dL/dalpha alpha where the opacity is not clamped (the clamp has zero slope)
+          const float2 aln = make_float2(oe.x < kAlphaMax ? alm.x : 0.f, oe.y < kAlphaMax ? alm.y : 0.f);
+          const float2 dp = fmul2(dl_dal, aln);
+          const float2 sx = fmul2(dp, dx), sy = fmul2(dp, dy);
+          gm[0] = fadd2(gm[0], sx);
+          gm[1] = fadd2(gm[1], sy);
+          gm[2] = ffma2(sx, dx, gm[2]);
+          gm[3] = ffma2(sx, dy, gm[3]);
+          gm[4] = ffma2(sy, dy, gm[4]);
+          gm[5] = fadd2(gm[5], dp);
         }
         if (__any_sync(0xffffffffu, contrib)) {
+          float gv[8];
+#pragma unroll
+          for (int t = 0; t < 7; ++t) gv[t] = gm[t].x + gm[t].y;
+          gv[7] = 0.f;
           const float sum = warp_reduce_scatter8(gv, lane);
           const int t8 = (lane >> 2) & 7;
           if ((lane & 3) == 0 && t8 < 7) atomicAdd(&s_acc[j * 8 + t8], sum);
@@ -373,11 +475,11 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
       const float4 m1 = *reinterpret_cast<const float4*>(&s_acc[j * 8 + 4]);
       if (m0.x != 0.f || m0.y != 0.f || m0.z != 0.f || m0.w != 0.f || m1.x != 0.f || m1.y != 0.f ||
           m1.z != 0.f) {
-        const float4 a = s_a[j];  // (u_x, u_y, -a/2, -b)
-        const float nc = s_b[j].x;  // -c/2
-        const float4 q0 = make_float4(2.f * a.z * m0.x + a.w * m0.y, a.w * m0.x + 2.f * nc * m0.y, -0.5f * m0.z,
+        const float na = s_q[1][j].x, nb = s_q[1][j].z;  // -a/2, -b
+        const float nc = s_q[2][j].x, o = s_q[2][j].z;   // -c/2, opacity
+        const float4 q0 = make_float4(2.f * na * m0.x + nb * m0.y, nb * m0.x + 2.f * nc * m0.y, -0.5f * m0.z,
                                       -m0.w);
-        const float4 q1 = make_float4(-0.5f * m1.x, __fdividef(m1.y, s_b[j].y), m1.z, 0.f);
+        const float4 q1 = make_float4(-0.5f * m1.x, __fdividef(m1.y, o), m1.z, 0.f);
         float4* dst = reinterpret_cast<float4*>(g2d + 8 * (vn_base + s_g[j]));
         atomicAdd(dst, q0);
         atomicAdd(dst + 1, q1);

@@ -86,6 +86,36 @@ __device__ __forceinline__ float xg_exp(float x) {
   return fmul(p, __int_as_float(((int)k + 127) << 23));
 }
 
+// Packed two-lane FP32 (the f32x2 instructions of sm_100 and later): each lane is rounded
+// exactly as the scalar operation, so packed and scalar sequences give the same bits.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// xg_exp of two values, lane for lane bit-identical to it: rint is taken by adding and
+// subtracting 1.5 * 2^23 (exact, ties to even, for |x log2 e| < 2^22), whose sum also holds
+// the integer k in its low mantissa bits.
+__device__ __forceinline__ float2 xg_exp2v(float2 x) {
+  constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
+  constexpr int kRoundBits = 0x4B400000;
+  x.x = fmaxf(x.x, -80.0f);
+  x.y = fmaxf(x.y, -80.0f);
+  const float2 m = fadd2(fmul2(x, f2(kLog2e)), f2(kRound));
+  const float2 k = fadd2(m, f2(-kRound));
+  float2 r = ffma2(k, f2(-kLn2Hi), x);
+  r = ffma2(k, f2(-kLn2Lo), r);
+  float2 p = ffma2(r, f2((float)(1.0 / 720.0)), f2((float)(1.0 / 120.0)));
+  p = ffma2(p, r, f2((float)(1.0 / 24.0)));
+  p = ffma2(p, r, f2((float)(1.0 / 6.0)));
+  p = ffma2(p, r, f2(0.5f));
+  p = ffma2(p, r, f2(1.0f));
+  p = ffma2(p, r, f2(1.0f));
+  const float2 scale = make_float2(__int_as_float((__float_as_int(m.x) - kRoundBits + 127) << 23),
+                                   __int_as_float((__float_as_int(m.y) - kRoundBits + 127) << 23));
+  return fmul2(p, scale);
+}
+
 // ln x for finite x >= 1: x = m 2^e, m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s), s = (m-1)/(m+1).
 __device__ __forceinline__ float xg_log_ge1(float x) {
   const unsigned b = __float_as_uint(x);
