@@ -323,6 +323,67 @@ int64_t xg_acui_count(const double size_mm[3], const int32_t grid[3], double int
 xg_status xg_acui_points(const double size_mm[3], const int32_t grid[3], double interval, float* mean,
                          int64_t capacity, void* stream);
 
+/* Adaptive density control.  The paper adjusts the number of Gaussians with the adaptive
+ * control of 3D Gaussian splatting (Sec. 3.2) without restating it; these calls follow that
+ * method's published rules.  Parameters are raw: centres, log-scales, quaternions, opacity
+ * logits and features, device SoA [3][n], [3][n], [4][n], [n], [n_features][n].  The same
+ * layout carries Adam's first and second moments. */
+typedef struct {
+  float* mean;
+  float* log_scale;
+  float* quat;
+  float* opacity_logit;
+  float* features;
+  int32_t n_features;
+  int32_t reserved; /* set to 0 */
+  int64_t n;
+} xg_param_set;
+
+/* Densify where accum / denom >= grad_thresh (FP32 division; never where denom = 0): a
+ * Gaussian whose largest log-scale is <= size_log_thresh is cloned (an identical copy),
+ * a larger one is split into two with centres mu + R diag(s) z_k and log-scales reduced by
+ * ln 1.6.  Prune where the opacity logit < prune_logit or the largest log-scale >
+ * max_log_size (INFINITY: never); children are tested with their own log-scales.  All
+ * comparisons are in FP32, none may be NaN. */
+typedef struct {
+  float grad_thresh;
+  float size_log_thresh;
+  float prune_logit;
+  float max_log_size;
+} xg_density_rules;
+
+/* Adds, for every Gaussian and every view of the frame's current pass in which it touches
+ * a tile, scale * |dL/du| (the projected-centre gradient written by the last xg_render_bwd)
+ * to accum[n] and 1 to denom[n] (device arrays, accumulated, not overwritten).  Enqueued on
+ * `stream`; graph-capturable.  Errors: XG_ERR_INVALID_ARG, XG_ERR_CUDA. */
+xg_status xg_densify_stats(xg_frame* frame, float scale, float* accum, int32_t* denom, void* stream);
+
+/* Device scratch bytes xg_densify_plan needs. */
+size_t xg_densify_workspace_bytes(void);
+
+/* The plan: offsets[g] (device, n + 1 entries) = first output slot of Gaussian g in the
+ * order [g if kept], [its clone], [child 0, child 1]; offsets[n] = the new count.  The
+ * caller reads offsets[n] to size the outputs of xg_densify_apply.  Requires 1 <= n <= 2^30.
+ * Errors: XG_ERR_INVALID_ARG, XG_ERR_CUDA. */
+xg_status xg_densify_plan(const xg_param_set* params, const float* accum, const int32_t* denom,
+                          const xg_density_rules* rules, uint32_t* offsets, void* workspace, void* stream);
+
+/* Writes the new parameters and Adam moments (out_* with n = offsets[n], same
+ * n_features): kept Gaussians keep their moments, clones and children start from zero
+ * moments.  normals: device [2][3][n] standard-normal samples z_k (drawn by the caller).
+ * Inputs and outputs must not overlap.  With a new count of 0 the outputs may be empty
+ * (NULL pointers) and nothing is written.  Errors: XG_ERR_INVALID_ARG, XG_ERR_CUDA. */
+xg_status xg_densify_apply(const xg_param_set* params, const xg_param_set* adam_m, const xg_param_set* adam_v,
+                           const float* accum, const int32_t* denom, const xg_density_rules* rules,
+                           const uint32_t* offsets, const float* normals, const xg_param_set* out_params,
+                           const xg_param_set* out_m, const xg_param_set* out_v, void* stream);
+
+/* Opacity reset: opacity_logit[g] = min(opacity_logit[g], reset_logit) (device, in place),
+ * and the opacity logits' Adam moments adam_m[n], adam_v[n] set to zero (either may be
+ * NULL).  Errors: XG_ERR_INVALID_ARG, XG_ERR_CUDA. */
+xg_status xg_opacity_reset(float* opacity_logit, float* adam_m, float* adam_v, int64_t n, float reset_logit,
+                           void* stream);
+
 /* Largest pair count xg_sort_pairs_noalloc accepts. */
 #define XG_NOALLOC_MAX_PAIRS (1 << 20)
 

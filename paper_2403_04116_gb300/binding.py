@@ -18,7 +18,8 @@ XG_ERR_WORKSPACE = 4
 XG_ERR_CHECK = 5
 
 # Every symbol include/xg.h declares.
-EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_frame_select_views", "xg_acui_count", "xg_acui_points", "xg_frame_copy_status", "xg_project",
+EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_frame_select_views", "xg_densify_stats", "xg_densify_workspace_bytes",
+           "xg_densify_plan", "xg_densify_apply", "xg_opacity_reset", "xg_acui_count", "xg_acui_points", "xg_frame_copy_status", "xg_project",
            "xg_bin_sort",
            "xg_render_fwd", "xg_render_bwd", "xg_frame_read_status", "xg_frame_layout", "xg_loss_l1",
            "xg_frame_set_timing", "xg_frame_read_timing", "xg_activate", "xg_activate_bwd",
@@ -78,6 +79,17 @@ class XgAdamGroup(ctypes.Structure):
     _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
                 ("v", ctypes.c_void_p), ("count", ctypes.c_int64), ("lr", ctypes.c_float),
                 ("lr_final", ctypes.c_float), ("decay_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class XgParamSet(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("log_scale", ctypes.c_void_p), ("quat", ctypes.c_void_p),
+                ("opacity_logit", ctypes.c_void_p), ("features", ctypes.c_void_p), ("n_features", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("n", ctypes.c_int64)]
+
+
+class XgDensityRules(ctypes.Structure):
+    _fields_ = [("grad_thresh", ctypes.c_float), ("size_log_thresh", ctypes.c_float),
+                ("prune_logit", ctypes.c_float), ("max_log_size", ctypes.c_float)]
 
 
 class XgError(RuntimeError):
@@ -153,6 +165,17 @@ def lib(build_if_missing: bool = False):
     L.xg_adam_step.argtypes = [ctypes.POINTER(XgAdamGroup), ctypes.c_int32, P, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, P]
     L.xg_adam_step.restype = ctypes.c_int
+    PS = ctypes.POINTER(XgParamSet)
+    L.xg_densify_stats.argtypes = [P, ctypes.c_float, P, P, P]
+    L.xg_densify_stats.restype = ctypes.c_int
+    L.xg_densify_workspace_bytes.argtypes = []
+    L.xg_densify_workspace_bytes.restype = ctypes.c_size_t
+    L.xg_densify_plan.argtypes = [PS, P, P, ctypes.POINTER(XgDensityRules), P, P, P]
+    L.xg_densify_plan.restype = ctypes.c_int
+    L.xg_densify_apply.argtypes = [PS, PS, PS, P, P, ctypes.POINTER(XgDensityRules), P, P, PS, PS, PS, P]
+    L.xg_densify_apply.restype = ctypes.c_int
+    L.xg_opacity_reset.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_float, P]
+    L.xg_opacity_reset.restype = ctypes.c_int
     L.xg_psnr.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, P, P]
     L.xg_psnr.restype = ctypes.c_int
     L.xg_sort_pairs_noalloc.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int32, P, P, P, P]
@@ -285,6 +308,32 @@ def xg_loss_l1_ssim(image: int, target: int, n_views: int, width: int, height: i
 def xg_adam_step(groups, step: int, beta1: float, beta2: float, eps: float, stream: int) -> None:
     arr = (XgAdamGroup * len(groups))(*groups)
     _check(lib().xg_adam_step(arr, len(groups), step, beta1, beta2, eps, stream), "xg_adam_step")
+
+
+def xg_densify_stats(frame: int, scale: float, accum: int, denom: int, stream: int) -> None:
+    _check(lib().xg_densify_stats(frame, scale, accum, denom, stream), "xg_densify_stats")
+
+
+def xg_densify_workspace_bytes() -> int:
+    return int(lib().xg_densify_workspace_bytes())
+
+
+def xg_densify_plan(params: XgParamSet, accum: int, denom: int, rules: XgDensityRules, offsets: int, workspace: int,
+                    stream: int) -> None:
+    _check(lib().xg_densify_plan(ctypes.byref(params), accum, denom, ctypes.byref(rules), offsets, workspace, stream),
+           "xg_densify_plan")
+
+
+def xg_densify_apply(params: XgParamSet, m: XgParamSet, v: XgParamSet, accum: int, denom: int, rules: XgDensityRules,
+                     offsets: int, normals: int, out: XgParamSet, out_m: XgParamSet, out_v: XgParamSet,
+                     stream: int) -> None:
+    _check(lib().xg_densify_apply(ctypes.byref(params), ctypes.byref(m), ctypes.byref(v), accum, denom,
+                                  ctypes.byref(rules), offsets, normals, ctypes.byref(out), ctypes.byref(out_m),
+                                  ctypes.byref(out_v), stream), "xg_densify_apply")
+
+
+def xg_opacity_reset(opacity_logit: int, adam_m, adam_v, n: int, reset_logit: float, stream: int) -> None:
+    _check(lib().xg_opacity_reset(opacity_logit, adam_m, adam_v, n, reset_logit, stream), "xg_opacity_reset")
 
 
 def xg_psnr(image: int, target: int, n_views: int, pixels_per_view: int, psnr: int, stream: int) -> None:

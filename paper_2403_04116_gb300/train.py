@@ -9,8 +9,9 @@ into fixed groups, one frame and one captured graph per group, replayed in turn.
     python -m paper_2403_04116_gb300.train [--steps 20000] [--gaussians 200000] ...
 
 prints one JSON line: wall time, steps/s, training loss, held-out PSNR before and after.
-The number of Gaussians is fixed (the paper's adaptive density control is not part of
-this build).  ``--init acui`` starts from the ACUI grid of Eq. 13 (xg_acui_points) instead
+``--densify`` turns on adaptive density control (clone / split / prune and the opacity
+reset, by the published rules of 3D Gaussian splatting, which the paper adopts); without
+it the number of Gaussians stays fixed.  ``--init acui`` starts from the ACUI grid of Eq. 13 (xg_acui_points) instead
 of cuboid-uniform Gaussians; ``--noise 0.03`` adds the paper's 3 % projection noise to the
 training targets (held-out PSNR is taken against the noise-free projections).
 """
@@ -49,6 +50,20 @@ class TrainConfig:
     beta2: float = 0.999
     eps: float = 1e-15
     decay_steps: int = 20000
+    # adaptive density control (3D Gaussian splatting's published defaults; readings for
+    # X-ray: gradients of the projected centre in pixels are taken per view, scaled to
+    # normalised device units (W / 2) and to a loss averaged over one view)
+    densify: bool = False
+    densify_from: int = 500
+    densify_until: int = 15000
+    densify_interval: int = 100
+    opacity_reset_interval: int = 3000
+    grad_thresh: float = 2e-4
+    percent_dense: float = 0.01     # clone at or below, split above this fraction of the scene side
+    min_opacity: float = 0.005
+    max_size_fraction: float = 0.1  # prune Gaussians larger than this fraction of the scene side
+    reset_opacity: float = 0.01
+    seed: int = 0
 
 
 def raw_from_activated(g: dict, n_features: int, gen: np.random.Generator) -> dict:
@@ -110,6 +125,11 @@ class Trainer:
         self.views = list(views)
         self.targets = targets
         self.capacity_margin = capacity_margin
+        self.iteration = 0
+        self.gen = np.random.default_rng(cfg.seed)
+        self.accum = torch.zeros(n, device=self.device)
+        self.denom = torch.zeros(n, dtype=torch.int32, device=self.device)
+        self.dens_ws = torch.empty(B.xg_densify_workspace_bytes() // 4 + 4, dtype=torch.int32, device=self.device)
         self.frames, self.images, self.grad_images, self.loss_ws, self.graphs = [], [], [], [], []
         self._raw = self._raw_struct()
         self._groups = self._adam_groups()
@@ -131,8 +151,13 @@ class Trainer:
     def _activated(self) -> tuple:
         return (self.p["mean"], self.act["scale"], self.p["quat"], self.act["opacity"], self.act["intensity"])
 
+    def _param_set(self, d: dict) -> B.XgParamSet:
+        return B.XgParamSet(d["mean"].data_ptr(), d["log_scale"].data_ptr(), d["quat"].data_ptr(),
+                            d["opacity_logit"].data_ptr(), d["features"].data_ptr(), self.nf, 0, d["mean"].shape[1])
+
     def _build(self) -> None:
         s = _stream_handle()
+        self.frames, self.images, self.grad_images, self.loss_ws = [], [], [], []
         B.xg_activate(self._raw, self.act["scale"].data_ptr(), self.act["opacity"].data_ptr(),
                       self.act["intensity"].data_ptr(), s)
         for idx in self.groups:
@@ -164,22 +189,22 @@ class Trainer:
         B.xg_activate_bwd(self._raw, self.g_act["scale"].data_ptr(), self.g_act["opacity"].data_ptr(),
                           self.g_act["intensity"].data_ptr(), self.g["log_scale"].data_ptr(),
                           self.g["opacity_logit"].data_ptr(), self.g["features"].data_ptr(), s)
+        if self.cfg.densify:
+            # |dL/du| per visible view, in normalised device units for a one-view mean loss
+            B.xg_densify_stats(f.handle, float(f.V * f.W / 2), self.accum.data_ptr(), self.denom.data_ptr(), s)
         B.xg_adam_step(self._groups, self.step_count.data_ptr(), self.cfg.beta1, self.cfg.beta2, self.cfg.eps, s)
 
+    def _capture_group(self, gi: int) -> None:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._step_calls(gi)
+        self.graphs[gi] = g
+
     def capture(self) -> None:
-        """Record one CUDA graph per view group (each group is stepped once while warming up)."""
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            for gi in range(len(self.groups)):
-                self._step_calls(gi)
-        torch.cuda.current_stream().wait_stream(side)
-        self.check_capacity()
+        """Record one CUDA graph per view group that has none (recording runs nothing)."""
         for gi in range(len(self.groups)):
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
-                self._step_calls(gi)
-            self.graphs[gi] = g
+            if self.graphs[gi] is None:
+                self._capture_group(gi)
 
     def check_capacity(self) -> bool:
         """True when every frame's pairs fitted (synchronises); frames that overflowed are
@@ -196,19 +221,75 @@ class Trainer:
                 raise B.XgError(st.code, "training step")
         return ok
 
+    def _resize(self, n: int) -> None:
+        """Per-Gaussian work buffers for n Gaussians; frames and graphs are rebuilt."""
+        self.n = n
+        dev = self.device
+        self.g = {k: torch.zeros_like(v) for k, v in self.p.items()}
+        self.act = {"scale": torch.empty(3, n, device=dev), "opacity": torch.empty(n, device=dev),
+                    "intensity": torch.empty(n, device=dev)}
+        self.g_act = {"scale": torch.empty(3, n, device=dev), "opacity": torch.empty(n, device=dev),
+                      "intensity": torch.empty(n, device=dev)}
+        self.accum = torch.zeros(n, device=dev)
+        self.denom = torch.zeros(n, dtype=torch.int32, device=dev)
+        self._raw = self._raw_struct()
+        self._groups = self._adam_groups()
+        self._build()
+
+    def densify(self) -> int:
+        """One densify-and-prune round (synchronises once to read the new count); returns N."""
+        c, side = self.cfg, self.cfg.position_scale
+        rules = B.XgDensityRules(c.grad_thresh, math.log(c.percent_dense * side),
+                                 math.log(c.min_opacity / (1.0 - c.min_opacity)), math.log(c.max_size_fraction * side))
+        s = _stream_handle()
+        offsets = torch.empty(self.n + 1, dtype=torch.int32, device=self.device)
+        B.xg_densify_plan(self._param_set(self.p), self.accum.data_ptr(), self.denom.data_ptr(), rules,
+                          offsets.data_ptr(), self.dens_ws.data_ptr(), s)
+        n_new = int(offsets[self.n].item()) & 0xFFFFFFFF
+        if n_new == 0:
+            raise RuntimeError("density control pruned every Gaussian")
+        shapes = {"mean": (3,), "log_scale": (3,), "quat": (4,), "opacity_logit": (), "features": (self.nf,)}
+        new = [{k: torch.empty(*shp, n_new, device=self.device) for k, shp in shapes.items()} for _ in range(3)]
+        normals = torch.from_numpy(self.gen.standard_normal((2, 3, self.n)).astype(np.float32)).to(self.device)
+        B.xg_densify_apply(self._param_set(self.p), self._param_set(self.m), self._param_set(self.v),
+                           self.accum.data_ptr(), self.denom.data_ptr(), rules, offsets.data_ptr(), normals.data_ptr(),
+                           self._param_set(new[0]), self._param_set(new[1]), self._param_set(new[2]), s)
+        self.p, self.m, self.v = new
+        self._resize(n_new)
+        return n_new
+
+    def reset_opacity(self) -> None:
+        c = self.cfg
+        B.xg_opacity_reset(self.p["opacity_logit"].data_ptr(), self.m["opacity_logit"].data_ptr(),
+                           self.v["opacity_logit"].data_ptr(), self.n,
+                           math.log(c.reset_opacity / (1.0 - c.reset_opacity)), _stream_handle())
+
     # ---- public -------------------------------------------------------------------------
     def step(self, t: int) -> None:
+        """One training step on view group t mod groups: replayed from its graph, or run as
+        launches and then recorded (after a rebuild the next visit records it again)."""
         gi = t % len(self.groups)
         if self.graphs[gi] is None:
             self._step_calls(gi)
+            self._capture_group(gi)
         else:
             self.graphs[gi].replay()
 
     def train(self, steps: int, check_every: int = 500) -> None:
+        c = self.cfg
         for t in range(steps):
             self.step(t)
-            if check_every and (t + 1) % check_every == 0 and not self.check_capacity():
-                self.capture()
+            self.iteration += 1
+            it = self.iteration
+            changed = False
+            if c.densify and it < c.densify_until:
+                if it >= c.densify_from and it % c.densify_interval == 0:
+                    self.densify()
+                    changed = True
+                if it % c.opacity_reset_interval == 0:
+                    self.reset_opacity()
+            if check_every and it % check_every == 0 and not changed:
+                self.check_capacity()  # frames that overflowed are rebuilt; their graphs re-recorded
 
     @torch.no_grad()
     def render(self, views) -> torch.Tensor:
@@ -256,12 +337,14 @@ def main() -> None:
     ap.add_argument("--acui-grid", type=int, default=256, help="voxels per axis M of Eq. 13")
     ap.add_argument("--acui-interval", type=float, default=8.0, help="sampling interval d of Eq. 13")
     ap.add_argument("--noise", type=float, default=0.0, help="projection noise level (0.03 in the paper)")
+    ap.add_argument("--densify", action="store_true", help="adaptive density control (clone / split / prune)")
     args = ap.parse_args()
     tw_th, b, p = args.tile.split(":")
     tw, th = (int(x) for x in tw_th.split("x"))
     fcfg = FrameConfig(tw, th, batch=int(b), pixels_per_thread=int(p))
     side, tr_v, tr_t, te_v, te_t, g = config3(args.gaussians, args.detector)
-    cfg = TrainConfig(views_per_step=args.views_per_step, position_scale=side, decay_steps=args.steps)
+    cfg = TrainConfig(views_per_step=args.views_per_step, position_scale=side, decay_steps=args.steps,
+                      densify=args.densify)
     B.lib(build_if_missing=True)
     if args.init == "acui":
         raw = acui_raw(side, args.acui_grid, args.acui_interval, cfg.n_features)
@@ -272,6 +355,7 @@ def main() -> None:
     dev = torch.device("cuda")
     tr_t, te_t = torch.from_numpy(tr_t).to(dev), torch.from_numpy(te_t).to(dev)
     trainer = Trainer(raw, tr_v, tr_t, cfg, fcfg)
+    n_start = trainer.n
     psnr0 = trainer.psnr(te_v, te_t)
     trainer.capture()
     torch.cuda.synchronize()
@@ -281,8 +365,8 @@ def main() -> None:
     wall = time.perf_counter() - t0
     loss = trainer.loss.cpu().numpy()
     psnr1 = trainer.psnr(te_v, te_t)
-    print(json.dumps({"workload": "config3", "init": args.init, "noise": args.noise,
-                      "gaussians": trainer.n, "detector": args.detector,
+    print(json.dumps({"workload": "config3", "init": args.init, "noise": args.noise, "densify": args.densify,
+                      "gaussians_start": n_start, "gaussians": trainer.n, "detector": args.detector,
                       "train_views": len(tr_v), "test_views": len(te_v), "views_per_step": args.views_per_step,
                       "steps": args.steps, "wall_s": wall, "steps_per_s": args.steps / wall,
                       "last_loss": float(loss[0]), "last_l1": float(loss[1]), "last_ssim": float(loss[2]),
