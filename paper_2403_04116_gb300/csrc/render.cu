@@ -34,37 +34,51 @@ namespace xg {
 
 constexpr int kMaxWarps = 16;  // 512-thread tiles
 
-// Packed staging for the pixel-pair kernels: every field duplicated so that one broadcast
-// shared load yields both lanes of a packed operand.  s_q[0..3][j] = (u_x u_x u_y u_y),
+// One list entry staged for the pixel-pair kernels: every field duplicated so that one
+// broadcast shared load yields both lanes of a packed operand.  q0..q3 = (u_x u_x u_y u_y),
 // (na na nb nb), (nc nc o o), (i i thr thr) with na, nb, nc = -a/2, -b, -c/2 and thr the
-// exponent threshold; s_box as in stage_batch.
+// exponent threshold; box = conservative pixel box (x0, x1, y0, y1) of the footprint.
+struct Staged {
+  float4 q0, q1, q2, q3, box;
+};
+
+__device__ __forceinline__ Staged stage_record(const float4 a, const float4 b, const Camera& cam) {
+  Staged e;
+  const float na = -0.5f * a.z, nb = -a.w, nc = -0.5f * b.x;
+  // ln(255 o) with the fast hardware log (absolute error below 1e-5 here): the threshold
+  // keeps a 1e-4 margin and the box 0.1 % + 0.01 px, so both stay conservative
+  const float l255o = __logf(255.f * b.y);
+  const float thr = -l255o - 1e-4f;
+  e.q0 = make_float4(a.x, a.x, a.y, a.y);
+  e.q1 = make_float4(na, na, nb, nb);
+  e.q2 = make_float4(nc, nc, b.y, b.y);
+  e.q3 = make_float4(b.z, b.z, thr, thr);
+  const float two_l = 2.f * fmaxf(l255o, 0.f);
+  const float det = a.z * b.x - a.w * a.w;
+  float ex = INFINITY, ey = INFINITY;
+  if (det > 0.f) {
+    const float sdet = __fdividef(two_l, det);
+    ex = __fsqrt_rn(sdet * b.x) * 1.001f + 0.01f;
+    ey = __fsqrt_rn(sdet * a.z) * 1.001f + 0.01f;
+  }
+  const float cx = a.x + cam.hw, cy = a.y + cam.hh;
+  e.box = make_float4(cx - ex, cx + ex, cy - ey, cy + ey);
+  return e;
+}
+
+// Stages list entries [first, first + cnt) of a tile into shared memory for the whole CTA.
 template <int kBatch>
 __device__ __forceinline__ void stage_batch_pairs(const uint32_t* __restrict__ value, const float4* __restrict__ rec,
                                                   int64_t vn_base, uint32_t first, int cnt, const Camera& cam,
                                                   float4 (*s_q)[kBatch], float4* s_box, uint32_t* s_g) {
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     const uint32_t g = value[first + j];
-    const float4 a = rec[2 * (vn_base + g)];
-    const float4 b = rec[2 * (vn_base + g) + 1];
-    const float na = -0.5f * a.z, nb = -a.w, nc = -0.5f * b.x;
-    // ln(255 o) with the fast hardware log (absolute error below 1e-5 here): the threshold
-    // keeps a 1e-4 margin and the box 0.1 % + 0.01 px, so both stay conservative
-    const float l255o = __logf(255.f * b.y);
-    const float thr = -l255o - 1e-4f;
-    s_q[0][j] = make_float4(a.x, a.x, a.y, a.y);
-    s_q[1][j] = make_float4(na, na, nb, nb);
-    s_q[2][j] = make_float4(nc, nc, b.y, b.y);
-    s_q[3][j] = make_float4(b.z, b.z, thr, thr);
-    const float two_l = 2.f * fmaxf(l255o, 0.f);
-    const float det = a.z * b.x - a.w * a.w;
-    float ex = INFINITY, ey = INFINITY;
-    if (det > 0.f) {
-      const float s = __fdividef(two_l, det);
-      ex = __fsqrt_rn(s * b.x) * 1.001f + 0.01f;
-      ey = __fsqrt_rn(s * a.z) * 1.001f + 0.01f;
-    }
-    const float cx = a.x + cam.hw, cy = a.y + cam.hh;
-    s_box[j] = make_float4(cx - ex, cx + ex, cy - ey, cy + ey);
+    const Staged e = stage_record(rec[2 * (vn_base + g)], rec[2 * (vn_base + g) + 1], cam);
+    s_q[0][j] = e.q0;
+    s_q[1][j] = e.q1;
+    s_q[2][j] = e.q2;
+    s_q[3][j] = e.q3;
+    s_box[j] = e.box;
     if (s_g) s_g[j] = g;
   }
 }
@@ -90,12 +104,21 @@ __device__ __forceinline__ float max_power_over_rect(float na, float nb, float n
   return best;
 }
 
-// The staged entries whose footprint can reach this warp's pixel block [bx0, bx0+7] x
-// [by0, by1] (pixel indices), in list order; returns their count.  An entry is kept when its
-// box meets the block and the largest exponent over the block's pixel centres is within a
-// margin (1e-2 + 1e-3 |thr|, far above FP32 rounding of these sums) of the threshold below
-// which no pixel can reach opacity 1/255: only entries that no pixel of the block could
-// take are dropped, so decisions are unchanged.
+// Whether a footprint can reach the warp's pixel block [bx0, bx0+7] x [by0, by1] (pixel
+// indices): its box meets the block and the largest exponent over the block's pixel centres
+// is within a margin (1e-2 + 1e-3 |thr|, far above FP32 rounding of these sums) of the
+// threshold below which no pixel can reach opacity 1/255.  Only entries that no pixel of the
+// block could take fail, so decisions are unchanged.
+__device__ __forceinline__ bool reaches_block(const float4 box, float ux, float uy, float na, float nb, float nc,
+                                              float thr, float bx0, float by0, float by1, const Camera& cam) {
+  if (!(box.x <= bx0 + 7.f && box.y >= bx0 && box.z <= by1 && box.w >= by0)) return false;
+  const float cx = ux + cam.hw, cy = uy + cam.hh;
+  const float best = max_power_over_rect(na, nb, nc, cx - (bx0 + 7.f), cx - bx0, cy - by1, cy - by0);
+  return best >= thr - (1e-2f + 1e-3f * fabsf(thr));
+}
+
+// The staged entries that can reach this warp's block (reaches_block), in list order;
+// returns their count.
 template <int kBatch>
 __device__ __forceinline__ int warp_list(const float4 (*s_q)[kBatch], const float4* s_box, int cnt, float bx0,
                                          float by0, float by1, const Camera& cam, uint16_t* list, int lane) {
@@ -103,18 +126,8 @@ __device__ __forceinline__ int warp_list(const float4 (*s_q)[kBatch], const floa
   int m = 0;
   for (int j0 = 0; j0 < cnt; j0 += 32) {
     const int j = j0 + lane;
-    bool hit = false;
-    if (j < cnt) {
-      const float4 bx = s_box[j];
-      hit = bx.x <= bx0 + 7.f && bx.y >= bx0 && bx.z <= by1 && bx.w >= by0;
-      if (hit) {
-        const float cx = s_q[0][j].x + cam.hw, cy = s_q[0][j].z + cam.hh;
-        const float thr = s_q[3][j].z;
-        const float best = max_power_over_rect(s_q[1][j].x, s_q[1][j].z, s_q[2][j].x, cx - (bx0 + 7.f), cx - bx0,
-                                               cy - by1, cy - by0);
-        hit = best >= thr - (1e-2f + 1e-3f * fabsf(thr));
-      }
-    }
+    const bool hit = j < cnt && reaches_block(s_box[j], s_q[0][j].x, s_q[0][j].z, s_q[1][j].x, s_q[1][j].z,
+                                              s_q[2][j].x, s_q[3][j].z, bx0, by0, by1, cam);
     const uint32_t mask = __ballot_sync(0xffffffffu, hit);
     if (hit) list[m + __popc(mask & lt_mask)] = (uint16_t)j;
     m += __popc(mask);
@@ -176,6 +189,51 @@ __device__ __forceinline__ float power_of(const float4 a, const float nc, float 
   return ffma(dx, t, fmul(fmul(nc, dy), dy));
 }
 
+// One list entry for a thread's pixel pairs: exponent, exp, opacity, transmittance and
+// colour of both pixels of each pair with packed instructions, decisions per pixel.
+template <int NP>
+__device__ __forceinline__ void fwd_entry(const float4 q0, const float4 q1, const float4 q2, const float4 q3,
+                                          uint32_t pos, float2 npx, const float2 (&npy)[NP], float2 (&T)[NP],
+                                          float2 (&C)[NP], uint32_t (&nc)[NP][2], uint32_t (&lastp)[NP][2],
+                                          bool (&done)[NP][2], uint32_t& nev) {
+  const float2 dx = fadd2(make_float2(q0.x, q0.y), npx);
+#pragma unroll
+  for (int pr = 0; pr < NP; ++pr) {
+    if (done[pr][0] && done[pr][1]) continue;
+    // the exponent dx (na dx + nb dy) + (nc dy) dy of both pixels
+    const float2 dy = fadd2(make_float2(q0.z, q0.w), npy[pr]);
+    const float2 t = ffma2(make_float2(q1.x, q1.y), dx, fmul2(make_float2(q1.z, q1.w), dy));
+    const float2 p = ffma2(dx, t, fmul2(fmul2(make_float2(q2.x, q2.y), dy), dy));
+    nev += (uint32_t)!done[pr][0] + (uint32_t)!done[pr][1];
+    const bool in0 = !done[pr][0] && !(p.x < q3.z), in1 = !done[pr][1] && !(p.y < q3.z);
+    if (!(in0 || in1)) continue;  // opacity provably below 1/255 for both
+    const float2 oe = fmul2(make_float2(q2.z, q2.w), xg_exp2v(p));
+    const float2 al = make_float2(fminf(kAlphaMax, oe.x), fminf(kAlphaMax, oe.y));
+    const float2 Tn = fmul2(T[pr], ffma2(al, f2(-1.0f), f2(1.0f)));
+    const float2 Cn = ffma2(make_float2(q3.x, q3.y), fmul2(al, T[pr]), C[pr]);
+    if (in0 && !(al.x < kAlphaMin)) {
+      if (Tn.x < kTMin) {
+        done[pr][0] = true;
+      } else {
+        C[pr].x = Cn.x;
+        T[pr].x = Tn.x;
+        ++nc[pr][0];
+        lastp[pr][0] = pos;
+      }
+    }
+    if (in1 && !(al.y < kAlphaMin)) {
+      if (Tn.y < kTMin) {
+        done[pr][1] = true;
+      } else {
+        C[pr].y = Cn.y;
+        T[pr].y = Tn.y;
+        ++nc[pr][1];
+        lastp[pr][1] = pos;
+      }
+    }
+  }
+}
+
 // Forward.  A thread's pixels are taken in pairs (4 rows apart; for one pixel per thread
 // the second of the pair is idle), and the exponent, exp, opacity, transmittance and colour
 // of both are computed with packed two-lane instructions; the decisions stay per pixel.
@@ -187,9 +245,6 @@ __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ ra
                                                     float* __restrict__ image, uint32_t* __restrict__ ncontrib,
                                                     float* __restrict__ tfinal, uint32_t* __restrict__ last) {
   constexpr int NP = PPT > 1 ? PPT / 2 : 1;  // pixel pairs per thread
-  __shared__ float4 s_q[4][kBatch];
-  __shared__ float4 s_box[kBatch];
-  __shared__ uint16_t s_list[kMaxWarps][kBatch];
   const int tile = blockIdx.x, v = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int lx, ly;
@@ -203,7 +258,6 @@ __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ ra
   const uint2 r = st->code == XG_OK ? range[(int64_t)v * tiles_per_view + tile] : make_uint2(0u, 0u);
   const int nlist = (int)(r.y - r.x);
   const int64_t vn_base = (int64_t)v * n;
-  uint16_t* my_list = s_list[warp];
 
   float2 npy[NP], T[NP], C[NP];
   uint32_t nc[NP][2], lastp[NP][2];
@@ -229,6 +283,10 @@ __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ ra
     for (int pr = 0; pr < NP; ++pr) d = d && done[pr][0] && done[pr][1];
     return d;
   };
+  __shared__ float4 s_q[4][kBatch];
+  __shared__ float4 s_box[kBatch];
+  __shared__ uint16_t s_list[kMaxWarps][kBatch];
+  uint16_t* my_list = s_list[warp];
   for (int base = 0; base < nlist; base += kBatch) {
     if (__syncthreads_count(all_done()) == (int)blockDim.x) break;
     const int cnt = min(kBatch, nlist - base);
@@ -240,44 +298,8 @@ __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ ra
     for (int k = 0; k < m; ++k) {
       if (all_done()) break;
       const int j = my_list[k];
-      const float4 q0 = s_q[0][j], q1 = s_q[1][j], q2 = s_q[2][j], q3 = s_q[3][j];
-      const float2 dx = fadd2(make_float2(q0.x, q0.y), npx);
-      const uint32_t pos = (uint32_t)(base + j + 1);
-#pragma unroll
-      for (int pr = 0; pr < NP; ++pr) {
-        if (done[pr][0] && done[pr][1]) continue;
-        // the exponent dx (na dx + nb dy) + (nc dy) dy of both pixels
-        const float2 dy = fadd2(make_float2(q0.z, q0.w), npy[pr]);
-        const float2 t = ffma2(make_float2(q1.x, q1.y), dx, fmul2(make_float2(q1.z, q1.w), dy));
-        const float2 p = ffma2(dx, t, fmul2(fmul2(make_float2(q2.x, q2.y), dy), dy));
-        nev += (uint32_t)!done[pr][0] + (uint32_t)!done[pr][1];
-        const bool in0 = !done[pr][0] && !(p.x < q3.z), in1 = !done[pr][1] && !(p.y < q3.z);
-        if (!(in0 || in1)) continue;  // opacity provably below 1/255 for both
-        const float2 oe = fmul2(make_float2(q2.z, q2.w), xg_exp2v(p));
-        const float2 al = make_float2(fminf(kAlphaMax, oe.x), fminf(kAlphaMax, oe.y));
-        const float2 Tn = fmul2(T[pr], ffma2(al, f2(-1.0f), f2(1.0f)));
-        const float2 Cn = ffma2(make_float2(q3.x, q3.y), fmul2(al, T[pr]), C[pr]);
-        if (in0 && !(al.x < kAlphaMin)) {
-          if (Tn.x < kTMin) {
-            done[pr][0] = true;
-          } else {
-            C[pr].x = Cn.x;
-            T[pr].x = Tn.x;
-            ++nc[pr][0];
-            lastp[pr][0] = pos;
-          }
-        }
-        if (in1 && !(al.y < kAlphaMin)) {
-          if (Tn.y < kTMin) {
-            done[pr][1] = true;
-          } else {
-            C[pr].y = Cn.y;
-            T[pr].y = Tn.y;
-            ++nc[pr][1];
-            lastp[pr][1] = pos;
-          }
-        }
-      }
+      fwd_entry<NP>(s_q[0][j], s_q[1][j], s_q[2][j], s_q[3][j], (uint32_t)(base + j + 1), npx, npy, T, C, nc,
+                    lastp, done, nev);
     }
   }
   uint32_t nct = 0;
@@ -415,9 +437,7 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
         const uint32_t pos = (uint32_t)(base + j);
         // packed sums over the thread's pixels: six moments of dp = dL/dpower (dp, dp d,
         // dp d d^T) and dL/dintensity
-        float2 gm[7];
-#pragma unroll
-        for (int t = 0; t < 7; ++t) gm[t] = f2(0.f);
+        float2 gm[7];  // set by the thread's first contributing pair, then accumulated
         bool contrib = false;
 #pragma unroll
         for (int pr = 0; pr < NP; ++pr) {
@@ -433,31 +453,41 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
           const float2 al = make_float2(fminf(kAlphaMax, oe.x), fminf(kAlphaMax, oe.y));
           const bool ok0 = in0 && !(al.x < kAlphaMin), ok1 = in1 && !(al.y < kAlphaMin);
           if (!(ok0 || ok1)) continue;
-          contrib = true;
           ncon += (uint32_t)ok0 + (uint32_t)ok1;
           // alpha of the pixels that contribute, 0 for the other one
           const float2 alm = make_float2(ok0 ? al.x : 0.f, ok1 ? al.y : 0.f);
           const float2 omal = ffma2(alm, f2(-1.0f), f2(1.0f));
           Tc[pr] = make_float2(__fdividef(Tc[pr].x, omal.x), __fdividef(Tc[pr].y, omal.y));
-          const float2 gw = fmul2(G[pr], Tc[pr]);                           // dL/dC T
-          gm[6] = ffma2(gw, alm, gm[6]);                                    // dL/d intensity
+          const float2 gw = fmul2(G[pr], Tc[pr]);  // dL/dC T; gw alm is the dL/d intensity term
           const float2 dl_dal = fmul2(gw, ffma2(A[pr], f2(-1.0f), make_float2(q3.x, q3.y)));
           A[pr] = ffma2(alm, make_float2(q3.x, q3.y), fmul2(omal, A[pr]));
           // dp = dL/dalpha alpha where the opacity is not clamped (the clamp has zero slope)
           const float2 aln = make_float2(oe.x < kAlphaMax ? alm.x : 0.f, oe.y < kAlphaMax ? alm.y : 0.f);
           const float2 dp = fmul2(dl_dal, aln);
           const float2 sx = fmul2(dp, dx), sy = fmul2(dp, dy);
-          gm[0] = fadd2(gm[0], sx);
-          gm[1] = fadd2(gm[1], sy);
-          gm[2] = ffma2(sx, dx, gm[2]);
-          gm[3] = ffma2(sx, dy, gm[3]);
-          gm[4] = ffma2(sy, dy, gm[4]);
-          gm[5] = fadd2(gm[5], dp);
+          if (!contrib) {
+            gm[0] = sx;
+            gm[1] = sy;
+            gm[2] = fmul2(sx, dx);
+            gm[3] = fmul2(sx, dy);
+            gm[4] = fmul2(sy, dy);
+            gm[5] = dp;
+            gm[6] = fmul2(gw, alm);
+            contrib = true;
+          } else {
+            gm[0] = fadd2(gm[0], sx);
+            gm[1] = fadd2(gm[1], sy);
+            gm[2] = ffma2(sx, dx, gm[2]);
+            gm[3] = ffma2(sx, dy, gm[3]);
+            gm[4] = ffma2(sy, dy, gm[4]);
+            gm[5] = fadd2(gm[5], dp);
+            gm[6] = ffma2(gw, alm, gm[6]);
+          }
         }
         if (__any_sync(0xffffffffu, contrib)) {
           float gv[8];
 #pragma unroll
-          for (int t = 0; t < 7; ++t) gv[t] = gm[t].x + gm[t].y;
+          for (int t = 0; t < 7; ++t) gv[t] = contrib ? gm[t].x + gm[t].y : 0.f;
           gv[7] = 0.f;
           const float sum = warp_reduce_scatter8(gv, lane);
           const int t8 = (lane >> 2) & 7;
