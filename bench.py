@@ -255,6 +255,26 @@ def cpu_oracle_rate(name: str, target_seconds: float = 12.0) -> dict:
             "sample": f"FP64 oracle {what}, {sample}"}
 
 
+def cpu_replica_rate(name: str, target_seconds: float = 6.0) -> dict:
+    """The FP32 replica (the tiled forward of the kernels' decision sequence, in C on the host
+    cores), whole views: a second CPU reference beside the FP64 oracle."""
+    import oracle
+    w, g, views, _ = _workload(name)
+    tile = tuple(w["tile"])
+    t0 = time.perf_counter()
+    oracle.replica_full(g, views[0], tile)
+    t1 = time.perf_counter() - t0
+    k = max(1, min(len(views), int(round(target_seconds / max(t1, 1e-3)))))
+    ids = [(i * max(1, len(views) // k)) % len(views) for i in range(k)]
+    t0 = time.perf_counter()
+    for i in ids:
+        oracle.replica_full(g, views[i], tile)
+    t = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": len(ids) / t, "unit": "projections/s", "cores": threads, "kind": "fp32 replica, forward",
+            "sample": f"{len(ids)} of {w['views']} views, {tile[0]}x{tile[1]} tiles, {t:.1f} s"}
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -473,9 +493,10 @@ def run_ours(args) -> None:
         e2e_autograd = {"value": timed_host(e2e_step), "unit": "projections/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": 4, "path": "render() autograd + L1Loss, uncaptured stream launches"}
 
-    cpu = None
+    cpu = cpu_replica = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_rate(args.workload)
+        cpu_replica = cpu_replica_rate(args.workload)
 
     if rank == 0:
         cfg_line = _config(args.workload, w, world)
@@ -493,7 +514,7 @@ def run_ours(args) -> None:
                     "ms_per_step": ms_plain / plain_steps},
                 "stream_launched": {"ms_per_step": ms_stream_step},
                 "clocks": clock_info, "e2e": e2e, "e2e_autograd": e2e_autograd, "gpu_launches": gpu_launches,
-                "roofline": roof, "cpu_baseline": cpu, "pairs": int(st.pairs),
+                "roofline": roof, "cpu_baseline": cpu, "cpu_replica": cpu_replica, "pairs": int(st.pairs),
                 "work": {"fwd_evaluated": int(st.fwd_evaluated), "fwd_contrib": int(st.fwd_contrib),
                          "bwd_evaluated": int(st.bwd_evaluated), "bwd_contrib": int(st.bwd_contrib)},
                 "kernels_ms_per_step": {k: round(v[1] / timing_steps, 4) for k, v in sorted(kernels.items())}}
