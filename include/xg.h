@@ -129,9 +129,12 @@ typedef struct {
  *   count      uint32[V*n]    tiles touched
  *   offset     uint32[V*n]    exclusive prefix sum of count, taken over the (view,
  *                             Gaussian) entries in (view, t_z, index) order
- *   key_tile   uint32[cap]    sorted pairs: view * T + tile
+ *   key_tile   uint32[cap]    sorted pairs: key view * S + tile, S = range_stride (the
+ *                             power of two >= T); pairs are ordered by (tile, view, t_z,
+ *                             index), so every (view, tile) list is contiguous
  *   value      uint32[cap]    sorted pairs: Gaussian index
- *   range      uint32[V*T][2] [start, end) of each tile in the sorted pairs ([0, 0) if empty)
+ *   range      uint32[V*S][2] [start, end) of (view, tile) at view * S + tile in the sorted
+ *                             pairs ([0, 0) if empty or tile >= T)
  *   tfinal     float[V][H][W] transmittance after the last contributor
  *   last       uint32[V][H][W] 1-based position in the tile's list of the last contributor
  *   grad2d     float[V*n][8]  per (view, Gaussian): dL/du_x, dL/du_y, dL/da, dL/db, dL/dc,
@@ -142,7 +145,7 @@ typedef struct {
   int64_t tiles_per_view;
   int32_t tiles_x, tiles_y;
   int32_t sort_passes;
-  int32_t reserved;
+  int32_t range_stride; /* S: power of two >= tiles_per_view */
 } xg_layout;
 
 typedef struct xg_frame xg_frame;

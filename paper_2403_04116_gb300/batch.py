@@ -229,11 +229,11 @@ def autotune_scan(n: int, views, gaussians: tuple, tiles=((16, 16), (32, 16)), p
     b0, p0 = shapes[0]
     for tw, th in tiles:
         for vpp in passes:
-            tiles_per_view = -(-views[0].width // tw) * -(-views[0].height // th)
-            if vpp * tiles_per_view > (1 << 16) and vpp != passes[0]:
-                continue  # a third stage-3 radix pass
             cfg = FrameConfig(tw, th, batch=b0, pixels_per_thread=p0)
-            ms = time_scan(cfg, vpp)
+            try:
+                ms = time_scan(cfg, vpp)
+            except (ValueError, B.XgError):
+                continue  # more pairs per pass than one frame indexes
             if best is None or ms < best[2]:
                 best = (cfg, vpp, ms)
     cfg0, vpp, _ = best

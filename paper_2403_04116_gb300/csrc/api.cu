@@ -39,21 +39,25 @@ bool valid_sizes(int64_t n, int32_t n_views, int32_t per_pass, int32_t W, int32_
 struct Sizes {
   int32_t tiles_x, tiles_y;
   int64_t tiles_per_view;
-  int32_t tile_bits, entry_passes, tile_passes;
+  int32_t tile_bits;   // bits of a tile index within its view: pair key = view << tile_bits | tile
+  int64_t range_keys;  // n_views << tile_bits
+  int32_t entry_passes, tile_passes;
 };
 
 bool sizes_of(const xg_config* cfg, int64_t n_views, int32_t W, int32_t H, Sizes* s) {
   s->tiles_x = (W + cfg->tile_w - 1) / cfg->tile_w;
   s->tiles_y = (H + cfg->tile_h - 1) / cfg->tile_h;
   s->tiles_per_view = (int64_t)s->tiles_x * s->tiles_y;
-  const int64_t keys = n_views * s->tiles_per_view;
-  if (keys >= ((int64_t)1 << 31)) return false;
   int bits = 0;
-  while (((int64_t)1 << bits) < keys) ++bits;
+  while (((int64_t)1 << bits) < s->tiles_per_view) ++bits;
+  s->range_keys = n_views << bits;
+  if (s->range_keys >= ((int64_t)1 << 31)) return false;
   int vbits = 0;
   while (((int64_t)1 << vbits) < n_views) ++vbits;
   s->tile_bits = bits;
   s->entry_passes = 4 + (vbits + 7) / 8;
+  // the emitted pairs are already in view order, so a stable sort by the tile bits alone
+  // leaves every (tile, view) list contiguous and in depth order
   s->tile_passes = (bits + 7) / 8;
   return true;
 }
@@ -92,7 +96,7 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t n_scan, in
   for (int b = 0; b < 2; ++b) o->key_tile[b] = take(4 * cap);
   for (int b = 0; b < 2; ++b) o->value[b] = take(4 * cap);
   o->hist = take(4 * 256 * ((size_t)xg::kSortBlocks + 1));
-  o->range = take(8 * (size_t)V * (size_t)s->tiles_per_view);
+  o->range = take(8 * (size_t)s->range_keys);
   o->tfinal = take(4 * pix);
   o->last = take(4 * pix);
   o->grad2d = take(4 * 8 * VN);
@@ -201,6 +205,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   f->tiles_y = s.tiles_y;
   f->tiles_per_view = s.tiles_per_view;
   f->tile_bits = s.tile_bits;
+  f->range_keys = s.range_keys;
   f->entry_passes = s.entry_passes;
   f->tile_passes = s.tile_passes;
   f->sorted_buf = s.tile_passes & 1;  // each pass moves the pairs to the other buffer
@@ -249,6 +254,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   L.tiles_x = s.tiles_x;
   L.tiles_y = s.tiles_y;
   L.sort_passes = s.entry_passes + s.tile_passes;
+  L.range_stride = 1 << s.tile_bits;
 
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = xg::radix_prepare();  // kernel attributes, set outside any stream capture

@@ -1,20 +1,21 @@
 // Tile binning and the depth-keyed radix sort (Sec. 3.2: Gaussians are assigned to the
 // tiles their projection touches and sorted by depth).
 //
-// The (tile, depth) order of the pairs is built in two stable LSD radix sorts, so that the
-// many pairs (one per touched tile) are moved only by their tile key:
+// The (view, tile, depth) order of the pairs is built in two stable LSD radix sorts, so
+// that the many pairs (one per touched tile) are moved only by their tile index:
 //
 //   1. the V*n (view, Gaussian) entries, keyed (view, bits of t_z) -- 4 depth passes and
 //      ceil(log2(V)/8) view passes over V*n entries (k_project writes the keys);
 //   2. the tile counts, gathered in that order, are prefix-summed and every entry emits one
-//      (view * T + tile, Gaussian) pair per touched tile at its offset, so the emitted list
-//      is ordered by (view, depth, index);
-//   3. the pairs are sorted stably by tile key alone (ceil(log2(V*T)/8) passes), which
-//      leaves every tile's list in (depth, index) order;
-//   4. ranges: [start, end) per (view, tile).
+//      (view << B | tile, Gaussian) pair per touched tile at its offset (B = ceil(log2 T)),
+//      so the emitted list is ordered by (view, depth, index);
+//   3. the pairs are sorted stably by the B tile bits alone (ceil(B/8) passes): the list
+//      ends up ordered by (tile, view, depth, index), every (view, tile) list contiguous and
+//      in (depth, index) order;
+//   4. ranges: [start, end) per (view, tile), indexed by the pair key view << B | tile.
 //
-// The result equals a stable sort of all pairs by the 64-bit key (tile, bits of t_z) of an
-// index-ordered emission, at well under half of its memory traffic.
+// Each (view, tile) list equals a stable sort of that tile's pairs by the bits of t_z, at
+// well under half of the memory traffic of sorting all pairs by a 64-bit key.
 //
 // Every kernel here runs on a fixed grid of kSortBlocks CTAs that split the work into
 // contiguous chunks computed on the device from the item count, so the host never needs to
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* __re
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ count, const uint32_t* __restrict__ offset,
                                               const ushort4* __restrict__ rect, const uint32_t* __restrict__ view,
                                               const uint32_t* __restrict__ gid, int64_t n, int64_t total,
-                                              int tiles_x, int64_t tiles_per_view, int64_t capacity,
+                                              int tiles_x, int tile_bits, int64_t capacity,
                                               DevStatus* __restrict__ st, uint32_t* __restrict__ key_tile,
                                               uint32_t* __restrict__ value) {
   if (st->code != XG_OK) return;
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ count
       const uint32_t x0 = e_xy0 & 0xffffu, y0 = e_xy0 >> 16, x1 = e_xy1 & 0xffffu;
       const uint32_t wdt = x1 - x0 + 1u;
       const uint32_t ty = y0 + k / wdt, tx = x0 + k % wdt;
-      key_tile[base + p] = (uint32_t)(e_v * tiles_per_view) + ty * (uint32_t)tiles_x + tx;
+      key_tile[base + p] = (e_v << tile_bits) | (ty * (uint32_t)tiles_x + tx);
       value[base + p] = e_g;
     }
   }
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ count
 // from array `digit_word`.  Histograms are block-major: hist[block][256], then the 256
 // digit totals.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ word, int shift,
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ word, int shift, uint32_t mask,
                                                              const DevStatus* __restrict__ st, int64_t fixed_count,
                                                              uint32_t* __restrict__ hist) {
   __shared__ uint32_t s_h[kWarps][256];
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
   const int64_t total = items_of(st, fixed_count);
   const int64_t chunk = chunk_of(total);
   const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
-  for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&s_h[warp][(word[i] >> shift) & 255u], 1u);
+  for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&s_h[warp][(word[i] >> shift) & mask], 1u);
   __syncthreads();
   uint32_t c = 0;
 #pragma unroll
@@ -294,6 +295,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // the rest (a chunk's ragged last tile, unaligned caller arrays) are loaded directly.
 template <int WORDS, int DW>
 __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(SortArrays<WORDS> arr, int shift,
+                                                                                uint32_t mask,
                                                                 DevStatus* __restrict__ st, int64_t fixed_count,
                                                                 const uint32_t* __restrict__ hist) {
   extern __shared__ __align__(128) uint32_t s_dyn[];  // [2][WORDS][kSortTile]
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
     for (int k = 0; k < kSortItems; ++k) {
       const int64_t i = base + warp * (32 * kSortItems) + k * 32 + lane;
       const bool valid = i < end;
-      dig[k] = valid ? ((item[k][DW] >> shift) & 255u) : 256u;
+      dig[k] = valid ? ((item[k][DW] >> shift) & mask) : 256u;
       const uint32_t peers = __match_any_sync(0xffffffffu, dig[k]);
       const int leader = __ffs(peers) - 1;
       if constexpr (WORDS == 2) {
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
     __syncthreads();
     const int n_tile = (int)min((int64_t)kSortTile, end - base);
     for (int i = tid; i < n_tile; i += kSortThreads) {
-      const uint32_t d = (BUF(j, DW)[i] >> shift) & 255u;
+      const uint32_t d = (BUF(j, DW)[i] >> shift) & mask;
       const uint32_t pos = s_delta[d] + (uint32_t)i;
       if ((int64_t)pos >= total) {  // cannot happen when the histograms are right
         st->code = XG_ERR_CHECK;
@@ -493,13 +495,14 @@ cudaError_t radix_prepare() {
 }
 
 template <int WORDS>
-cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, int64_t fixed_count,
+cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, uint32_t mask,
+                       int64_t fixed_count,
                        DevStatus* status, uint32_t* hist, cudaStream_t st) {
   const cudaError_t prep = radix_prepare();
   if (prep != cudaSuccess) return prep;
   {
     Timed t(f, kRadixHist, st);
-    k_radix_hist<<<kSortBlocks, kSortThreads, 0, st>>>(arr.in[digit_word], shift, status, fixed_count, hist);
+    k_radix_hist<<<kSortBlocks, kSortThreads, 0, st>>>(arr.in[digit_word], shift, mask, status, fixed_count, hist);
   }
   {
     Timed t(f, kRadixScan, st);
@@ -509,16 +512,16 @@ cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word
     Timed t(f, kRadixScatter, st);
     constexpr size_t smem = scatter_smem<WORDS>();
     if (digit_word == 0)
-      k_radix_scatter<WORDS, 0><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, status, fixed_count, hist);
+      k_radix_scatter<WORDS, 0><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, mask, status, fixed_count, hist);
     else
-      k_radix_scatter<WORDS, 1><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, status, fixed_count, hist);
+      k_radix_scatter<WORDS, 1><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, mask, status, fixed_count, hist);
   }
   return cudaGetLastError();
 }
 
-template cudaError_t radix_pass<2>(xg_frame*, const SortArrays<2>&, int, int, int64_t, DevStatus*, uint32_t*,
+template cudaError_t radix_pass<2>(xg_frame*, const SortArrays<2>&, int, int, uint32_t, int64_t, DevStatus*, uint32_t*,
                                     cudaStream_t);
-template cudaError_t radix_pass<3>(xg_frame*, const SortArrays<3>&, int, int, int64_t, DevStatus*, uint32_t*,
+template cudaError_t radix_pass<3>(xg_frame*, const SortArrays<3>&, int, int, uint32_t, int64_t, DevStatus*, uint32_t*,
                                     cudaStream_t);
 
 cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
@@ -532,7 +535,7 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     SortArrays<3> arr;
     arr.in[0] = p.ent_view[cur], arr.in[1] = p.ent_depth[cur], arr.in[2] = p.ent_gid[cur];
     arr.out[0] = p.ent_view[cur ^ 1], arr.out[1] = p.ent_depth[cur ^ 1], arr.out[2] = p.ent_gid[cur ^ 1];
-    const cudaError_t e = radix_pass<3>(f, arr, digit_word, shift, VN, p.status, p.hist, st);
+    const cudaError_t e = radix_pass<3>(f, arr, digit_word, shift, 255u, VN, p.status, p.hist, st);
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }
@@ -554,7 +557,7 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   {
     Timed t(f, kEmit, st);
     k_emit<<<(unsigned)((VN + 255) / 256), 256, 0, st>>>(p.count, p.offset, p.rect, ent_view, ent_gid, f->n, VN,
-                                                         f->tiles_x, f->tiles_per_view, f->cfg.pair_capacity,
+                                                         f->tiles_x, f->tile_bits, f->cfg.pair_capacity,
                                                          p.status, p.key_tile[0], p.value[0]);
   }
   // stage 3: stable sort of the pairs by tile key
@@ -563,7 +566,10 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     SortArrays<2> arr;
     arr.in[0] = p.key_tile[pc], arr.in[1] = p.value[pc];
     arr.out[0] = p.key_tile[pc ^ 1], arr.out[1] = p.value[pc ^ 1];
-    const cudaError_t e = radix_pass<2>(f, arr, 0, 8 * pass, -1, p.status, p.hist, st);
+    // the last pass takes only the tile bits left: the view bits above them must not move pairs
+    const int left = f->tile_bits - 8 * pass;
+    const uint32_t mask = left >= 8 ? 255u : (1u << left) - 1u;
+    const cudaError_t e = radix_pass<2>(f, arr, 0, 8 * pass, mask, -1, p.status, p.hist, st);
     if (e != cudaSuccess) return e;
     pc ^= 1;
   }
@@ -571,12 +577,12 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   cudaError_t e;
   {
     Timed t(f, kMemset, st);
-    e = cudaMemsetAsync(p.range, 0, sizeof(uint2) * (size_t)(f->n_views * f->tiles_per_view), st);
+    e = cudaMemsetAsync(p.range, 0, sizeof(uint2) * (size_t)f->range_keys, st);
   }
   if (e != cudaSuccess) return e;
   {
     Timed t(f, kRanges, st);
-    k_ranges<<<kSortBlocks * 4, 256, 0, st>>>(p.key_tile[pc], (int64_t)f->n_views * f->tiles_per_view, p.status,
+    k_ranges<<<kSortBlocks * 4, 256, 0, st>>>(p.key_tile[pc], f->range_keys, p.status,
                                                p.range);
   }
   return cudaGetLastError();

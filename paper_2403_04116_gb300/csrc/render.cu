@@ -240,7 +240,7 @@ __device__ __forceinline__ void fwd_entry(const float4 q0, const float4 q1, cons
 template <int kBatch, int PPT>
 __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ range, const uint32_t* __restrict__ value,
                                                     const float4* __restrict__ rec, int64_t n, int W, int H,
-                                                    int tiles_x, int64_t tiles_per_view, int tw, int th,
+                                                    int tiles_x, int64_t range_stride, int tw, int th,
                                                     const Camera* __restrict__ cams, DevStatus* __restrict__ st,
                                                     float* __restrict__ image, uint32_t* __restrict__ ncontrib,
                                                     float* __restrict__ tfinal, uint32_t* __restrict__ last) {
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ ra
   const float by1 = by0 + (float)(4 * PPT - 1);
   const Camera cam = cams[v];
   const float2 npx = f2(-fsub((float)x, cam.hw));
-  const uint2 r = st->code == XG_OK ? range[(int64_t)v * tiles_per_view + tile] : make_uint2(0u, 0u);
+  const uint2 r = st->code == XG_OK ? range[(int64_t)v * range_stride + tile] : make_uint2(0u, 0u);
   const int nlist = (int)(r.y - r.x);
   const int64_t vn_base = (int64_t)v * n;
 
@@ -330,7 +330,7 @@ cudaError_t launch_render_fwd(xg_frame* f, float* image, uint32_t* n_contrib, cu
   const int threads = f->cfg.tile_w * f->cfg.tile_h / ppt;
 #define XG_FWD(B, P)                                                                                       \
   k_render_fwd<B, P><<<grid, threads, 0, st>>>(p.range, p.value[f->sorted_buf], p.rec, f->n, f->width,    \
-                                               f->height, f->tiles_x, f->tiles_per_view, f->cfg.tile_w,   \
+                                               f->height, f->tiles_x, (int64_t)1 << f->tile_bits, f->cfg.tile_w,   \
                                                f->cfg.tile_h, p.cam, p.status, image, n_contrib, p.tfinal, \
                                                p.last)
   switch (ppt * 1000 + f->cfg.batch) {
@@ -358,7 +358,7 @@ cudaError_t launch_render_fwd(xg_frame* f, float* image, uint32_t* n_contrib, cu
 template <int kBatch, int PPT>
 __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ range, const uint32_t* __restrict__ value,
                                                     const float4* __restrict__ rec, int64_t n, int n_views, int W,
-                                                    int H, int tiles_x, int64_t tiles_per_view, int tw, int th,
+                                                    int H, int tiles_x, int64_t range_stride, int tw, int th,
                                                     const Camera* __restrict__ cams, DevStatus* __restrict__ st,
                                                     const float* __restrict__ grad_image,
                                                     const float* __restrict__ tfinal, const uint32_t* __restrict__ last,
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
   const float by1 = by0 + (float)(4 * PPT - 1);
   const Camera cam = cams[v];
   const float2 npx = f2(-fsub((float)x, cam.hw));
-  const uint2 r = range[(int64_t)v * tiles_per_view + tile];
+  const uint2 r = range[(int64_t)v * range_stride + tile];
   const int64_t vn_base = (int64_t)v * n;
   uint16_t* my_list = s_list[warp];
 
@@ -535,7 +535,7 @@ cudaError_t launch_render_bwd(xg_frame* f, const float* grad_image, cudaStream_t
   const int threads = f->cfg.tile_w * f->cfg.tile_h / ppt;
 #define XG_BWD(B, P)                                                                                            \
   k_render_bwd<B, P><<<grid, threads, 0, st>>>(p.range, p.value[f->sorted_buf], p.rec, f->n, f->n_views,       \
-                                               f->width, f->height, f->tiles_x, f->tiles_per_view,             \
+                                               f->width, f->height, f->tiles_x, (int64_t)1 << f->tile_bits,             \
                                                f->cfg.tile_w, f->cfg.tile_h, p.cam, p.status, grad_image,      \
                                                p.tfinal, p.last, p.grad2d)
   switch (ppt * 1000 + f->cfg.batch) {

@@ -198,9 +198,10 @@ struct xg_frame {
   int32_t width, height;
   int32_t tiles_x, tiles_y;
   int64_t tiles_per_view;
-  int32_t tile_bits;     // bits of view * T + tile
+  int32_t tile_bits;     // bits of a tile index within its view: pair key = view << tile_bits | tile
+  int64_t range_keys;    // n_views << tile_bits: entries of the range array
   int32_t entry_passes;  // stage-1 passes: 4 depth bytes + view bytes
-  int32_t tile_passes;   // stage-3 passes over the pairs
+  int32_t tile_passes;   // stage-3 passes over the pairs (the tile bits only)
   int32_t sorted_buf;    // which ping-pong buffer holds the sorted pairs
   void* workspace;
   size_t workspace_bytes;
@@ -236,11 +237,12 @@ cudaError_t launch_loss_l1(const float* image, const float* target, int64_t coun
                            float* loss, cudaStream_t st);
 
 // One LSD radix pass (histogram, digit scan, stable scatter; binning.cu) over WORDS arrays,
-// the digit taken from arr.in[digit_word] >> shift.  The item count is `fixed_count` when it
-// is >= 0, else the pair count in the status word.  `f` may be NULL (no timing).
+// the digit (arr.in[digit_word] >> shift) & mask (mask <= 255).  The item count is
+// `fixed_count` when it is >= 0, else the pair count in the status word.  `f` may be NULL
+// (no timing).
 template <int WORDS>
-cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, int64_t fixed_count,
-                       DevStatus* status, uint32_t* hist, cudaStream_t st);
+cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, uint32_t mask,
+                       int64_t fixed_count, DevStatus* status, uint32_t* hist, cudaStream_t st);
 // Sets the scatter kernels' shared-memory attributes (once per process); call outside
 // stream capture before the first radix_pass.
 cudaError_t radix_prepare();

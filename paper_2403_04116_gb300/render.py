@@ -78,6 +78,7 @@ class Frame:
         self.layout = B.xg_frame_layout(self.handle)
         self.tiles_x, self.tiles_y = self.layout.tiles_x, self.layout.tiles_y
         self.tiles_per_view = self.layout.tiles_per_view
+        self.range_stride = self.layout.range_stride  # range entry of (view, tile): view * stride + tile
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -144,7 +145,7 @@ class Frame:
             "records": (torch.float32, (VN, 8)), "depth": (torch.float32, (VN,)), "rect": (torch.int16, (VN, 4)),
             "count": (torch.int32, (VN,)), "offset": (torch.int32, (VN,)), "key_tile": (torch.int32, (cap,)),
             "value": (torch.int32, (cap,)),
-            "range": (torch.int32, (self.V * self.tiles_per_view, 2)), "tfinal": (torch.float32, (P,)),
+            "range": (torch.int32, (self.V * self.range_stride, 2)), "tfinal": (torch.float32, (P,)),
             "last": (torch.int32, (P,)), "grad2d": (torch.float32, (VN, 8)),
         }
         dtype, shape = spec[name]

@@ -46,7 +46,7 @@ def run_forward(g: dict, views, tile=(16, 16), capacity=None, near_mm=0.2, batch
            "tfinal": f.array("tfinal").cpu().numpy().reshape(f.V, f.H, f.W),
            "last": f.array("last").cpu().numpy().reshape(f.V, f.H, f.W)}
     # depth key of every sorted pair, looked up from its (view, Gaussian)
-    views_of = out["key_tile"].astype(np.int64) // f.tiles_per_view
+    views_of = out["key_tile"].astype(np.int64) // f.range_stride
     out["key_depth"] = proj["depth"].view(np.uint32)[views_of * n + out["value"].astype(np.int64)]
     return out
 

@@ -56,7 +56,7 @@ def test_sampled_views_bit_exact_against_replica(workload):
     image = step.image.cpu().numpy()
     tfin = f.array("tfinal").cpu().numpy().reshape(V, W, W)
     last = f.array("last").cpu().numpy().view(np.uint32).reshape(V, W, W)
-    rng = f.array("range").cpu().numpy().view(np.uint32).reshape(V, -1, 2)
+    rng = f.array("range").cpu().numpy().view(np.uint32).reshape(V, f.range_stride, 2)[:, :f.tiles_per_view]
     val = f.array("value").cpu().numpy()
     for v in (0, 17, 49):
         rep = oracle.replica_full(workload["g"], workload["views"][v], tile)

@@ -58,21 +58,28 @@ def _case(name):
 
 
 def _expected_index(g, views, tile):
+    """The frame's sorted pairs and ranges built from the replica's per-view tile lists: the
+    (view, tile) lists laid out in (tile, view) order, keyed view * S + tile with S the power
+    of two >= T."""
     reps = [oracle.replica_full(g, v, tile) for v in views]
     T = reps[0]["range"].shape[0]
-    key_tile, value, key_depth, ranges = [], [], [], []
+    S = 1 << int(np.ceil(np.log2(T))) if T > 1 else 1
+    key_tile, value, key_depth = [], [], []
+    ranges = np.zeros((len(views) * S, 2), np.uint32)
     base = 0
-    for v, r in enumerate(reps):
-        lens = (r["range"][:, 1] - r["range"][:, 0]).astype(np.int64)
-        key_tile.append((v * T + np.repeat(np.arange(T), lens)).astype(np.uint32))
-        value.append(r["list"].astype(np.int32))
-        key_depth.append(r["depth"].view(np.uint32)[r["list"]])
-        rg = r["range"].astype(np.int64)
-        rg = np.where(lens[:, None] > 0, rg + base, 0)
-        ranges.append(rg.astype(np.uint32))
-        base += r["M"]
+    for t in range(T):
+        for v, r in enumerate(reps):
+            a, b = (int(x) for x in r["range"][t])
+            if b <= a:
+                continue
+            lst = r["list"][a:b]
+            key_tile.append(np.full(b - a, v * S + t, np.uint32))
+            value.append(lst.astype(np.int32))
+            key_depth.append(r["depth"].view(np.uint32)[lst])
+            ranges[v * S + t] = (base, base + b - a)
+            base += b - a
     return reps, {"key_tile": np.concatenate(key_tile), "value": np.concatenate(value),
-                  "key_depth": np.concatenate(key_depth), "range": np.concatenate(ranges), "M": base}
+                  "key_depth": np.concatenate(key_depth), "range": ranges, "M": base}
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))

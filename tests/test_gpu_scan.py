@@ -72,7 +72,7 @@ def test_view_bit_exact_against_replica(scan, v):
     k = v - first
     tfin = f.array("tfinal").cpu().numpy().reshape(-1, W, W)[k]
     last = f.array("last").cpu().numpy().view(np.uint32).reshape(-1, W, W)[k]
-    rng = f.array("range").cpu().numpy().view(np.uint32).reshape(-1, f.tiles_per_view, 2)[k]
+    rng = f.array("range").cpu().numpy().view(np.uint32).reshape(-1, f.range_stride, 2)[k, :f.tiles_per_view]
     f.select(0)
     np.testing.assert_array_equal(img[k].cpu().numpy().view(np.uint32), rep["image"].view(np.uint32))
     np.testing.assert_array_equal(tfin.view(np.uint32), rep["tfinal"].view(np.uint32))

@@ -43,9 +43,9 @@ def _binned_frame(n, n_views, W, H, tile, cid):
 
 
 def _emitted_pairs(f: Frame, M: int):
-    """Every (tile, depth, Gaussian) pair of the frame in (view, Gaussian index) order, each
-    Gaussian's tiles row-major -- an unsorted input whose stable sort by (tile, depth) is
-    the frame's sorted pair list."""
+    """Every pair of the frame in (view, Gaussian index) order, each Gaussian's tiles
+    row-major, keyed tile * V + view -- an unsorted input whose stable sort by (key, depth)
+    is the frame's sorted pair list, which is ordered by (tile, view, depth, index)."""
     rect = f.array("rect").cpu().numpy().astype(np.int64)
     count = f.array("count").cpu().numpy().view(np.uint32)
     offset = np.concatenate([[0], np.cumsum(count.astype(np.int64))[:-1]])
@@ -55,7 +55,7 @@ def _emitted_pairs(f: Frame, M: int):
         v, g = divmod(int(vg), f.n)
         x0, y0, x1, y1 = rect[vg]
         ys, xs = np.mgrid[y0:y1 + 1, x0:x1 + 1]
-        tiles = (v * f.tiles_per_view + ys.ravel() * f.tiles_x + xs.ravel()).astype(np.uint32)
+        tiles = ((ys.ravel() * f.tiles_x + xs.ravel()) * f.V + v).astype(np.uint32)
         o = int(offset[vg])
         kt[o:o + tiles.size] = tiles
         kd[o:o + tiles.size] = dbits[vg]
@@ -83,11 +83,12 @@ def test_noalloc_sort_matches_bin_sort_twice(first, second):
         keys = f.V * f.tiles_per_view
         tile_bits = int(np.ceil(np.log2(keys))) if keys > 1 else 0
         got = _sort_noalloc(kt, kd, val, tile_bits)
-        kt_s = f.array("key_tile")[:M].cpu().numpy().view(np.uint32)
+        key = f.array("key_tile")[:M].cpu().numpy().view(np.uint32).astype(np.int64)
+        view, tile = key // f.range_stride, key % f.range_stride
         val_s = f.array("value")[:M].cpu().numpy().view(np.uint32)
         dbits = f.array("depth").cpu().numpy().view(np.uint32)
-        kd_s = dbits[(kt_s.astype(np.int64) // f.tiles_per_view) * f.n + val_s]
-        want = [kt_s, kd_s, val_s]
+        kd_s = dbits[view * f.n + val_s]
+        want = [(tile * f.V + view).astype(np.uint32), kd_s, val_s]
         for g_, w_, name in zip(got, want, ("key_tile", "key_depth", "value")):
             np.testing.assert_array_equal(g_, w_, err_msg=name)
 
