@@ -132,3 +132,64 @@ def test_sampled_gradients_against_fp64_oracle(workload):
         checked += want.size
     assert checked == 40 * 12
     assert np.count_nonzero(np.abs(ora["mean"][:, sample]) > 1e-3) > 60  # gradients well above the floor
+
+
+def test_gradients_against_central_differences_on_200_parameters(workload):
+    """The GPU gradient of L = sum over two views of G * I (G = +-1, zero on ambiguous
+    pixels) against central differences (eps 1e-4) of the FP64 oracle's forward on 200
+    sampled (Gaussian, parameter) pairs, each rendered over its footprint pixels."""
+    g, views, step = workload["g"], workload["views"], workload["step"]
+    gen = np.random.default_rng(8)
+    vids = (3, 29)
+    G = np.zeros((V, W, W))
+    for v in vids:
+        r = oracle.render64(g, views[v])
+        Gv = gen.choice([-1.0, 1.0], size=(W, W))
+        Gv[r["ambiguous"] != 0] = 0.0
+        G[v] = Gv
+    f = step.frame
+    grads = tuple(torch.empty_like(t) for t in workload["dev"])
+    f.render_bwd(workload["dev"], torch.from_numpy(G.astype(np.float32)).cuda(), grads)
+    torch.cuda.synchronize()
+    gpu = {k: t.cpu().numpy().astype(np.float64) for k, t in zip(NAMES, grads)}
+    ora = None
+    for v in vids:  # the oracle's term magnitudes, for the FP32 part of the tolerance
+        ora = oracle.grad64(g, views[v], G[v], out=ora)
+    rows = {"mean": 3, "scale": 3, "quat": 4, "opacity": 1, "intensity": 1}
+    # Gaussians that contribute in both views
+    proj = [oracle.project64(g, views[v]) for v in vids]
+    visible = np.nonzero(proj[0][:, 0].astype(bool) & proj[1][:, 0].astype(bool))[0]
+    g64 = {k: np.asarray(x, np.float64) for k, x in g.items()}
+    eps, checked, tried = 1e-4, 0, 0
+    yy, xx = np.mgrid[0:W, 0:W]
+    while checked < 200 and tried < 400:
+        tried += 1
+        k = int(gen.choice(visible))
+        key = str(gen.choice(list(rows), p=[3 / 12, 3 / 12, 4 / 12, 1 / 12, 1 / 12]))
+        idx = (int(gen.integers(rows[key])), k) if rows[key] > 1 else (k,)
+        pix_of = []
+        for pr in proj:
+            ux, uy, A, C = pr[k, 4], pr[k, 5], pr[k, 6], pr[k, 8]
+            rr = np.sqrt(2 * max(np.log(255 * g["opacity"][k]), 0.0) * max(A, C)) + 3.0
+            box = (np.abs(xx + 0.5 - ux) <= rr) & (np.abs(yy + 0.5 - uy) <= rr)
+            pix_of.append(np.nonzero(box.reshape(-1))[0].astype(np.int32))
+        vals, cons = [], []
+        for sign in (1.0, -1.0):
+            gp = {kk: vv.copy() for kk, vv in g64.items()}
+            gp[key][idx] += sign * eps
+            total, nc = 0.0, []
+            for v, pix in zip(vids, pix_of):
+                r = oracle.render64(gp, views[v], pixels=pix)
+                total += float((r["image"].reshape(-1)[pix] * G[v].reshape(-1)[pix]).sum())
+                nc.append(r["ncontrib"].reshape(-1)[pix])
+            vals.append(total)
+            cons.append(np.concatenate(nc))
+        if not np.array_equal(cons[0], cons[1]):
+            continue  # a blending decision flips inside the stencil
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        got = gpu[key][idx]
+        mag = ora["mag"][key][idx]
+        assert abs(got - fd) <= GRAD_RTOL * abs(fd) + GRAD_ATOL + GRAD_TERM_REL * mag + 1e-4 * abs(fd), \
+            (key, idx, got, fd, mag)
+        checked += 1
+    assert checked >= 150, (checked, tried)
