@@ -52,7 +52,9 @@ typedef enum {
   XG_ERR_CUDA = 3,        /* a CUDA launch or copy failed; see cudaGetLastError */
   XG_ERR_WORKSPACE = 4,   /* the workspace is too small or misaligned */
   XG_ERR_CHECK = 5        /* a device-side bounds check failed, or a bounded wait in a kernel expired
-                             (a library or device defect); outputs invalid */
+                             (a library or device defect, or the XG_SPIN_LIMIT fault injection:
+                             that environment variable, read once per process, caps the
+                             kernels' first waits, 0 making every one expire); outputs invalid */
 } xg_status;
 
 /* One cone-beam projection (Sec. 3.3, Eq. 12).  The source orbits at distance sod_mm from

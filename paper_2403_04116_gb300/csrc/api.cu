@@ -2,6 +2,7 @@
 // FP32 camera table built from the scanner parameters (Sec. 3.3, Eq. 12), and the
 // stream-ordered launches of each stage.
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -141,6 +142,12 @@ __global__ void k_copy_status(const xg::DevStatus* __restrict__ s, xg_device_sta
   out->bwd_evaluated = (int64_t)s->bwd_evaluated;
   out->bwd_contrib = (int64_t)s->bwd_contrib;
 }
+
+// An NVTX range around one C-ABI stage call (host side: it marks the enqueueing).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 }  // namespace
 
@@ -357,22 +364,26 @@ static bool valid_gaussians(const xg_frame* f, const xg_gaussians* g) {
 }
 
 xg_status xg_project(xg_frame* frame, const xg_gaussians* g, void* stream) {
+  const Range range("xg_project");
   if (!frame || !valid_gaussians(frame, g)) return XG_ERR_INVALID_ARG;
   return xg::launch_project(frame, g, (cudaStream_t)stream) == cudaSuccess ? XG_OK : XG_ERR_CUDA;
 }
 
 xg_status xg_bin_sort(xg_frame* frame, void* stream) {
+  const Range range("xg_bin_sort");
   if (!frame) return XG_ERR_INVALID_ARG;
   return xg::launch_bin_sort(frame, (cudaStream_t)stream) == cudaSuccess ? XG_OK : XG_ERR_CUDA;
 }
 
 xg_status xg_render_fwd(xg_frame* frame, float* image, uint32_t* n_contrib, void* stream) {
+  const Range range("xg_render_fwd");
   if (!frame || !image) return XG_ERR_INVALID_ARG;
   return xg::launch_render_fwd(frame, image, n_contrib, (cudaStream_t)stream) == cudaSuccess ? XG_OK : XG_ERR_CUDA;
 }
 
 xg_status xg_render_bwd(xg_frame* frame, const xg_gaussians* g, const float* grad_image, const xg_grads* out,
                         void* stream) {
+  const Range range("xg_render_bwd");
   if (!frame || !valid_gaussians(frame, g) || !grad_image || !out || !out->mean || !out->scale || !out->quat ||
       !out->opacity || !out->intensity)
     return XG_ERR_INVALID_ARG;

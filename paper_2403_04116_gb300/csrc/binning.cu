@@ -21,6 +21,8 @@
 // contiguous chunks computed on the device from the item count, so the host never needs to
 // know the pair count and the whole sequence can be captured in a CUDA graph.  There is no
 // inter-CTA waiting: every scan is reduce / scan-of-partials / down-sweep in three launches.
+#include <stdlib.h>
+
 #include "xg_internal.cuh"
 
 namespace xg {
@@ -71,20 +73,33 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T& total) {
 // ------------------------------------------------------------------------------------------
 // scan of the tile counts, read in the (view, depth) order of stage 1
 // ------------------------------------------------------------------------------------------
+// Tile count of sorted entry i; an entry outside [0, V) x [0, n) (which a correct stage 1
+// never produces) counts 0 and records XG_ERR_CHECK.
 __device__ __forceinline__ uint32_t count_at(const uint32_t* __restrict__ count, const uint32_t* __restrict__ view,
-                                             const uint32_t* __restrict__ gid, int64_t n, int64_t i) {
-  return count[(int64_t)view[i] * n + gid[i]];
+                                             const uint32_t* __restrict__ gid, int64_t n, int64_t total, int64_t i,
+                                             DevStatus* __restrict__ st) {
+  const int64_t e = (int64_t)view[i] * n + gid[i];
+  if (gid[i] >= n || e >= total) {
+    st->code = XG_ERR_CHECK;
+    return 0u;
+  }
+  return count[e];
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_scan_reduce(const uint32_t* __restrict__ count,
                                                               const uint32_t* __restrict__ view,
                                                               const uint32_t* __restrict__ gid, int64_t n,
-                                                              int64_t total, unsigned long long* __restrict__ part) {
+                                                              int64_t total, DevStatus* __restrict__ st,
+                                                              unsigned long long* __restrict__ part) {
   __shared__ unsigned long long s_warp[kWarps];
+  if (st->code != XG_OK) {  // stage 1 failed a check: its entries are not to be read
+    if (threadIdx.x == 0) part[blockIdx.x] = 0ull;
+    return;
+  }
   const int64_t chunk = chunk_of(total);
   const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
   unsigned long long acc = 0;
-  for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads) acc += count_at(count, view, gid, n, i);
+  for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads) acc += count_at(count, view, gid, n, total, i, st);
   unsigned long long tot;
   block_exclusive_scan<kSortThreads>(acc, s_warp, tot);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
@@ -100,25 +115,28 @@ __global__ void __launch_bounds__(1024) k_scan_top(unsigned long long* __restric
   const unsigned long long ex = block_exclusive_scan<1024>(c, s_warp, run);
   if (b < kSortBlocks) part[b] = ex;
   if (b == 0) {
-    st->scan_total = run;
-    st->pairs = (long long)run;
+    const bool failed = st->code != XG_OK;  // a check failed in stage 1: keep its code
+    st->scan_total = failed ? 0ull : run;
+    st->pairs = failed ? 0ll : (long long)run;
     st->fwd_evaluated = st->fwd_contrib = st->bwd_evaluated = st->bwd_contrib = 0ull;
-    st->code = run > (unsigned long long)capacity ? XG_ERR_CAPACITY : XG_OK;
+    if (!failed) st->code = run > (unsigned long long)capacity ? XG_ERR_CAPACITY : XG_OK;
   }
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* __restrict__ count,
                                                             const uint32_t* __restrict__ view,
                                                             const uint32_t* __restrict__ gid, int64_t n,
-                                                            int64_t total, const unsigned long long* __restrict__ part,
+                                                            int64_t total, DevStatus* __restrict__ st,
+                                                            const unsigned long long* __restrict__ part,
                                                             uint32_t* __restrict__ offset) {
   __shared__ unsigned long long s_warp[kWarps];
+  if (st->code == XG_ERR_CHECK) return;
   const int64_t chunk = chunk_of(total);
   const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
   unsigned long long run = part[blockIdx.x];
   for (int64_t base = beg; base < end; base += kSortThreads) {
     const int64_t i = base + threadIdx.x;
-    const unsigned long long c = i < end ? count_at(count, view, gid, n, i) : 0ull;
+    const unsigned long long c = i < end ? count_at(count, view, gid, n, total, i, st) : 0ull;
     unsigned long long tot;
     const unsigned long long ex = block_exclusive_scan<kSortThreads>(c, s_warp, tot);
     if (i < end) offset[i] = (uint32_t)(run + ex);
@@ -267,9 +285,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// Bounded wait for the phase with this parity; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t spin = 0; spin < kSpinLimit; ++spin)
+// Bounded wait for the phase with this parity; false if `limit` tries ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t spin = 0; spin < limit; ++spin)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -295,7 +313,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // the rest (a chunk's ragged last tile, unaligned caller arrays) are loaded directly.
 template <int WORDS, int DW>
 __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(SortArrays<WORDS> arr, int shift,
-                                                                                uint32_t mask,
+                                                                                uint32_t mask, uint32_t spin,
                                                                 DevStatus* __restrict__ st, int64_t fixed_count,
                                                                 const uint32_t* __restrict__ hist) {
   extern __shared__ __align__(128) uint32_t s_dyn[];  // [2][WORDS][kSortTile]
@@ -342,10 +360,10 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
     uint32_t item[kSortItems][WORDS], dig[kSortItems], rank[kSortItems];
     if (BULK_TILE(base)) {
       // every tile before j was a full bulk tile, so tile j completes phase j
-      const bool ok = mbar_wait_bounded(&s_bar, (uint32_t)(j & 1));
+      const bool ok = mbar_wait_bounded(&s_bar, (uint32_t)(j & 1), spin);
       if (__syncthreads_or(!ok)) {
         if (tid == 0) st->code = XG_ERR_CHECK;
-        mbar_wait_bounded(&s_bar, (uint32_t)(j & 1));  // let the copy in flight land first
+        mbar_wait_bounded(&s_bar, (uint32_t)(j & 1), kSpinLimit);  // let the copy in flight land first
         return;
       }
 #pragma unroll
@@ -466,6 +484,16 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
 // ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
+uint32_t spin_limit() {
+  static const uint32_t limit = [] {
+    const char* e = getenv("XG_SPIN_LIMIT");
+    if (!e || !*e) return kSpinLimit;
+    const unsigned long v = strtoul(e, nullptr, 10);
+    return v < kSpinLimit ? (uint32_t)v : kSpinLimit;
+  }();
+  return limit;
+}
+
 template <int WORDS>
 constexpr size_t scatter_smem() {
   return 2 * WORDS * kSortTile * sizeof(uint32_t);
@@ -512,9 +540,11 @@ cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word
     Timed t(f, kRadixScatter, st);
     constexpr size_t smem = scatter_smem<WORDS>();
     if (digit_word == 0)
-      k_radix_scatter<WORDS, 0><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, mask, status, fixed_count, hist);
+      k_radix_scatter<WORDS, 0><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status,
+                                                                          fixed_count, hist);
     else
-      k_radix_scatter<WORDS, 1><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, mask, status, fixed_count, hist);
+      k_radix_scatter<WORDS, 1><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status,
+                                                                          fixed_count, hist);
   }
   return cudaGetLastError();
 }
@@ -527,6 +557,12 @@ template cudaError_t radix_pass<3>(xg_frame*, const SortArrays<3>&, int, int, ui
 cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   const FramePtrs& p = f->p;
   const int64_t VN = (int64_t)f->n_views * f->n;
+  // every binning starts from a clean code (a failed check of an earlier call does not stick)
+  {
+    Timed t(f, kMemset, st);
+    const cudaError_t e = cudaMemsetAsync(&p.status->code, 0, sizeof(p.status->code), st);
+    if (e != cudaSuccess) return e;
+  }
   // stage 1: (view, depth) order of the V*n entries; words: view, depth bits, Gaussian
   int cur = 0;
   for (int pass = 0; pass < f->entry_passes; ++pass) {
@@ -544,7 +580,7 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   // stage 2: offsets of each entry's pairs in that order, then the pairs
   {
     Timed t(f, kScanReduce, st);
-    k_scan_reduce<<<kSortBlocks, kSortThreads, 0, st>>>(p.count, ent_view, ent_gid, f->n, VN, p.scan_part);
+    k_scan_reduce<<<kSortBlocks, kSortThreads, 0, st>>>(p.count, ent_view, ent_gid, f->n, VN, p.status, p.scan_part);
   }
   {
     Timed t(f, kScanTop, st);
@@ -552,7 +588,8 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   }
   {
     Timed t(f, kScanDown, st);
-    k_scan_down<<<kSortBlocks, kSortThreads, 0, st>>>(p.count, ent_view, ent_gid, f->n, VN, p.scan_part, p.offset);
+    k_scan_down<<<kSortBlocks, kSortThreads, 0, st>>>(p.count, ent_view, ent_gid, f->n, VN, p.status, p.scan_part,
+                                                      p.offset);
   }
   {
     Timed t(f, kEmit, st);

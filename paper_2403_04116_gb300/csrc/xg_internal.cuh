@@ -25,6 +25,10 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 // iteration limit of every spin-wait in a kernel; on expiry the kernel records
 // XG_ERR_CHECK in the status word and returns
 constexpr uint32_t kSpinLimit = 1u << 22;
+// The limit the kernels' first waits use: kSpinLimit, or the XG_SPIN_LIMIT environment
+// variable (read once per process) to make waits expire for fault-injection tests.  Waits
+// that drain copies in flight before a kernel returns always use kSpinLimit.
+uint32_t spin_limit();
 
 // Decision constants (float roundings of the paper-level values).
 constexpr double kLn2D = 0.69314718055994530942;

@@ -264,6 +264,27 @@ class Trainer:
                            self.v["opacity_logit"].data_ptr(), self.n,
                            math.log(c.reset_opacity / (1.0 - c.reset_opacity)), _stream_handle())
 
+    # ---- checkpoint / resume ------------------------------------------------------------
+    def save(self, path: str) -> None:
+        """Parameters, Adam moments and step, the iteration count, the density statistics
+        and the random state: everything a resumed run continues from (synchronises)."""
+        torch.save({"p": self.p, "m": self.m, "v": self.v, "step_count": self.step_count,
+                    "iteration": self.iteration, "accum": self.accum, "denom": self.denom,
+                    "rng": self.gen.bit_generator.state}, path)
+
+    def load(self, path: str) -> None:
+        """Restore a checkpoint written by save(); its N may differ from the current one."""
+        ck = torch.load(path, map_location=self.device)
+        self.p = {k: ck["p"][k].contiguous() for k in NAMES}
+        self.m = {k: ck["m"][k].contiguous() for k in NAMES}
+        self.v = {k: ck["v"][k].contiguous() for k in NAMES}
+        self.step_count.copy_(ck["step_count"])
+        self.iteration = int(ck["iteration"])
+        self.gen.bit_generator.state = ck["rng"]
+        self._resize(self.p["mean"].shape[1])
+        self.accum.copy_(ck["accum"])
+        self.denom.copy_(ck["denom"])
+
     # ---- public -------------------------------------------------------------------------
     def step(self, t: int) -> None:
         """One training step on view group t mod groups: replayed from its graph, or run as

@@ -183,3 +183,31 @@ def test_short_training_run_improves_heldout_psnr():
     torch.cuda.synchronize()
     after = tr.psnr(te_v, te).mean()
     assert math.isfinite(after) and after > before + 1.0, (before, after)
+
+
+def test_checkpoint_resume_continues_the_run(tmp_path):
+    from paper_2403_04116_gb300.train import NAMES, TrainConfig, Trainer, config3, raw_from_activated
+    side, tr_v, tr_t, te_v, te_t, g = config3(3000, 128, seed_id=63)
+    # density control runs before the checkpoint (steps 40 and 80) so the count changes, and
+    # not after it, where a near-threshold decision could flip with the atomics' order
+    cfg = TrainConfig(views_per_step=8, position_scale=side, decay_steps=200, densify=True, densify_from=40,
+                      densify_interval=40, densify_until=81)
+    raw = raw_from_activated(g, cfg.n_features, np.random.default_rng(2))
+    targets = torch.from_numpy(tr_t).cuda()
+    a = Trainer(raw, tr_v, targets, cfg, FrameConfig(16, 16))
+    a.train(100, check_every=0)
+    n_ck = a.n
+    assert n_ck != 3000
+    path = str(tmp_path / "ck.pt")
+    a.save(path)
+    a.train(60, check_every=0)
+    b = Trainer(raw, tr_v, targets, cfg, FrameConfig(16, 16))
+    b.load(path)
+    assert b.iteration == 100 and b.n == n_ck
+    b.train(60, check_every=0)
+    torch.cuda.synchronize()
+    assert a.n == b.n and a.iteration == b.iteration == 160
+    assert int(a.step_count.item()) == int(b.step_count.item()) == 160
+    # the same run: equal up to the order of the float atomics in the backward pass
+    for k in NAMES:
+        np.testing.assert_allclose(b.p[k].cpu().numpy(), a.p[k].cpu().numpy(), rtol=1e-3, atol=1e-4)
