@@ -140,6 +140,25 @@ def phantom_line_integrals(ph: dict, view: View) -> np.ndarray:
     return out
 
 
+def phantom_density(ph: dict, shape, voxel_mm: float) -> np.ndarray:
+    """Density of the phantom at the voxel centres of a [nz, ny, nx] volume centred on the
+    origin (voxel (i, j, k) at ((i + 1/2 - nx/2) s, (j + 1/2 - ny/2) s, (k + 1/2 - nz/2) s))."""
+    nz, ny, nx = shape
+    axes = [(np.arange(m) + 0.5 - m / 2.0) * voxel_mm for m in (nx, ny, nz)]
+    Z, Y, X = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+    pts = np.stack([X, Y, Z], axis=-1)
+    out = np.zeros(shape)
+    for c, ax, r, rho in zip(ph["centre"], ph["axes"], ph["rot"], ph["density"]):
+        loc = np.einsum("ij,...j->...i", r.T, pts - c) / ax
+        out[(loc * loc).sum(axis=-1) <= 1.0] += rho
+    return out
+
+
+def sphere_phantom(centre, radius: float, density: float = 1.0) -> dict:
+    return {"centre": np.asarray([centre], np.float64), "axes": np.full((1, 3), float(radius)),
+            "rot": np.eye(3)[None], "density": np.asarray([density], np.float64)}
+
+
 def phantom_targets(ph: dict, views: list[View]) -> np.ndarray:
     """Projections of the phantom for every view, scaled by their common maximum to [0, 1]."""
     imgs = np.stack([phantom_line_integrals(ph, v) for v in views])
