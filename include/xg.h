@@ -389,6 +389,31 @@ xg_status xg_densify_apply(const xg_param_set* params, const xg_param_set* adam_
 xg_status xg_opacity_reset(float* opacity_logit, float* adam_m, float* adam_v, int64_t n, float reset_logit,
                            void* stream);
 
+/* FDK reconstruction (Feldkamp, Davis, Kress) of a volume from projections of a full
+ * circular scan: the paper's downstream use of rendered views (Sec. 4, Table 2).  Views
+ * are evenly spaced over 2 pi and share one scanner (only the angle changes).  Steps:
+ * P_w = P L_SO / sqrt(L_SO^2 + p^2 + zeta^2) at pixel centres scaled to the rotation axis
+ * (tau = pitch L_SO / L_SD); Q = tau (h * P_w) along each detector row with the ramp kernel
+ * h[0] = 1 / (4 tau^2), h[n odd] = -1 / (pi^2 n^2 tau^2); f(mu) = (pi / V) sum_v U^2 Q_v
+ * at mu's projection (bilinear, zero off the detector), U = L_SO / t_z.  The volume is
+ * [nz][ny][nx] floats, voxel (i, j, k) centred at ((i + 1/2 - nx/2) s, (j + 1/2 - ny/2) s,
+ * (k + 1/2 - nz/2) s) mm, s = voxel_mm. */
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t reserved; /* set to 0 */
+  double voxel_mm;
+} xg_volume;
+
+/* Device workspace bytes of xg_fdk (0 for invalid sizes); 256-byte aligned. */
+size_t xg_fdk_workspace_bytes(int32_t n_views, int32_t width, int32_t height);
+
+/* views: host array of n_views; projections: device [n_views][H][W]; volume: device,
+ * overwritten.  Enqueued on `stream` (the camera constants are uploaded from host memory,
+ * so the call is not graph-capturable).  Errors: XG_ERR_INVALID_ARG, XG_ERR_WORKSPACE,
+ * XG_ERR_CUDA. */
+xg_status xg_fdk(const xg_view* views, int32_t n_views, const float* projections, const xg_volume* vol,
+                 float* volume, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Largest pair count xg_sort_pairs_noalloc accepts. */
 #define XG_NOALLOC_MAX_PAIRS (1 << 20)
 

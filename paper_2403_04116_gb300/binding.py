@@ -18,7 +18,7 @@ XG_ERR_WORKSPACE = 4
 XG_ERR_CHECK = 5
 
 # Every symbol include/xg.h declares.
-EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_frame_select_views", "xg_densify_stats", "xg_densify_workspace_bytes",
+EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_frame_select_views", "xg_fdk_workspace_bytes", "xg_fdk", "xg_densify_stats", "xg_densify_workspace_bytes",
            "xg_densify_plan", "xg_densify_apply", "xg_opacity_reset", "xg_acui_count", "xg_acui_points", "xg_frame_copy_status", "xg_project",
            "xg_bin_sort",
            "xg_render_fwd", "xg_render_bwd", "xg_frame_read_status", "xg_frame_layout", "xg_loss_l1",
@@ -90,6 +90,11 @@ class XgParamSet(ctypes.Structure):
 class XgDensityRules(ctypes.Structure):
     _fields_ = [("grad_thresh", ctypes.c_float), ("size_log_thresh", ctypes.c_float),
                 ("prune_logit", ctypes.c_float), ("max_log_size", ctypes.c_float)]
+
+
+class XgVolume(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("voxel_mm", ctypes.c_double)]
 
 
 class XgError(RuntimeError):
@@ -165,6 +170,10 @@ def lib(build_if_missing: bool = False):
     L.xg_adam_step.argtypes = [ctypes.POINTER(XgAdamGroup), ctypes.c_int32, P, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, P]
     L.xg_adam_step.restype = ctypes.c_int
+    L.xg_fdk_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    L.xg_fdk_workspace_bytes.restype = ctypes.c_size_t
+    L.xg_fdk.argtypes = [ctypes.POINTER(XgView), ctypes.c_int32, P, ctypes.POINTER(XgVolume), P, P, ctypes.c_size_t, P]
+    L.xg_fdk.restype = ctypes.c_int
     PS = ctypes.POINTER(XgParamSet)
     L.xg_densify_stats.argtypes = [P, ctypes.c_float, P, P, P]
     L.xg_densify_stats.restype = ctypes.c_int
@@ -308,6 +317,16 @@ def xg_loss_l1_ssim(image: int, target: int, n_views: int, width: int, height: i
 def xg_adam_step(groups, step: int, beta1: float, beta2: float, eps: float, stream: int) -> None:
     arr = (XgAdamGroup * len(groups))(*groups)
     _check(lib().xg_adam_step(arr, len(groups), step, beta1, beta2, eps, stream), "xg_adam_step")
+
+
+def xg_fdk_workspace_bytes(n_views: int, width: int, height: int) -> int:
+    return int(lib().xg_fdk_workspace_bytes(n_views, width, height))
+
+
+def xg_fdk(views, projections: int, vol: XgVolume, volume: int, workspace: int, nbytes: int, stream: int) -> None:
+    arr = (XgView * len(views))(*[XgView(v.sod_mm, v.sdd_mm, v.pitch_u_mm, v.pitch_v_mm, v.angle_rad, v.width,
+                                         v.height) for v in views])
+    _check(lib().xg_fdk(arr, len(views), projections, ctypes.byref(vol), volume, workspace, nbytes, stream), "xg_fdk")
 
 
 def xg_densify_stats(frame: int, scale: float, accum: int, denom: int, stream: int) -> None:

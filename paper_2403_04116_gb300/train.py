@@ -336,15 +336,45 @@ class Trainer:
         return out.cpu().numpy()
 
 
-def config3(n: int, W: int, seed_id: int = 3):
-    """Scan of the paper's protocol (Sec. 4.1): 100 projections over 0-180 degrees, the even
-    ones for training, the odd ones held out; cuboid-uniform initial Gaussians."""
+def config3(n: int, W: int, seed_id: int = 3, span_rad: float = math.pi):
+    """Scan of the paper's protocol (Sec. 4.1): 100 projections over 0-180 degrees (or
+    another span), the even ones for training, the odd ones held out; cuboid-uniform
+    initial Gaussians."""
     side = synth.scene_side_mm(W)
-    views = synth.circular_views(100, W, W, span_rad=math.pi)
+    views = synth.circular_views(100, W, W, span_rad=span_rad)
     ph = synth.ellipsoid_phantom(10, side, synth.rng(seed_id, 1))
     targets = synth.phantom_targets(ph, views)
     g = synth.gaussians(n, side, synth.rng(seed_id, 0))
     return side, views[0::2], targets[0::2], views[1::2], targets[1::2], g
+
+
+def ct_report(trainer: "Trainer", side: float, W: int, n: int, seed_id: int = 3, span_rad: float = math.pi) -> dict:
+    """The paper's downstream use (Table 2), on the synthetic phantom: FDK volumes (n^3, the
+    scene cube) from 360 views rendered by the trained Gaussians, from 360 exact projections
+    and from 50 exact projections (sparse view), each scored by 3-D PSNR against the
+    phantom's density (in the units of the normalised projections)."""
+    from .ct import fdk, psnr3d
+    ph = synth.ellipsoid_phantom(10, side, synth.rng(seed_id, 1))
+    scan = synth.circular_views(100, W, W, span_rad=span_rad)  # the training scan's normalisation
+    norm = max(float(synth.phantom_line_integrals(ph, v).max()) for v in scan)
+    vox = side / n
+    truth = synth.phantom_density(ph, (n, n, n), vox) / norm
+    full = synth.circular_views(360, W, W)
+    rendered = trainer.render(full)
+    fdk(rendered, full, (n, n, n), vox)  # warm-up
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    vol = fdk(rendered, full, (n, n, n), vox)
+    t1.record()
+    torch.cuda.synchronize()
+    out = {"volume": [n, n, n], "voxel_mm": vox, "fdk_ms_360_views": t0.elapsed_time(t1),
+           "psnr_rendered_360": psnr3d(vol.cpu().numpy(), truth)}
+    for name, k in (("psnr_exact_360", 360), ("psnr_exact_50", 50)):
+        vs = synth.circular_views(k, W, W)
+        proj = np.stack([synth.phantom_line_integrals(ph, v) for v in vs]) / norm
+        vol = fdk(torch.from_numpy(proj.astype(np.float32)).to(rendered.device), vs, (n, n, n), vox)
+        out[name] = psnr3d(vol.cpu().numpy(), truth)
+    return out
 
 
 def main() -> None:
@@ -359,11 +389,15 @@ def main() -> None:
     ap.add_argument("--acui-interval", type=float, default=8.0, help="sampling interval d of Eq. 13")
     ap.add_argument("--noise", type=float, default=0.0, help="projection noise level (0.03 in the paper)")
     ap.add_argument("--densify", action="store_true", help="adaptive density control (clone / split / prune)")
+    ap.add_argument("--span", type=float, default=180.0, help="degrees covered by the 100 scan views (paper: 180)")
+    ap.add_argument("--fdk", type=int, default=0, help="after training, reconstruct an N^3 volume by FDK from 360 "
+                                                          "rendered views and report its 3-D PSNR")
     args = ap.parse_args()
     tw_th, b, p = args.tile.split(":")
     tw, th = (int(x) for x in tw_th.split("x"))
     fcfg = FrameConfig(tw, th, batch=int(b), pixels_per_thread=int(p))
-    side, tr_v, tr_t, te_v, te_t, g = config3(args.gaussians, args.detector)
+    span = math.radians(args.span)
+    side, tr_v, tr_t, te_v, te_t, g = config3(args.gaussians, args.detector, span_rad=span)
     cfg = TrainConfig(views_per_step=args.views_per_step, position_scale=side, decay_steps=args.steps,
                       densify=args.densify)
     B.lib(build_if_missing=True)
@@ -386,13 +420,15 @@ def main() -> None:
     wall = time.perf_counter() - t0
     loss = trainer.loss.cpu().numpy()
     psnr1 = trainer.psnr(te_v, te_t)
-    print(json.dumps({"workload": "config3", "init": args.init, "noise": args.noise, "densify": args.densify,
+    ct = ct_report(trainer, side, args.detector, args.fdk, span_rad=span) if args.fdk else None
+    print(json.dumps({"workload": "config3", "span_deg": args.span, "init": args.init, "noise": args.noise,
+                      "densify": args.densify,
                       "gaussians_start": n_start, "gaussians": trainer.n, "detector": args.detector,
                       "train_views": len(tr_v), "test_views": len(te_v), "views_per_step": args.views_per_step,
                       "steps": args.steps, "wall_s": wall, "steps_per_s": args.steps / wall,
                       "last_loss": float(loss[0]), "last_l1": float(loss[1]), "last_ssim": float(loss[2]),
                       "heldout_psnr_before": float(psnr0.mean()), "heldout_psnr_after": float(psnr1.mean()),
-                      "tile": args.tile}), flush=True)
+                      "tile": args.tile, "ct": ct}), flush=True)
 
 
 if __name__ == "__main__":

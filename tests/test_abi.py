@@ -93,3 +93,18 @@ def test_frame_create_rejects_bad_arguments_before_touching_the_device(lib):
 def test_status_strings(lib):
     assert B.xg_status_str(B.XG_OK) == "ok"
     assert "capacity" in B.xg_status_str(B.XG_ERR_CAPACITY)
+
+
+def test_fdk_argument_checks_before_any_device_work(lib):
+    from paper_2403_04116_gb300.synth import View, circular_views
+    views = circular_views(8, 32, 32)
+    vol = B.XgVolume(16, 16, 16, 0, 1.0)
+    assert B.xg_fdk_workspace_bytes(8, 32, 32) > 8 * 32 * 32 * 4
+    assert B.xg_fdk_workspace_bytes(0, 32, 32) == 0
+    bad = list(views)
+    bad[3] = View(900.0, 1500.0, 1.0, 1.0, 0.3, 32, 32)  # another scanner distance
+    for vs, v, code in ((bad, vol, B.XG_ERR_INVALID_ARG), (views, B.XgVolume(0, 16, 16, 0, 1.0), B.XG_ERR_INVALID_ARG),
+                        (views, vol, B.XG_ERR_WORKSPACE)):
+        with pytest.raises(B.XgError) as e:
+            B.xg_fdk(vs, 1 << 20, v, 1 << 20, 0, 0, 0)
+        assert e.value.code == code
