@@ -58,7 +58,9 @@ def metric_train(w: dict) -> str:
     return f"X-ray projections/s fwd and fwd+bwd ({w['n'] / 1000:g}k Gaussians, {w['W']}²) and % of roofline"
 
 # FP32 lane instructions charged per evaluated (pixel, list entry) pair of the compositing
-# kernels, and per contributing pair on top ("Roofline").
+# kernels, and per contributing pair on top: the exponent, exp, opacity and blend of a pair,
+# and for a contributor the transmittance update and accumulation (forward) or the
+# recovered transmittance, blend-behind update and six dL/dpower moments (backward).
 FWD_OPS_EVAL, FWD_OPS_CONTRIB = 20, 4
 BWD_OPS_EVAL, BWD_OPS_CONTRIB = 20, 30
 SMS, FP32_LANES = 152, 128
