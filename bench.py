@@ -247,7 +247,7 @@ def cpu_oracle_rate(name: str, target_seconds: float = 12.0) -> dict:
         rate, sample = (p / npx) / t, f"view 0 of {w['views']}, {p} of {npx} pixels sampled at random, {t:.1f} s"
     else:
         # whole views, spread over the scan; a scan of few views is repeated
-        k = max(1, min(50 * len(views), int(round(target_seconds / t1))))
+        k = max(1, min(2000 * len(views), int(round(target_seconds / max(t1, 1e-4)))))
         ids = [(i * max(1, len(views) // k)) % len(views) for i in range(k)]
         t = run(ids)
         rate, sample = len(ids) / t, f"{len(ids)} views of {w['views']} (repeated if fewer), all pixels, {t:.1f} s"
@@ -266,15 +266,15 @@ def cpu_replica_rate(name: str, target_seconds: float = 6.0) -> dict:
     t0 = time.perf_counter()
     oracle.replica_full(g, views[0], tile)
     t1 = time.perf_counter() - t0
-    k = max(1, min(len(views), int(round(target_seconds / max(t1, 1e-3)))))
-    ids = [(i * max(1, len(views) // k)) % len(views) for i in range(k)]
+    k = max(1, min(2000 * len(views), int(round(target_seconds / max(t1, 1e-4)))))
+    ids = [(i * max(1, len(views) // k)) % len(views) for i in range(k)]  # a short scan is repeated
     t0 = time.perf_counter()
     for i in ids:
         oracle.replica_full(g, views[i], tile)
     t = time.perf_counter() - t0
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": len(ids) / t, "unit": "projections/s", "cores": threads, "kind": "fp32 replica, forward",
-            "sample": f"{len(ids)} of {w['views']} views, {tile[0]}x{tile[1]} tiles, {t:.1f} s"}
+            "sample": f"{len(ids)} views of {w['views']} (repeated if fewer), {tile[0]}x{tile[1]} tiles, {t:.1f} s"}
 
 
 def run_reference(args) -> None:
