@@ -83,8 +83,22 @@ class GraphedStep:
         with torch.cuda.graph(self.graph):
             self._run()
 
+    def capture_host(self) -> None:
+        """Record the scan with the per-pass copies to ``host_image`` (pinned)."""
+        if self.host_image is None:
+            self.host_image = torch.empty(self.image.shape, dtype=torch.float32).pin_memory()
+            self._copy_stream = torch.cuda.Stream()
+        self.graph_host = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph_host):
+            self._copy_stream.wait_stream(torch.cuda.current_stream())
+            self._run(to_host=True)
+
     def replay(self) -> None:
         self.graph.replay()
+
+    def replay_host(self) -> None:
+        """One scan whose projections land in ``host_image`` when the stream reaches its end."""
+        self.graph_host.replay()
 
 
 class GraphedScan:
@@ -93,6 +107,9 @@ class GraphedScan:
 
     The device status word of each pass (pair count, capacity overflow, work counters) is
     copied into ``pass_status`` inside the graph, so one read after a replay covers them all.
+    ``capture_host`` records a second graph that also copies each pass's projections to
+    pinned host memory (``host_image``) on a side stream as soon as the pass is done, so
+    the copies overlap the following passes.
     """
 
     def __init__(self, n: int, views, cfg: FrameConfig, pair_capacity: int, views_per_pass: int, device="cuda"):
@@ -105,16 +122,28 @@ class GraphedScan:
         self.image = torch.empty(f.n_scan, f.H, f.W, device=device)
         self.pass_status = torch.zeros(len(self.starts), 7, dtype=torch.int64, device=device)
         self.graph = None
+        self.graph_host = None
+        self.host_image = None
+        self._copy_stream = None
 
-    def _run(self) -> None:
+    def _run(self, to_host: bool = False) -> None:
         f = self.frame
+        main = torch.cuda.current_stream()
         for i, first in enumerate(self.starts):
             V = f.select(first)
             f.project(*self.inputs)
             f.bin_sort()
             f.render_fwd(self.image[first:first + V])
             f.copy_status(self.pass_status[i])
+            if to_host:
+                done = torch.cuda.Event()
+                done.record(main)
+                self._copy_stream.wait_event(done)
+                with torch.cuda.stream(self._copy_stream):
+                    self.host_image[first:first + V].copy_(self.image[first:first + V], non_blocking=True)
         f.select(0)
+        if to_host:
+            main.wait_stream(self._copy_stream)
 
     def load(self, gaussians: tuple) -> None:
         for dst, src in zip(self.inputs, gaussians):
@@ -146,8 +175,22 @@ class GraphedScan:
         with torch.cuda.graph(self.graph):
             self._run()
 
+    def capture_host(self) -> None:
+        """Record the scan with the per-pass copies to ``host_image`` (pinned)."""
+        if self.host_image is None:
+            self.host_image = torch.empty(self.image.shape, dtype=torch.float32).pin_memory()
+            self._copy_stream = torch.cuda.Stream()
+        self.graph_host = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph_host):
+            self._copy_stream.wait_stream(torch.cuda.current_stream())
+            self._run(to_host=True)
+
     def replay(self) -> None:
         self.graph.replay()
+
+    def replay_host(self) -> None:
+        """One scan whose projections land in ``host_image`` when the stream reaches its end."""
+        self.graph_host.replay()
 
 
 class PlainSteps:

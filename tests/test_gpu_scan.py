@@ -113,3 +113,12 @@ def test_sampled_pixels_against_fp64_oracle(scan):
         n_amb += int(amb.sum())
         assert want.max() > 0.3  # a dense scene: pixels far from empty
     assert n_amb <= 0.6 * 4 * 384
+
+
+def test_host_copies_overlapped_in_the_graph_equal_the_device_images(scan):
+    sc = scan["scan"]
+    sc.capture_host()
+    sc.host_image.fill_(-1.0)
+    sc.replay_host()
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(sc.host_image, sc.image.cpu())
