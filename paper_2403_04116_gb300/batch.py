@@ -83,21 +83,36 @@ class GraphedStep:
         with torch.cuda.graph(self.graph):
             self._run()
 
-    def capture_host(self) -> None:
-        """Record the scan with the per-pass copies to ``host_image`` (pinned)."""
-        if self.host_image is None:
-            self.host_image = torch.empty(self.image.shape, dtype=torch.float32).pin_memory()
-            self._copy_stream = torch.cuda.Stream()
-        self.graph_host = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph_host):
-            self._copy_stream.wait_stream(torch.cuda.current_stream())
-            self._run(to_host=True)
-
     def replay(self) -> None:
         self.graph.replay()
 
+    def capture_host(self, host_gaussians: tuple, host_target: torch.Tensor) -> None:
+        """Record the step with its transfers: the Gaussians and the targets copied in from
+        these pinned host tensors (the targets on a side stream, overlapped with the forward
+        pass and joined before the loss) and the loss copied out to ``host_loss``.  Each
+        replay_host reads whatever the host tensors hold at that moment."""
+        self.host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+        self._host_in = (tuple(host_gaussians), host_target)  # keep the sources alive
+        copy = torch.cuda.Stream()
+        f = self.frame
+        self.graph_host = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph_host):
+            main = torch.cuda.current_stream()
+            for dst, src in zip(self.inputs, host_gaussians):
+                dst.copy_(src, non_blocking=True)
+            copy.wait_stream(main)
+            with torch.cuda.stream(copy):
+                self.target.copy_(host_target, non_blocking=True)
+            f.project(*self.inputs)
+            f.bin_sort()
+            f.render_fwd(self.image)
+            main.wait_stream(copy)
+            loss_l1_into(self.image, self.target, self.grad_image, self.loss)
+            f.render_bwd(self.inputs, self.grad_image, self.grads)
+            self.host_loss.copy_(self.loss, non_blocking=True)
+
     def replay_host(self) -> None:
-        """One scan whose projections land in ``host_image`` when the stream reaches its end."""
+        """One step from the host inputs; ``host_loss`` is valid once the stream reaches it."""
         self.graph_host.replay()
 
 

@@ -59,6 +59,37 @@ def test_graphed_step_matches_direct_calls_and_replays_new_inputs():
             _close(t.cpu().numpy(), grads[k])
 
 
+def test_graph_with_host_transfers_matches_the_device_step():
+    """capture_host: the inputs copied from pinned host tensors inside the graph (targets
+    overlapped with the forward pass) and the loss copied back give the device step's
+    results, and a replay after the host tensors change sees the new contents."""
+    g, views, target = _scene()
+    cfg = FrameConfig(16, 16)
+    dev = to_device(g)
+    n = dev[4].shape[0]
+    step = GraphedStep(n, views, cfg, size_pairs(n, views, cfg, dev))
+    host = tuple(t.cpu().pin_memory() for t in dev)
+    host_target = target.cpu().pin_memory()
+    step.load(dev, target)
+    step.capture()
+    step.capture_host(host, host_target)
+    for trial in range(2):
+        if trial == 1:
+            host[0].add_(0.5)
+            step.load(tuple(t.cuda() for t in host))
+        step.replay()
+        torch.cuda.synchronize()
+        image, loss = step.image.clone(), step.loss.clone()
+        grads = [t.clone() for t in step.grads]
+        step.image.zero_()
+        step.replay_host()
+        torch.cuda.current_stream().synchronize()
+        assert torch.equal(step.image, image)
+        assert float(step.host_loss[0]) == pytest.approx(float(loss), rel=1e-6)
+        for a, b in zip(step.grads, grads):
+            _close(a.cpu().numpy(), b.cpu().numpy())
+
+
 def test_plain_per_view_form_matches_batched():
     g, views, target = _scene(cid=42, V=4)
     cfg = FrameConfig(8, 8, batch=64)
