@@ -66,7 +66,7 @@ bool sizes_of(const xg_config* cfg, int64_t n_views, int32_t W, int32_t H, Sizes
 // Byte offsets of every array in the workspace, public and private, in allocation order.
 struct Offsets {
   size_t status, cameras, records, depth, rect, count, offset, scan_part;
-  size_t ent_view[2], ent_depth[2], ent_gid[2], key_tile[2], value[2], hist, range, tfinal, last, grad2d;
+  size_t ent_view[2], ent_depth[2], ent_gid[2], key_tile[2], value[2], hist, range, order, tfinal, last, grad2d;
   size_t total;
 };
 
@@ -98,6 +98,7 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t n_scan, in
   for (int b = 0; b < 2; ++b) o->value[b] = take(4 * cap);
   o->hist = take(4 * 256 * ((size_t)xg::kSortBlocks + 1));
   o->range = take(8 * (size_t)s->range_keys);
+  o->order = take(4 * (size_t)V * (size_t)s->tiles_per_view);
   o->tfinal = take(4 * pix);
   o->last = take(4 * pix);
   o->grad2d = take(4 * 8 * VN);
@@ -130,6 +131,11 @@ cudaError_t upload_cameras(const xg_frame* f, const xg_view* views, cudaStream_t
       cudaMemcpyAsync(f->cam_all, cams, sizeof(xg::Camera) * (size_t)f->n_scan, cudaMemcpyHostToDevice, st);
   free(cams);  // pageable source: the copy has been staged when cudaMemcpyAsync returns
   return e;
+}
+
+__global__ void k_iota(uint32_t* __restrict__ a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = (uint32_t)i;
 }
 
 __global__ void k_copy_status(const xg::DevStatus* __restrict__ s, xg_device_status* __restrict__ out) {
@@ -239,6 +245,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   }
   p.hist = (uint32_t*)(base + o.hist);
   p.range = (uint2*)(base + o.range);
+  p.order = (uint32_t*)(base + o.order);
   p.tfinal = (float*)(base + o.tfinal);
   p.last = (uint32_t*)(base + o.last);
   p.grad2d = (float*)(base + o.grad2d);
@@ -267,6 +274,11 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   cudaError_t e = xg::radix_prepare();  // kernel attributes, set outside any stream capture
   if (e == cudaSuccess) e = upload_cameras(f, views, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.status, 0, sizeof(xg::DevStatus), st);
+  if (e == cudaSuccess) {  // the work order before any binning: every (view, tile) once
+    const int64_t items = (int64_t)per_pass * s.tiles_per_view;
+    k_iota<<<(unsigned)std::min<int64_t>((items + 255) / 256, 4096), 256, 0, st>>>(p.order, items);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) {
     free(f);
     return XG_ERR_CUDA;

@@ -481,6 +481,44 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
   }
 }
 
+// The compositing kernels take the (view, tile) work items in this order: by descending
+// bucket of list length (four buckets per octave), so the long lists start in the first
+// waves and the short ones fill the tail.  One CTA: a histogram, its scan, a scatter.
+constexpr int kOrderBuckets = 129;
+
+__device__ __forceinline__ int length_bucket(uint32_t len) {
+  if (len == 0) return 0;
+  const int lead = 31 - __clz(len);                                    // floor(log2 len)
+  const int frac = lead >= 2 ? (int)((len >> (lead - 2)) & 3u) : (int)((len << (2 - lead)) & 3u);
+  return 1 + 4 * lead + frac;                                          // 1 .. 128
+}
+
+__global__ void __launch_bounds__(1024) k_work_order(const uint2* __restrict__ range, int n_views, int tiles_per_view,
+                                                     int tile_bits, const DevStatus* __restrict__ st,
+                                                     uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_cnt[kOrderBuckets], s_base[kOrderBuckets];
+  const int items = n_views * tiles_per_view;
+  const bool ok = st->code == XG_OK;
+  for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_cnt[b] = 0;
+  __syncthreads();
+  auto bucket_of = [&](int w) {
+    const int v = w / tiles_per_view, t = w - v * tiles_per_view;
+    const uint2 r = ok ? range[((int64_t)v << tile_bits) + t] : make_uint2(0u, 0u);
+    return length_bucket(r.y - r.x);
+  };
+  for (int w = threadIdx.x; w < items; w += blockDim.x) atomicAdd(&s_cnt[bucket_of(w)], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = kOrderBuckets - 1; b >= 0; --b) {  // longest first
+      s_base[b] = run;
+      run += s_cnt[b];
+    }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < items; w += blockDim.x) order[atomicAdd(&s_base[bucket_of(w)], 1u)] = (uint32_t)w;
+}
+
 // ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
@@ -621,6 +659,10 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     Timed t(f, kRanges, st);
     k_ranges<<<kSortBlocks * 4, 256, 0, st>>>(p.key_tile[pc], f->range_keys, p.status,
                                                p.range);
+  }
+  {
+    Timed t(f, kRanges, st);
+    k_work_order<<<1, 1024, 0, st>>>(p.range, f->n_views, (int)f->tiles_per_view, f->tile_bits, p.status, p.order);
   }
   return cudaGetLastError();
 }

@@ -238,14 +238,17 @@ __device__ __forceinline__ void fwd_entry(const float4 q0, const float4 q1, cons
 // the second of the pair is idle), and the exponent, exp, opacity, transmittance and colour
 // of both are computed with packed two-lane instructions; the decisions stay per pixel.
 template <int kBatch, int PPT>
-__global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ range, const uint32_t* __restrict__ value,
+__global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ range, const uint32_t* __restrict__ order,
+                                                    int tiles_per_view, const uint32_t* __restrict__ value,
                                                     const float4* __restrict__ rec, int64_t n, int W, int H,
                                                     int tiles_x, int64_t range_stride, int tw, int th,
                                                     const Camera* __restrict__ cams, DevStatus* __restrict__ st,
                                                     float* __restrict__ image, uint32_t* __restrict__ ncontrib,
                                                     float* __restrict__ tfinal, uint32_t* __restrict__ last) {
   constexpr int NP = PPT > 1 ? PPT / 2 : 1;  // pixel pairs per thread
-  const int tile = blockIdx.x, v = blockIdx.y;
+  const uint32_t work = order[blockIdx.x];  // (view, tile) items, longest tile lists first
+  if (work >= gridDim.x) return;            // only an order that no xg_bin_sort wrote
+  const int v = (int)(work / (uint32_t)tiles_per_view), tile = (int)(work % (uint32_t)tiles_per_view);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int lx, ly;
   pixel_in_tile<PPT>(threadIdx.x, tw, lx, ly);
@@ -324,12 +327,13 @@ __global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ ra
 
 cudaError_t launch_render_fwd(xg_frame* f, float* image, uint32_t* n_contrib, cudaStream_t st) {
   const FramePtrs& p = f->p;
-  dim3 grid((unsigned)f->tiles_per_view, (unsigned)f->n_views);
+  const dim3 grid((unsigned)(f->tiles_per_view * f->n_views));
   Timed t(f, kRenderFwd, st);
   const int ppt = f->cfg.pixels_per_thread;
   const int threads = f->cfg.tile_w * f->cfg.tile_h / ppt;
 #define XG_FWD(B, P)                                                                                       \
-  k_render_fwd<B, P><<<grid, threads, 0, st>>>(p.range, p.value[f->sorted_buf], p.rec, f->n, f->width,    \
+  k_render_fwd<B, P><<<grid, threads, 0, st>>>(p.range, p.order, (int)f->tiles_per_view,                  \
+                                               p.value[f->sorted_buf], p.rec, f->n, f->width,            \
                                                f->height, f->tiles_x, (int64_t)1 << f->tile_bits, f->cfg.tile_w,   \
                                                f->cfg.tile_h, p.cam, p.status, image, n_contrib, p.tfinal, \
                                                p.last)
@@ -356,7 +360,8 @@ cudaError_t launch_render_fwd(xg_frame* f, float* image, uint32_t* n_contrib, cu
 // its blended-behind intensity and every gradient term unchanged, so the pair's update is
 // one packed, branch-free sequence.
 template <int kBatch, int PPT>
-__global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ range, const uint32_t* __restrict__ value,
+__global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ range, const uint32_t* __restrict__ order,
+                                                    int tiles_per_view, const uint32_t* __restrict__ value,
                                                     const float4* __restrict__ rec, int64_t n, int n_views, int W,
                                                     int H, int tiles_x, int64_t range_stride, int tw, int th,
                                                     const Camera* __restrict__ cams, DevStatus* __restrict__ st,
@@ -371,7 +376,9 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
   __shared__ uint16_t s_list[kMaxWarps][kBatch];
   __shared__ uint32_t s_maxlast;
   if (st->code != XG_OK) return;
-  const int tile = blockIdx.x, v = blockIdx.y;
+  const uint32_t work = order[blockIdx.x];  // (view, tile) items, longest tile lists first
+  if (work >= gridDim.x) return;            // only an order that no xg_bin_sort wrote
+  const int v = (int)(work / (uint32_t)tiles_per_view), tile = (int)(work % (uint32_t)tiles_per_view);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int lx, ly;
   pixel_in_tile<PPT>(threadIdx.x, tw, lx, ly);
@@ -529,12 +536,13 @@ cudaError_t launch_render_bwd(xg_frame* f, const float* grad_image, cudaStream_t
     e = cudaMemsetAsync(p.grad2d, 0, sizeof(float) * 8 * (size_t)VN, st);
   }
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)f->tiles_per_view, (unsigned)f->n_views);
+  const dim3 grid((unsigned)(f->tiles_per_view * f->n_views));
   Timed t(f, kRenderBwd, st);
   const int ppt = f->cfg.pixels_per_thread;
   const int threads = f->cfg.tile_w * f->cfg.tile_h / ppt;
 #define XG_BWD(B, P)                                                                                            \
-  k_render_bwd<B, P><<<grid, threads, 0, st>>>(p.range, p.value[f->sorted_buf], p.rec, f->n, f->n_views,       \
+  k_render_bwd<B, P><<<grid, threads, 0, st>>>(p.range, p.order, (int)f->tiles_per_view,                       \
+                                               p.value[f->sorted_buf], p.rec, f->n, f->n_views,               \
                                                f->width, f->height, f->tiles_x, (int64_t)1 << f->tile_bits,             \
                                                f->cfg.tile_w, f->cfg.tile_h, p.cam, p.status, grad_image,      \
                                                p.tfinal, p.last, p.grad2d)

@@ -159,7 +159,8 @@ struct FramePtrs {
   uint32_t* key_tile[2];   // pairs (ping-pong)
   uint32_t* value[2];
   uint32_t* hist;     // [kSortBlocks + 1][256]: per-block digit counts, then digit totals
-  uint2* range;       // [V*T]
+  uint2* range;       // [V << tile_bits]
+  uint32_t* order;    // [V*T] (view, tile) work items, longest tile lists first
   float* tfinal;      // [V*H*W]
   uint32_t* last;     // [V*H*W]
   float* grad2d;      // [V*n][8]
