@@ -68,9 +68,9 @@ SMS, FP32_LANES = 152, 128
 # DRAM traffic per launch from an ncu capture (profiles/k_render_train50k.md), valid while
 # the kernel source is unchanged (sha256 prefix of the .cu file) and for the configuration
 # it was taken with.
-TRAFFIC = {"k_render_bwd": {"bytes_per_launch": 204.4e6, "source_sha": "46da28f04af8508f",
+TRAFFIC = {"k_render_bwd": {"bytes_per_launch": 329.0e6, "source_sha": "0c7af2037a1bc4a0",
                             "config": (16, 16, 128, 2), "workload": "train50k"},
-           "k_render_fwd": {"bytes_per_launch": 124.4e6, "source_sha": "46da28f04af8508f",
+           "k_render_fwd": {"bytes_per_launch": 131.0e6, "source_sha": "0c7af2037a1bc4a0",
                             "config": (16, 16, 128, 2), "workload": "train50k"}}
 
 
