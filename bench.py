@@ -431,12 +431,12 @@ def run_ours(args) -> None:
     else:
         VN = V * n
         M = int(st.pairs)
-        algo = {"k_radix_scatter": 24 * VN * 5 + 16 * M * 2, "k_project": 48 * n + 72 * VN,
-                "k_emit": 20 * VN + 8 * M, "k_project_bwd": 32 * VN + 56 * n}.get(dom, 0) / max(1, launches // timing_steps)
+        passes = frame.layout.sort_passes
+        algo = _algo_bytes(dom, n, VN, M, passes) / max(1, launches // timing_steps)
         roof = {"bound": "hbm", "achieved": algo / (avg_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     src = {"k_render_bwd": "render.cu", "k_render_fwd": "render.cu", "k_radix_scatter": "binning.cu",
-           "k_project": "project.cu", "k_emit": "binning.cu", "k_project_bwd": "project.cu"}.get(dom)
+           "k_project": "project.cu", "k_bin_scatter": "binning.cu", "k_project_bwd": "project.cu"}.get(dom)
     tr = TRAFFIC.get(dom)
     same = (tr and src and tr["source_sha"] == _source_sha(src) and tr["workload"] == args.workload
             and tr["config"] == (tile[0], tile[1], batch, ppt))
@@ -524,12 +524,14 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
-def _algo_bytes(kernel: str, n: int, VN: int, M: int, entry_passes: int, tile_passes: int) -> float:
+def _algo_bytes(kernel: str, n: int, VN: int, M: int, entry_passes: int) -> float:
     """Algorithmic DRAM bytes of one step's launches of a memory-bound kernel (each input
-    read once, each output written once)."""
-    return {"k_radix_scatter": 24 * VN * entry_passes + 16 * M * tile_passes, "k_project": 48 * n + 72 * VN,
-            "k_emit": 20 * VN + 8 * M, "k_project_bwd": 32 * VN + 56 * n, "k_ranges": 4 * M,
-            "k_radix_hist": 4 * VN * entry_passes + 4 * M * tile_passes}.get(kernel, 0)
+    read once, each output written once): the entry sort moves 3 words in and out per
+    pass; the binning kernels read each sorted entry's index, count and rectangle (16 B)
+    and the scatter writes one 4-byte index per pair."""
+    return {"k_radix_scatter": 24 * VN * entry_passes, "k_radix_hist": 4 * VN * entry_passes,
+            "k_project": 48 * n + 72 * VN, "k_project_bwd": 32 * VN + 56 * n,
+            "k_bin_count": 16 * VN, "k_bin_scatter": 16 * VN + 4 * M}.get(kernel, 0)
 
 
 def run_scan(args) -> None:
@@ -594,11 +596,16 @@ def run_scan(args) -> None:
 
     # per-kernel times: the same passes launched on the stream with event timing on
     timing_steps = 1  # the library keeps up to 2048 timed launches between reads
-    frame.read_timing()
-    frame.set_timing(True)
-    ms_stream = timed(scan._run, timing_steps)
-    frame.set_timing(False)
-    kernels = frame.read_timing()
+    for f in scan.frames:
+        f.read_timing()
+        f.set_timing(True)
+    ms_stream = timed(lambda: scan._run(serial=True), timing_steps)
+    kernels = {}
+    for f in scan.frames:
+        f.set_timing(False)
+        for k, (nl, ms) in f.read_timing().items():
+            n0, m0 = kernels.get(k, (0, 0.0))
+            kernels[k] = (n0 + nl, m0 + ms)
     stats = scan.statuses()
     M = sum(p for _, p, _, _ in stats)
     f_eval = sum(e for _, _, e, _ in stats)
@@ -609,8 +616,7 @@ def run_scan(args) -> None:
     peaks = _peaks()
     alu_peak = SMS * FP32_LANES * peaks["sm_max_mhz"] * 1e6 / 1e12
     VN = V * n
-    entry_passes = 4 + ((max(1, vpp - 1).bit_length() + 7) // 8)
-    tile_passes = frame.layout.sort_passes - entry_passes
+    entry_passes = frame.layout.sort_passes
     stages = {}
     for k, (nl, ms) in sorted(kernels.items()):
         if k == "memset":
@@ -620,7 +626,7 @@ def run_scan(args) -> None:
             ach = (FWD_OPS_EVAL * f_eval + FWD_OPS_CONTRIB * f_contrib) / (ms * 1e-3) / 1e12
             stages[k] = {"bound": "alu", "ms": ms, "achieved": ach, "unit": "TFP32op/s", "frac": ach / alu_peak}
         else:
-            b = _algo_bytes(k, n * len(scan.starts), VN, M, entry_passes, tile_passes)
+            b = _algo_bytes(k, n * len(scan.starts), VN, M, entry_passes)
             if b:
                 ach = b / (ms * 1e-3) / 1e9
                 stages[k] = {"bound": "hbm", "ms": ms, "achieved": ach, "unit": "GB/s", "frac": ach / peaks["hbm_gbs"]}

@@ -129,24 +129,22 @@ typedef struct {
  *   depth      float[V*n]     t_z (0 where it touches no tile)
  *   rect       uint16[V*n][4] tile rectangle (x0, y0, x1, y1), inclusive
  *   count      uint32[V*n]    tiles touched
- *   offset     uint32[V*n]    exclusive prefix sum of count, taken over the (view,
- *                             Gaussian) entries in (view, t_z, index) order
- *   key_tile   uint32[cap]    sorted pairs: key view * S + tile, S = range_stride (the
- *                             power of two >= T); pairs are ordered by (tile, view, t_z,
- *                             index), so every (view, tile) list is contiguous
- *   value      uint32[cap]    sorted pairs: Gaussian index
- *   range      uint32[V*S][2] [start, end) of (view, tile) at view * S + tile in the sorted
- *                             pairs ([0, 0) if empty or tile >= T)
+ *   value      uint32[cap]    the (view, tile, Gaussian) pairs as Gaussian indices, ordered
+ *                             by (tile, view, t_z, index): every (view, tile) list is
+ *                             contiguous and in depth order (the first `pairs` are valid)
+ *   range      uint32[V*S][2] [start, end) in `value` of (view, tile) at view * S + tile,
+ *                             S = range_stride, the power of two >= T ([0, 0) if the list
+ *                             is empty or tile >= T)
  *   tfinal     float[V][H][W] transmittance after the last contributor
  *   last       uint32[V][H][W] 1-based position in the tile's list of the last contributor
  *   grad2d     float[V*n][8]  per (view, Gaussian): dL/du_x, dL/du_y, dL/da, dL/db, dL/dc,
  *                             dL/dopacity, dL/dintensity, 0 (written by xg_render_bwd) */
 typedef struct {
-  size_t status, cameras, records, depth, rect, count, offset;
-  size_t key_tile, value, range, tfinal, last, grad2d;
+  size_t status, cameras, records, depth, rect, count;
+  size_t value, range, tfinal, last, grad2d;
   int64_t tiles_per_view;
   int32_t tiles_x, tiles_y;
-  int32_t sort_passes;
+  int32_t sort_passes;  /* radix passes over the V*n entries */
   int32_t range_stride; /* S: power of two >= tiles_per_view */
 } xg_layout;
 
@@ -181,12 +179,12 @@ xg_status xg_frame_select_views(xg_frame* frame, int32_t first_view, int32_t* n_
  * the frame's records, depth, rect and count arrays.  `g` must have the frame's n. */
 xg_status xg_project(xg_frame* frame, const xg_gaussians* g, void* stream);
 
-/* Tile binning and the depth-keyed radix sort (Sec. 3.2).  Orders the (view, Gaussian)
- * entries by (view, t_z) with a stable LSD radix sort, prefix-sums their tile counts in that
- * order, emits one (view * T + tile, Gaussian) pair per touched tile, sorts the pairs stably
- * by tile, and extracts each tile's range: every tile's list is in ascending t_z, ties by
- * ascending Gaussian index.  Sets XG_ERR_CAPACITY in the device status if the pairs exceed
- * pair_capacity. */
+/* Tile binning and the depth order (Sec. 3.2).  Orders the (view, Gaussian) entries by
+ * (view, t_z) with a stable LSD radix sort, counts the pairs every run of sorted entries
+ * puts on every tile, turns the counts into positions, and writes one pair per touched tile
+ * straight to its place in `value`, with each (view, tile) range: every list is in
+ * ascending t_z, ties by ascending Gaussian index.  Sets XG_ERR_CAPACITY in the device
+ * status (and leaves every list empty) if the pairs exceed pair_capacity. */
 xg_status xg_bin_sort(xg_frame* frame, void* stream);
 
 /* Front-to-back alpha compositing of intensity per detector pixel (Eq. 10).

@@ -117,18 +117,23 @@ class GraphedStep:
 
 
 class GraphedScan:
-    """Forward projections of every view of a scan, ``views_per_pass`` views at a time
-    through one frame, all passes captured in one CUDA graph.
+    """Forward projections of every view of a scan, ``views_per_pass`` views at a time,
+    all passes captured in one CUDA graph.
 
-    The device status word of each pass (pair count, capacity overflow, work counters) is
-    copied into ``pass_status`` inside the graph, so one read after a replay covers them all.
+    Two frames alternate on two streams, so a pass's binning and sort (latency- and
+    memory-bound) overlap the previous pass's compositing (issue-bound).  The device status
+    word of each pass (pair count, capacity overflow, work counters) is copied into
+    ``pass_status`` inside the graph, so one read after a replay covers them all.
     ``capture_host`` records a second graph that also copies each pass's projections to
     pinned host memory (``host_image``) on a side stream as soon as the pass is done, so
     the copies overlap the following passes.
     """
 
-    def __init__(self, n: int, views, cfg: FrameConfig, pair_capacity: int, views_per_pass: int, device="cuda"):
-        self.frame = Frame(n, views, cfg, pair_capacity, device, views_per_pass=views_per_pass)
+    def __init__(self, n: int, views, cfg: FrameConfig, pair_capacity: int, views_per_pass: int, device="cuda",
+                 overlap: bool = True):
+        self.frames = [Frame(n, views, cfg, pair_capacity, device, views_per_pass=views_per_pass)
+                       for _ in range(2 if overlap else 1)]
+        self.frame = self.frames[0]
         f = self.frame
         self.starts = list(range(0, f.n_scan, f.views_per_pass))
         self.inputs = (torch.zeros(3, n, device=device), torch.ones(3, n, device=device),
@@ -136,27 +141,40 @@ class GraphedScan:
         self.inputs[2][0] = 1.0
         self.image = torch.empty(f.n_scan, f.H, f.W, device=device)
         self.pass_status = torch.zeros(len(self.starts), 7, dtype=torch.int64, device=device)
+        self._streams = [None] + [torch.cuda.Stream() for _ in self.frames[1:]]
         self.graph = None
         self.graph_host = None
         self.host_image = None
         self._copy_stream = None
 
-    def _run(self, to_host: bool = False) -> None:
-        f = self.frame
+    def _run(self, to_host: bool = False, serial: bool = False) -> None:
+        """Enqueue every pass; ``serial`` keeps them all on the current stream (for
+        per-kernel timing without overlap)."""
         main = torch.cuda.current_stream()
+        streams = [main] * len(self.frames) if serial else [main] + self._streams[1:]
+        for s in streams[1:]:
+            if s is not main:
+                s.wait_stream(main)
         for i, first in enumerate(self.starts):
-            V = f.select(first)
-            f.project(*self.inputs)
-            f.bin_sort()
-            f.render_fwd(self.image[first:first + V])
-            f.copy_status(self.pass_status[i])
-            if to_host:
-                done = torch.cuda.Event()
-                done.record(main)
-                self._copy_stream.wait_event(done)
-                with torch.cuda.stream(self._copy_stream):
-                    self.host_image[first:first + V].copy_(self.image[first:first + V], non_blocking=True)
-        f.select(0)
+            k = i % len(self.frames)
+            f, s = self.frames[k], streams[k]
+            with torch.cuda.stream(s):
+                V = f.select(first)
+                f.project(*self.inputs)
+                f.bin_sort()
+                f.render_fwd(self.image[first:first + V])
+                f.copy_status(self.pass_status[i])
+                if to_host:
+                    done = torch.cuda.Event()
+                    done.record(s)
+                    self._copy_stream.wait_event(done)
+                    with torch.cuda.stream(self._copy_stream):
+                        self.host_image[first:first + V].copy_(self.image[first:first + V], non_blocking=True)
+        for f in self.frames:
+            f.select(0)
+        for s in streams[1:]:
+            if s is not main:
+                main.wait_stream(s)
         if to_host:
             main.wait_stream(self._copy_stream)
 

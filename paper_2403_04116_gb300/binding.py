@@ -63,8 +63,8 @@ class XgKernelTime(ctypes.Structure):
 
 class XgLayout(ctypes.Structure):
     _fields_ = [(name, ctypes.c_size_t) for name in
-                ("status", "cameras", "records", "depth", "rect", "count", "offset", "key_tile", "value",
-                 "range", "tfinal", "last", "grad2d")] + [
+                ("status", "cameras", "records", "depth", "rect", "count", "value", "range", "tfinal", "last",
+                 "grad2d")] + [
         ("tiles_per_view", ctypes.c_int64), ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
         ("sort_passes", ctypes.c_int32), ("range_stride", ctypes.c_int32)]
 

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/xg.h: argument checks, workspace layout, the
 // FP32 camera table built from the scanner parameters (Sec. 3.3, Eq. 12), and the
 // stream-ordered launches of each stage.
+#include <algorithm>
 #include <math.h>
 #include <nvtx3/nvToolsExt.h>
 #include <stdlib.h>
@@ -42,10 +43,11 @@ struct Sizes {
   int64_t tiles_per_view;
   int32_t tile_bits;   // bits of a tile index within its view: pair key = view << tile_bits | tile
   int64_t range_keys;  // n_views << tile_bits
-  int32_t entry_passes, tile_passes;
+  int32_t entry_passes;
+  int32_t bin_unit, bin_units, bin_rows, bin_groups;  // E, J, R, G of the pair scatter
 };
 
-bool sizes_of(const xg_config* cfg, int64_t n_views, int32_t W, int32_t H, Sizes* s) {
+bool sizes_of(const xg_config* cfg, int64_t n, int64_t n_views, int32_t W, int32_t H, Sizes* s) {
   s->tiles_x = (W + cfg->tile_w - 1) / cfg->tile_w;
   s->tiles_y = (H + cfg->tile_h - 1) / cfg->tile_h;
   s->tiles_per_view = (int64_t)s->tiles_x * s->tiles_y;
@@ -57,23 +59,33 @@ bool sizes_of(const xg_config* cfg, int64_t n_views, int32_t W, int32_t H, Sizes
   while (((int64_t)1 << vbits) < n_views) ++vbits;
   s->tile_bits = bits;
   s->entry_passes = 4 + (vbits + 7) / 8;
-  // the emitted pairs are already in view order, so a stable sort by the tile bits alone
-  // leaves every (tile, view) list contiguous and in depth order
-  s->tile_passes = (bits + 7) / 8;
+  // Pair scatter: groups of at most kBinGroupTiles tiles (whole rows), and units of sorted
+  // entries sized for about 16 CTAs (unit, group) per SM, fewer where the per-(unit, tile)
+  // counts would pass 2^24 words; every unit lies inside one view.
+  const int64_t T = s->tiles_per_view;
+  s->bin_rows = std::max(1, std::min(s->tiles_y, xg::kBinGroupTiles / s->tiles_x));
+  s->bin_groups = (s->tiles_y + s->bin_rows - 1) / s->bin_rows;
+  const int64_t target = ((int64_t)xg::kNumSMs * 16 + s->bin_groups - 1) / s->bin_groups;
+  const int64_t units = std::max<int64_t>(n_views, std::min<int64_t>(target, ((int64_t)1 << 24) / T));
+  int64_t E = (n_views * n + units - 1) / units;
+  E = std::max<int64_t>(256, (E + 255) / 256 * 256);
+  if (E >= ((int64_t)1 << 31)) return false;
+  s->bin_unit = (int32_t)E;
+  s->bin_units = (int32_t)((n + E - 1) / E);
   return true;
 }
 
 // Byte offsets of every array in the workspace, public and private, in allocation order.
 struct Offsets {
-  size_t status, cameras, records, depth, rect, count, offset, scan_part;
-  size_t ent_view[2], ent_depth[2], ent_gid[2], key_tile[2], value[2], hist, range, order, tfinal, last, grad2d;
+  size_t status, cameras, records, depth, rect, count;
+  size_t ent_view[2], ent_depth[2], ent_gid[2], value, hist, bin_hist, bin_total, range, order, tfinal, last, grad2d;
   size_t total;
 };
 
 // Per-pass arrays are sized for V views; the camera table holds all n_scan views.
 bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t n_scan, int32_t W, int32_t H, Sizes* s,
                   Offsets* o) {
-  if (!sizes_of(cfg, V, W, H, s)) return false;
+  if (!sizes_of(cfg, n, V, W, H, s)) return false;
   const size_t VN = (size_t)V * (size_t)n;
   const size_t cap = (size_t)cfg->pair_capacity;
   const size_t pix = (size_t)V * (size_t)W * (size_t)H;
@@ -89,14 +101,13 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t n_scan, in
   o->depth = take(4 * VN);
   o->rect = take(8 * VN);
   o->count = take(4 * VN);
-  o->offset = take(4 * VN);
-  o->scan_part = take(8 * (xg::kSortBlocks + 1));
   for (int b = 0; b < 2; ++b) o->ent_view[b] = take(4 * VN);
   for (int b = 0; b < 2; ++b) o->ent_depth[b] = take(4 * VN);
   for (int b = 0; b < 2; ++b) o->ent_gid[b] = take(4 * VN);
-  for (int b = 0; b < 2; ++b) o->key_tile[b] = take(4 * cap);
-  for (int b = 0; b < 2; ++b) o->value[b] = take(4 * cap);
+  o->value = take(4 * cap);
   o->hist = take(4 * 256 * ((size_t)xg::kSortBlocks + 1));
+  o->bin_hist = take(4 * (size_t)V * (size_t)s->bin_units * (size_t)s->tiles_per_view);
+  o->bin_total = take(4 * (size_t)V * (size_t)s->tiles_per_view);
   o->range = take(8 * (size_t)s->range_keys);
   o->order = take(4 * (size_t)V * (size_t)s->tiles_per_view);
   o->tfinal = take(4 * pix);
@@ -220,8 +231,10 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   f->tile_bits = s.tile_bits;
   f->range_keys = s.range_keys;
   f->entry_passes = s.entry_passes;
-  f->tile_passes = s.tile_passes;
-  f->sorted_buf = s.tile_passes & 1;  // each pass moves the pairs to the other buffer
+  f->bin_unit = s.bin_unit;
+  f->bin_units = s.bin_units;
+  f->bin_rows = s.bin_rows;
+  f->bin_groups = s.bin_groups;
   f->workspace = workspace;
   f->workspace_bytes = workspace_bytes;
 
@@ -234,16 +247,15 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   p.depth = (float*)(base + o.depth);
   p.rect = (ushort4*)(base + o.rect);
   p.count = (uint32_t*)(base + o.count);
-  p.offset = (uint32_t*)(base + o.offset);
-  p.scan_part = (unsigned long long*)(base + o.scan_part);
   for (int k = 0; k < 2; ++k) {
     p.ent_view[k] = (uint32_t*)(base + o.ent_view[k]);
     p.ent_depth[k] = (uint32_t*)(base + o.ent_depth[k]);
     p.ent_gid[k] = (uint32_t*)(base + o.ent_gid[k]);
-    p.key_tile[k] = (uint32_t*)(base + o.key_tile[k]);
-    p.value[k] = (uint32_t*)(base + o.value[k]);
   }
+  p.value = (uint32_t*)(base + o.value);
   p.hist = (uint32_t*)(base + o.hist);
+  p.bin_hist = (uint32_t*)(base + o.bin_hist);
+  p.bin_total = (uint32_t*)(base + o.bin_total);
   p.range = (uint2*)(base + o.range);
   p.order = (uint32_t*)(base + o.order);
   p.tfinal = (float*)(base + o.tfinal);
@@ -257,9 +269,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   L.depth = o.depth;
   L.rect = o.rect;
   L.count = o.count;
-  L.offset = o.offset;
-  L.key_tile = o.key_tile[f->sorted_buf];
-  L.value = o.value[f->sorted_buf];
+  L.value = o.value;
   L.range = o.range;
   L.tfinal = o.tfinal;
   L.last = o.last;
@@ -267,7 +277,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   L.tiles_per_view = s.tiles_per_view;
   L.tiles_x = s.tiles_x;
   L.tiles_y = s.tiles_y;
-  L.sort_passes = s.entry_passes + s.tile_passes;
+  L.sort_passes = s.entry_passes;
   L.range_stride = 1 << s.tile_bits;
 
   cudaStream_t st = (cudaStream_t)stream;
@@ -332,8 +342,8 @@ xg_status xg_frame_set_timing(xg_frame* frame, int32_t enable) {
 
 xg_status xg_frame_read_timing(xg_frame* frame, xg_kernel_time* out, int32_t capacity, int32_t* count) {
   static const char* const names[xg::kNumKernels] = {
-      "k_project", "k_scan_reduce", "k_scan_top", "k_scan_down", "k_emit", "k_radix_hist", "k_radix_colscan",
-      "k_radix_scatter", "k_ranges", "k_render_fwd", "k_render_bwd", "k_project_bwd", "memset"};
+      "k_project", "k_bin_count", "k_bin_colscan", "k_bin_base", "k_bin_scatter", "k_radix_hist", "k_radix_colscan",
+      "k_radix_scatter", "k_work_order", "k_render_fwd", "k_render_bwd", "k_project_bwd", "memset"};
   if (!frame || !count || (capacity > 0 && !out)) return XG_ERR_INVALID_ARG;
   if (frame->nrec > 0) {
     if (cudaEventSynchronize(frame->recs[frame->nrec - 1].b) != cudaSuccess) return XG_ERR_CUDA;

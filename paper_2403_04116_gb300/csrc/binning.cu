@@ -1,26 +1,26 @@
-// Tile binning and the depth-keyed radix sort (Sec. 3.2: Gaussians are assigned to the
-// tiles their projection touches and sorted by depth).
+// Tile binning and the depth order of every tile's list (Sec. 3.2: Gaussians are assigned
+// to the tiles their projection touches and sorted by depth).
 //
-// The (view, tile, depth) order of the pairs is built in two stable LSD radix sorts, so
-// that the many pairs (one per touched tile) are moved only by their tile index:
+// The (tile, view, depth) order of the pairs is built without sorting the pairs:
 //
-//   1. the V*n (view, Gaussian) entries, keyed (view, bits of t_z) -- 4 depth passes and
-//      ceil(log2(V)/8) view passes over V*n entries (k_project writes the keys);
-//   2. the tile counts, gathered in that order, are prefix-summed and every entry emits one
-//      (view << B | tile, Gaussian) pair per touched tile at its offset (B = ceil(log2 T)),
-//      so the emitted list is ordered by (view, depth, index);
-//   3. the pairs are sorted stably by the B tile bits alone (ceil(B/8) passes): the list
-//      ends up ordered by (tile, view, depth, index), every (view, tile) list contiguous and
-//      in (depth, index) order;
-//   4. ranges: [start, end) per (view, tile), indexed by the pair key view << B | tile.
+//   1. the V*n (view, Gaussian) entries are sorted by (view, bits of t_z) with a stable LSD
+//      radix sort -- 4 depth passes and ceil(log2(V)/8) view passes over V*n entries
+//      (k_project writes the keys), so view v's entries are [v*n, (v+1)*n) in depth order;
+//   2. each view's sorted entries are cut into units of E; per unit, the pairs falling on
+//      every tile are counted from the entries' tile rectangles with a 2-D difference array;
+//   3. a prefix over the units of each (view, tile) and a scan of the (view, tile) totals in
+//      (tile, view) order give every (unit, tile) its first output position, and the
+//      ranges [start, end) per (view, tile), indexed by view << B | tile (B = ceil(log2 T));
+//   4. each unit's entries are walked in order again and every pair's Gaussian index is
+//      written at its tile's next position.  Warp w of a CTA owns the tile rows congruent
+//      to w modulo 8, so each tile is advanced by one warp only, in entry order: the list
+//      of every (view, tile) comes out in (depth, index) order, contiguous, with no key
+//      array and no pass over the pairs other than the one that writes them.
 //
-// Each (view, tile) list equals a stable sort of that tile's pairs by the bits of t_z, at
-// well under half of the memory traffic of sorting all pairs by a 64-bit key.
-//
-// Every kernel here runs on a fixed grid of kSortBlocks CTAs that split the work into
-// contiguous chunks computed on the device from the item count, so the host never needs to
-// know the pair count and the whole sequence can be captured in a CUDA graph.  There is no
-// inter-CTA waiting: every scan is reduce / scan-of-partials / down-sweep in three launches.
+// The radix passes run on a fixed grid of kSortBlocks CTAs that split the work into
+// contiguous chunks computed on the device from the item count; the binning grids depend
+// only on the frame's sizes.  The host never needs to know the pair count, so the whole
+// sequence can be captured in a CUDA graph, and no CTA waits on another.
 #include <stdlib.h>
 
 #include "xg_internal.cuh"
@@ -68,150 +68,6 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T& total) {
   total = s_warp[NW - 1];
   __syncthreads();
   return before + x - v;
-}
-
-// ------------------------------------------------------------------------------------------
-// scan of the tile counts, read in the (view, depth) order of stage 1
-// ------------------------------------------------------------------------------------------
-// Tile count of sorted entry i; an entry outside [0, V) x [0, n) (which a correct stage 1
-// never produces) counts 0 and records XG_ERR_CHECK.
-__device__ __forceinline__ uint32_t count_at(const uint32_t* __restrict__ count, const uint32_t* __restrict__ view,
-                                             const uint32_t* __restrict__ gid, int64_t n, int64_t total, int64_t i,
-                                             DevStatus* __restrict__ st) {
-  const int64_t e = (int64_t)view[i] * n + gid[i];
-  if (gid[i] >= n || e >= total) {
-    st->code = XG_ERR_CHECK;
-    return 0u;
-  }
-  return count[e];
-}
-
-__global__ void __launch_bounds__(kSortThreads) k_scan_reduce(const uint32_t* __restrict__ count,
-                                                              const uint32_t* __restrict__ view,
-                                                              const uint32_t* __restrict__ gid, int64_t n,
-                                                              int64_t total, DevStatus* __restrict__ st,
-                                                              unsigned long long* __restrict__ part) {
-  __shared__ unsigned long long s_warp[kWarps];
-  if (st->code != XG_OK) {  // stage 1 failed a check: its entries are not to be read
-    if (threadIdx.x == 0) part[blockIdx.x] = 0ull;
-    return;
-  }
-  const int64_t chunk = chunk_of(total);
-  const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
-  unsigned long long acc = 0;
-  for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads) acc += count_at(count, view, gid, n, total, i, st);
-  unsigned long long tot;
-  block_exclusive_scan<kSortThreads>(acc, s_warp, tot);
-  if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(1024) k_scan_top(unsigned long long* __restrict__ part, int64_t capacity,
-                                                  DevStatus* __restrict__ st) {
-  static_assert(kSortBlocks <= 1024, "one partial per thread");
-  __shared__ unsigned long long s_warp[32];
-  const int b = threadIdx.x;
-  const unsigned long long c = b < kSortBlocks ? part[b] : 0ull;
-  unsigned long long run;
-  const unsigned long long ex = block_exclusive_scan<1024>(c, s_warp, run);
-  if (b < kSortBlocks) part[b] = ex;
-  if (b == 0) {
-    const bool failed = st->code != XG_OK;  // a check failed in stage 1: keep its code
-    st->scan_total = failed ? 0ull : run;
-    st->pairs = failed ? 0ll : (long long)run;
-    st->fwd_evaluated = st->fwd_contrib = st->bwd_evaluated = st->bwd_contrib = 0ull;
-    if (!failed) st->code = run > (unsigned long long)capacity ? XG_ERR_CAPACITY : XG_OK;
-  }
-}
-
-__global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* __restrict__ count,
-                                                            const uint32_t* __restrict__ view,
-                                                            const uint32_t* __restrict__ gid, int64_t n,
-                                                            int64_t total, DevStatus* __restrict__ st,
-                                                            const unsigned long long* __restrict__ part,
-                                                            uint32_t* __restrict__ offset) {
-  __shared__ unsigned long long s_warp[kWarps];
-  if (st->code == XG_ERR_CHECK) return;
-  const int64_t chunk = chunk_of(total);
-  const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
-  unsigned long long run = part[blockIdx.x];
-  for (int64_t base = beg; base < end; base += kSortThreads) {
-    const int64_t i = base + threadIdx.x;
-    const unsigned long long c = i < end ? count_at(count, view, gid, n, total, i, st) : 0ull;
-    unsigned long long tot;
-    const unsigned long long ex = block_exclusive_scan<kSortThreads>(c, s_warp, tot);
-    if (i < end) offset[i] = (uint32_t)(run + ex);
-    run += tot;
-  }
-}
-
-// ------------------------------------------------------------------------------------------
-// emit one (tile key, Gaussian) pair per touched tile, in (view, depth) order
-// ------------------------------------------------------------------------------------------
-// A warp takes 32 consecutive entries, whose pairs are contiguous in the output; lane l
-// writes pairs l, l+32, ... of the warp, finding its entry by a binary search over the
-// warp's prefix of counts, so every store instruction writes consecutive addresses.
-__global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ count, const uint32_t* __restrict__ offset,
-                                              const ushort4* __restrict__ rect, const uint32_t* __restrict__ view,
-                                              const uint32_t* __restrict__ gid, int64_t n, int64_t total,
-                                              int tiles_x, int tile_bits, int64_t capacity,
-                                              DevStatus* __restrict__ st, uint32_t* __restrict__ key_tile,
-                                              uint32_t* __restrict__ value) {
-  if (st->code != XG_OK) return;
-  const int64_t warp_first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31;
-  if (warp_first >= total) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t i = warp_first + lane;
-  uint32_t v = 0, g = 0, cnt = 0, o = 0, xy0 = 0, xy1 = 0;
-  if (i < total) {
-    v = view[i];
-    g = gid[i];
-    const int64_t vg = (int64_t)v * n + g;
-    cnt = count[vg];
-    o = offset[i];
-    if (cnt) {
-      const ushort4 r = rect[vg];
-      xy0 = (uint32_t)r.x | ((uint32_t)r.y << 16);
-      xy1 = (uint32_t)r.z | ((uint32_t)r.w << 16);
-    }
-  }
-  // exclusive prefix of the counts over the warp
-  uint32_t incl = cnt;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += y;
-  }
-  const uint32_t pre = incl - cnt;
-  const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-  const uint32_t base = __shfl_sync(0xffffffffu, o, 0);
-  if ((int64_t)base + tot > capacity) {  // cannot happen when the scan is right
-    if (lane == 0) st->code = XG_ERR_CHECK;
-    return;
-  }
-  for (uint32_t p0 = 0; p0 < tot; p0 += 32) {
-    const uint32_t p = p0 + lane;
-    // the last entry whose prefix is <= p (entries without pairs share the next prefix)
-    int e = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int cand = min(e + step, 31);
-      const uint32_t pc = __shfl_sync(0xffffffffu, pre, cand);
-      if (e + step <= 31 && pc <= p) e = cand;
-    }
-    const uint32_t e_pre = __shfl_sync(0xffffffffu, pre, e);
-    const uint32_t e_xy0 = __shfl_sync(0xffffffffu, xy0, e);
-    const uint32_t e_xy1 = __shfl_sync(0xffffffffu, xy1, e);
-    const uint32_t e_v = __shfl_sync(0xffffffffu, v, e);
-    const uint32_t e_g = __shfl_sync(0xffffffffu, g, e);
-    if (p < tot) {
-      const uint32_t k = p - e_pre;
-      const uint32_t x0 = e_xy0 & 0xffffu, y0 = e_xy0 >> 16, x1 = e_xy1 & 0xffffu;
-      const uint32_t wdt = x1 - x0 + 1u;
-      const uint32_t ty = y0 + k / wdt, tx = x0 + k % wdt;
-      key_tile[base + p] = (e_v << tile_bits) | (ty * (uint32_t)tiles_x + tx);
-      value[base + p] = e_g;
-    }
-  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -452,33 +308,358 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
 
 
 // ------------------------------------------------------------------------------------------
-// tile ranges in the sorted pairs
+// stages 2-4: the pairs, written straight into (tile, view, depth, index) order
 // ------------------------------------------------------------------------------------------
-// One thread per 4 consecutive sorted pairs (one 16-byte load); the keys just outside its
-// four come from the neighbouring loads through L1.  The key array is 16-byte aligned and
-// padded to a multiple of 16 bytes, so the last load stays inside it.
-__global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key_tile, int64_t n_keys,
-                                                DevStatus* __restrict__ st, uint2* __restrict__ range) {
-  const int64_t total = items_of(st, -1);
-  const int64_t quads = (total + 3) / 4;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < quads; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i0 = 4 * q;
-    const uint4 k4 = __ldg(reinterpret_cast<const uint4*>(key_tile) + q);
-    const uint32_t k[6] = {i0 > 0 ? __ldg(key_tile + i0 - 1) : 0xffffffffu, k4.x, k4.y, k4.z, k4.w,
-                           i0 + 4 < total ? __ldg(key_tile + i0 + 4) : 0xffffffffu};
+struct BinGeom {
+  int64_t n;      // Gaussians: view v's sorted entries are [v*n, (v+1)*n)
+  int64_t tiles;  // T, tiles per view
+  int32_t n_views;
+  int32_t tiles_x, tiles_y, tile_bits;
+  int32_t unit, units, rows, groups;  // E entries per unit, J units per view, R rows per group, G groups
+};
+
+// The CTA's unit u = v*J + j of sorted entries [beg, end) and its group of tile rows
+// [r0, r0 + rows): blockIdx.x = u*G + group.
+struct BinWork {
+  int64_t u, beg, end;
+  int v, r0, rows;
+};
+
+__device__ __forceinline__ BinWork bin_work(const BinGeom& g) {
+  BinWork w;
+  const int grp = (int)(blockIdx.x % (unsigned)g.groups);
+  w.u = blockIdx.x / (unsigned)g.groups;
+  w.v = (int)(w.u / g.units);
+  const int64_t j = w.u - (int64_t)w.v * g.units;
+  w.beg = (int64_t)w.v * g.n + j * g.unit;
+  w.end = min((int64_t)(w.v + 1) * g.n, w.beg + g.unit);
+  w.r0 = grp * g.rows;
+  w.rows = min(g.rows, g.tiles_y - w.r0);
+  return w;
+}
+
+// Sorted entry i's Gaussian and its tile rectangle clipped to the CTA's rows; false if it
+// touches none of them.  A Gaussian index >= n or a rectangle outside the tile grid (which
+// a correct projection and stage 1 never produce) records XG_ERR_CHECK and is skipped.
+__device__ __forceinline__ bool entry_rect(const BinGeom& g, const BinWork& w, int64_t i,
+                                           const uint32_t* __restrict__ ent_gid, const uint32_t* __restrict__ count,
+                                           const ushort4* __restrict__ rect, DevStatus* __restrict__ st,
+                                           uint32_t& gid, int& x0, int& x1, int& ya, int& yb) {
+  gid = ent_gid[i];
+  if (gid >= g.n) {
+    st->code = XG_ERR_CHECK;
+    return false;
+  }
+  const int64_t vg = (int64_t)w.v * g.n + gid;
+  if (count[vg] == 0) return false;
+  const ushort4 r = rect[vg];
+  if (r.x > r.z || r.y > r.w || r.z >= g.tiles_x || r.w >= g.tiles_y) {
+    st->code = XG_ERR_CHECK;
+    return false;
+  }
+  x0 = r.x;
+  x1 = r.z;
+  ya = max((int)r.y, w.r0);
+  yb = min((int)r.w, w.r0 + w.rows - 1);
+  return ya <= yb;
+}
+
+// (R + 1) x (tiles_x + 1) words, R * tiles_x <= max(kBinGroupTiles, tiles_x), R and tiles_x <= 512
+constexpr int kBinDiffWords = kBinGroupTiles + 2 * 512 + 1;
+
+// Stage 2: pairs per tile of one unit (and group of rows).  Every entry adds its rectangle
+// to a 2-D difference array in four shared atomics; prefix sums along the rows and then
+// down the columns turn it into the count of every tile.
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(BinGeom g, const uint32_t* __restrict__ ent_gid,
+                                                           const uint32_t* __restrict__ count,
+                                                           const ushort4* __restrict__ rect,
+                                                           DevStatus* __restrict__ st,
+                                                           uint32_t* __restrict__ bin_hist) {
+  __shared__ int32_t s_d[kBinDiffWords];
+  if (st->code != XG_OK) return;  // stage 1 failed a check: its entries are not to be read
+  const BinWork w = bin_work(g);
+  const int cols = g.tiles_x + 1;
+  const int cells = (w.rows + 1) * cols;
+  for (int k = threadIdx.x; k < cells; k += kBinThreads) s_d[k] = 0;
+  __syncthreads();
+  for (int64_t i = w.beg + threadIdx.x; i < w.end; i += kBinThreads) {
+    uint32_t gid;
+    int x0, x1, ya, yb;
+    if (!entry_rect(g, w, i, ent_gid, count, rect, st, gid, x0, x1, ya, yb)) continue;
+    const int a = (ya - w.r0) * cols, b = (yb - w.r0 + 1) * cols;
+    atomicAdd(&s_d[a + x0], 1);
+    atomicAdd(&s_d[a + x1 + 1], -1);
+    atomicAdd(&s_d[b + x0], -1);
+    atomicAdd(&s_d[b + x1 + 1], 1);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int y = warp; y < w.rows; y += kBinThreads / 32) {  // along each row: a warp per row
+    int carry = 0;
+    for (int xb = 0; xb < g.tiles_x; xb += 32) {
+      const int x = xb + lane;
+      int v = x < g.tiles_x ? s_d[y * cols + x] : 0;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int64_t i = i0 + e;
-      if (i >= total) break;
-      const uint32_t t = k[e + 1];
-      if ((int64_t)t >= n_keys) {  // cannot happen when emit and sort are right
-        st->code = XG_ERR_CHECK;
-        continue;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
       }
-      if (i == 0 || k[e] != t) range[t].x = (uint32_t)i;
-      if (i == total - 1 || k[e + 2] != t) range[t].y = (uint32_t)(i + 1);
+      v += carry;
+      if (x < g.tiles_x) s_d[y * cols + x] = v;
+      carry = __shfl_sync(0xffffffffu, v, 31);
     }
   }
+  __syncthreads();
+  for (int x = threadIdx.x; x < g.tiles_x; x += kBinThreads) {  // down each column
+    int run = 0;
+    for (int y = 0; y < w.rows; ++y) {
+      run += s_d[y * cols + x];
+      s_d[y * cols + x] = run;
+    }
+  }
+  __syncthreads();
+  uint32_t* out = bin_hist + w.u * g.tiles + (int64_t)w.r0 * g.tiles_x;
+  const int nt = w.rows * g.tiles_x;
+  for (int k = threadIdx.x; k < nt; k += kBinThreads) {
+    const int y = k / g.tiles_x;
+    out[k] = (uint32_t)s_d[y * cols + (k - y * g.tiles_x)];
+  }
+}
+
+// Stage 3a: per (view, tile), the exclusive prefix over the view's units of bin_hist, in
+// place, and the total in bin_total[tile * V + view].  A CTA takes 32 tiles of one view
+// (blockIdx.x = view * ceil(T / 32) + tile block); its 8 warps split the units in slices.
+__global__ void __launch_bounds__(256) k_bin_colscan(BinGeom g, const DevStatus* __restrict__ st,
+                                                     uint32_t* __restrict__ bin_hist, uint32_t* __restrict__ bin_total) {
+  __shared__ uint32_t s_part[8][32];
+  if (st->code != XG_OK) return;
+  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+  const int64_t blocks = (g.tiles + 31) / 32;
+  const int v = (int)(blockIdx.x / blocks);
+  const int64_t t = (blockIdx.x - (int64_t)v * blocks) * 32 + lane;
+  const int per = (g.units + 7) / 8;
+  const int j0 = min(g.units, slice * per), j1 = min(g.units, j0 + per);
+  uint32_t* col = bin_hist + (int64_t)v * g.units * g.tiles + t;
+  uint32_t sum = 0;
+  if (t < g.tiles)
+    for (int j = j0; j < j1; ++j) sum += col[(int64_t)j * g.tiles];
+  s_part[slice][lane] = sum;
+  __syncthreads();
+  if (slice == 0) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t c = s_part[k][lane];
+      s_part[k][lane] = run;
+      run += c;
+    }
+    if (t < g.tiles) bin_total[t * g.n_views + v] = run;
+  }
+  __syncthreads();
+  if (t < g.tiles) {
+    uint32_t run = s_part[slice][lane];
+    for (int j = j0; j < j1; ++j) {
+      const uint32_t c = col[(int64_t)j * g.tiles];
+      col[(int64_t)j * g.tiles] = run;
+      run += c;
+    }
+  }
+}
+
+// Stage 3b: the exclusive prefix of bin_total in (tile, view) order gives every (view,
+// tile) list its place; written as range[view << B | tile] = [start, end), with [0, 0) for
+// empty lists and the keys past the last tile.  The pair count and the capacity check go to the status word
+// (on a failed stage 1 or capacity overflow every range is empty).  One CTA.
+__global__ void __launch_bounds__(1024) k_bin_base(BinGeom g, int64_t capacity, const uint32_t* __restrict__ bin_total,
+                                                   DevStatus* __restrict__ st, uint2* __restrict__ range) {
+  __shared__ unsigned long long s_warp[32];
+  const bool failed = st->code != XG_OK;
+  const int64_t nb = g.tiles * g.n_views;
+  const int64_t per = (nb + 1023) / 1024;
+  const int64_t q0 = min(nb, (int64_t)threadIdx.x * per), q1 = min(nb, q0 + per);
+  unsigned long long sum = 0;
+  if (!failed)
+    for (int64_t q = q0; q < q1; ++q) sum += bin_total[q];
+  unsigned long long total;
+  unsigned long long run = block_exclusive_scan<1024>(sum, s_warp, total);
+  const bool ok = !failed && total <= (unsigned long long)capacity;
+  for (int64_t q = q0; q < q1; ++q) {
+    const uint32_t c = ok ? bin_total[q] : 0u;
+    const int64_t t = q / g.n_views;
+    const int64_t v = q - t * g.n_views;
+    range[(v << g.tile_bits) + t] = c ? make_uint2((uint32_t)run, (uint32_t)(run + c)) : make_uint2(0u, 0u);
+    run += c;
+  }
+  const int64_t pad = ((int64_t)1 << g.tile_bits) - g.tiles;
+  for (int64_t k = threadIdx.x; k < pad * g.n_views; k += 1024) {
+    const int64_t v = k / pad;
+    range[(v << g.tile_bits) + g.tiles + (k - v * pad)] = make_uint2(0u, 0u);
+  }
+  if (threadIdx.x == 0) {
+    st->scan_total = failed ? 0ull : total;
+    st->pairs = failed ? 0ll : (long long)total;
+    st->fwd_evaluated = st->fwd_contrib = st->bwd_evaluated = st->bwd_contrib = 0ull;
+    if (!failed) st->code = ok ? XG_OK : XG_ERR_CAPACITY;
+  }
+}
+
+// One staged entry: (x0 | x1 << 16, ya | yb << 16), or ya > yb when it has no tile here.
+__device__ __forceinline__ uint2 stage_entry(const BinGeom& g, const BinWork& w, int64_t i,
+                                             const uint32_t* __restrict__ ent_gid, const uint32_t* __restrict__ count,
+                                             const ushort4* __restrict__ rect, DevStatus* __restrict__ st,
+                                             uint32_t& gid) {
+  int x0, x1, ya, yb;
+  if (i < w.end && entry_rect(g, w, i, ent_gid, count, rect, st, gid, x0, x1, ya, yb))
+    return make_uint2((uint32_t)x0 | (uint32_t)x1 << 16, (uint32_t)ya | (uint32_t)yb << 16);
+  gid = 0u;
+  return make_uint2(0u, 1u);
+}
+
+// Stage 4: the unit's pairs at their places.  The CTA's tiles keep their next output
+// position in shared memory (range start + the unit's prefix).  Blocks of 256 entries are
+// staged in shared memory (the next block's loads are in flight while one is processed);
+// warp w walks every entry of the block in order, but only over the tile rows r0 + w,
+// r0 + w + 8, ... of its rectangle, 32 pairs at a time.  Two pairs of one round on the same
+// tile come from different entries; match_any ranks them in lane (= entry) order.
+//
+// Stores are combined per 32-byte sector of the output: a tile's values wait in an 8-slot
+// shared buffer (slot = position mod 8) until the sector is complete, and then leave as two
+// 16-byte stores; a sector filled within one round is stored by its 8 lanes directly.  Only
+// the sectors a unit shares with its neighbours at the ends of a tile's run are written
+// value by value (the slots before the run hold kNoValue).
+constexpr uint32_t kNoValue = 0xffffffffu;
+
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const uint32_t* __restrict__ ent_gid,
+                                                             const uint32_t* __restrict__ count,
+                                                             const ushort4* __restrict__ rect,
+                                                             const uint32_t* __restrict__ bin_hist,
+                                                             const uint2* __restrict__ range,
+                                                             DevStatus* __restrict__ st, uint32_t* __restrict__ value) {
+  constexpr int kW = kBinThreads / 32;  // warps; warp w owns the rows congruent to w mod kW
+  constexpr int TG = kBinGroupTiles;
+  __shared__ uint32_t s_pos[TG];
+  __shared__ __align__(16) uint32_t s_buf[8][TG];  // [slot][tile]
+  __shared__ uint2 s_ent[2][kBinThreads];
+  __shared__ uint32_t s_gid[2][kBinThreads];
+  if (st->code != XG_OK) return;
+  const int64_t pairs = st->pairs;
+  const BinWork w = bin_work(g);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const int64_t t0 = (int64_t)w.r0 * g.tiles_x;
+  const int nt = w.rows * g.tiles_x;
+  {
+    const uint2* rng = range + ((int64_t)w.v << g.tile_bits) + t0;
+    const uint32_t* hst = bin_hist + w.u * g.tiles + t0;
+    for (int k = threadIdx.x; k < nt; k += kBinThreads) {
+      const uint32_t p = rng[k].x + hst[k];
+      s_pos[k] = p;
+      for (uint32_t q = 0; q < (p & 7u); ++q) s_buf[q][k] = kNoValue;
+    }
+  }
+  bool bad = false;  // a position past the pair count (cannot happen when the counts are right)
+  uint32_t gid_next;
+  uint2 ent_next = stage_entry(g, w, w.beg + threadIdx.x, ent_gid, count, rect, st, gid_next);
+  s_ent[0][threadIdx.x] = ent_next;
+  s_gid[0][threadIdx.x] = gid_next;
+  __syncthreads();
+  int buf = 0;
+  for (int64_t blk = w.beg; blk < w.end; blk += kBinThreads, buf ^= 1) {
+    const bool more = blk + kBinThreads < w.end;
+    if (more) ent_next = stage_entry(g, w, blk + kBinThreads + threadIdx.x, ent_gid, count, rect, st, gid_next);
+    for (int sub = 0; sub < kBinThreads / 32; ++sub) {
+      const uint2 e = s_ent[buf][sub * 32 + lane];
+      const int x0 = (int)(e.x & 0xffffu), x1 = (int)(e.x >> 16), ya = (int)(e.y & 0xffffu), yb = (int)(e.y >> 16);
+      const int yf = ya + ((warp - (ya - w.r0)) & (kW - 1));  // this warp's first row at or after ya
+      const uint32_t wdt = (uint32_t)(x1 - x0 + 1);
+      const uint32_t cnt = yf <= yb ? ((uint32_t)(yb - yf) / kW + 1u) * wdt : 0u;
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const uint32_t pre = incl - cnt;
+      const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      if (tot == 0u) continue;
+      // local first row, first column and width - 1 (each < 512) in one word
+      const uint32_t packed = (uint32_t)(yf - w.r0) | (uint32_t)x0 << 10 | (wdt - 1u) << 20;
+      const float rcp = __frcp_rn((float)wdt);
+      for (uint32_t p0 = 0; p0 < tot; p0 += 32) {
+        const uint32_t p = p0 + lane;
+        // the last entry whose prefix is <= p (entries without pairs share the next prefix)
+        int ei = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cand = min(ei + step, 31);
+          const uint32_t pc = __shfl_sync(0xffffffffu, pre, cand);
+          if (ei + step <= 31 && pc <= p) ei = cand;
+        }
+        const uint32_t e_pre = __shfl_sync(0xffffffffu, pre, ei);
+        const uint32_t e_pk = __shfl_sync(0xffffffffu, packed, ei);
+        const float e_rcp = __shfl_sync(0xffffffffu, rcp, ei);
+        const uint32_t e_gid = s_gid[buf][sub * 32 + ei];
+        const uint32_t k = p - e_pre, ew = (e_pk >> 20) + 1u;
+        // k / ew: the quotient is below 64 and (k + 1/2) / ew is at least 1/(2 ew) >= 2^-10
+        // away from an integer, far above the 2^-23 relative error of the two roundings
+        const uint32_t row = __float2uint_rz(__fmul_rn(__uint2float_rn(k) + 0.5f, e_rcp));
+        const uint32_t col = k - row * ew;
+        const uint32_t tl = ((e_pk & 1023u) + row * kW) * (uint32_t)g.tiles_x + ((e_pk >> 10) & 1023u) + col;
+        bool valid = p < tot;
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? tl : 0xffffffffu);
+        const uint32_t old = valid ? s_pos[tl] : 0u;
+        const uint32_t pos = old + (uint32_t)__popc(peers & lt_mask);
+        const uint32_t end = old + (uint32_t)__popc(peers);
+        if (valid && (int64_t)pos >= pairs) {
+          bad = true;
+          valid = false;
+        }
+        const bool done = valid && (pos | 7u) < end;     // its sector is complete after this round
+        const bool merge = done && (pos & ~7u) < old;    // ... and holds values of earlier rounds
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) s_pos[tl] = end;
+        if (merge) s_buf[pos & 7u][tl] = e_gid;
+        __syncwarp();
+        if (merge && (pos & 7u) == 7u) {
+          uint32_t v[8];
+          bool whole = true;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            v[q] = s_buf[q][tl];
+            whole &= v[q] != kNoValue;
+          }
+          uint32_t* dst = value + (pos & ~7u);
+          if (whole) {
+            reinterpret_cast<uint4*>(dst)[0] = make_uint4(v[0], v[1], v[2], v[3]);
+            reinterpret_cast<uint4*>(dst)[1] = make_uint4(v[4], v[5], v[6], v[7]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              if (v[q] != kNoValue) dst[q] = v[q];
+          }
+        } else if (done && !merge) {
+          value[pos] = e_gid;  // the sector's 8 lanes store together
+        }
+        __syncwarp();
+        if (valid && !done) s_buf[pos & 7u][tl] = e_gid;
+      }
+    }
+    if (more) {
+      s_ent[buf ^ 1][threadIdx.x] = ent_next;
+      s_gid[buf ^ 1][threadIdx.x] = gid_next;
+    }
+    __syncthreads();
+  }
+  // the last, incomplete sector of every tile's run
+  for (int k = threadIdx.x; k < nt; k += kBinThreads) {
+    const uint32_t p = s_pos[k];
+    uint32_t* dst = value + (p & ~7u);
+    for (uint32_t q = 0; q < (p & 7u); ++q) {
+      const uint32_t v = s_buf[q][k];
+      if (v != kNoValue) dst[q] = v;
+    }
+  }
+  if (bad) st->code = XG_ERR_CHECK;
 }
 
 // The compositing kernels take the (view, tile) work items in this order: by descending
@@ -613,55 +794,31 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }
-  const uint32_t* ent_view = p.ent_view[cur];
   const uint32_t* ent_gid = p.ent_gid[cur];
-  // stage 2: offsets of each entry's pairs in that order, then the pairs
+  // stages 2-4: counts per unit and tile, their prefixes and the ranges, the pairs
+  const BinGeom g = {f->n, f->tiles_per_view, f->n_views, f->tiles_x, f->tiles_y, f->tile_bits,
+                     f->bin_unit, f->bin_units, f->bin_rows, f->bin_groups};
+  const unsigned ctas = (unsigned)((int64_t)f->n_views * f->bin_units * f->bin_groups);
   {
-    Timed t(f, kScanReduce, st);
-    k_scan_reduce<<<kSortBlocks, kSortThreads, 0, st>>>(p.count, ent_view, ent_gid, f->n, VN, p.status, p.scan_part);
+    Timed t(f, kBinCount, st);
+    k_bin_count<<<ctas, kBinThreads, 0, st>>>(g, ent_gid, p.count, p.rect, p.status, p.bin_hist);
   }
   {
-    Timed t(f, kScanTop, st);
-    k_scan_top<<<1, 1024, 0, st>>>(p.scan_part, f->cfg.pair_capacity, p.status);
+    Timed t(f, kBinColscan, st);
+    k_bin_colscan<<<(unsigned)((int64_t)f->n_views * ((f->tiles_per_view + 31) / 32)), 256, 0, st>>>(
+        g, p.status, p.bin_hist, p.bin_total);
   }
   {
-    Timed t(f, kScanDown, st);
-    k_scan_down<<<kSortBlocks, kSortThreads, 0, st>>>(p.count, ent_view, ent_gid, f->n, VN, p.status, p.scan_part,
-                                                      p.offset);
+    Timed t(f, kBinBase, st);
+    k_bin_base<<<1, 1024, 0, st>>>(g, f->cfg.pair_capacity, p.bin_total, p.status, p.range);
   }
   {
-    Timed t(f, kEmit, st);
-    k_emit<<<(unsigned)((VN + 255) / 256), 256, 0, st>>>(p.count, p.offset, p.rect, ent_view, ent_gid, f->n, VN,
-                                                         f->tiles_x, f->tile_bits, f->cfg.pair_capacity,
-                                                         p.status, p.key_tile[0], p.value[0]);
-  }
-  // stage 3: stable sort of the pairs by tile key
-  int pc = 0;
-  for (int pass = 0; pass < f->tile_passes; ++pass) {
-    SortArrays<2> arr;
-    arr.in[0] = p.key_tile[pc], arr.in[1] = p.value[pc];
-    arr.out[0] = p.key_tile[pc ^ 1], arr.out[1] = p.value[pc ^ 1];
-    // the last pass takes only the tile bits left: the view bits above them must not move pairs
-    const int left = f->tile_bits - 8 * pass;
-    const uint32_t mask = left >= 8 ? 255u : (1u << left) - 1u;
-    const cudaError_t e = radix_pass<2>(f, arr, 0, 8 * pass, mask, -1, p.status, p.hist, st);
-    if (e != cudaSuccess) return e;
-    pc ^= 1;
-  }
-  // stage 4: ranges
-  cudaError_t e;
-  {
-    Timed t(f, kMemset, st);
-    e = cudaMemsetAsync(p.range, 0, sizeof(uint2) * (size_t)f->range_keys, st);
-  }
-  if (e != cudaSuccess) return e;
-  {
-    Timed t(f, kRanges, st);
-    k_ranges<<<kSortBlocks * 4, 256, 0, st>>>(p.key_tile[pc], f->range_keys, p.status,
-                                               p.range);
+    Timed t(f, kBinScatter, st);
+    k_bin_scatter<<<ctas, kBinThreads, 0, st>>>(g, ent_gid, p.count, p.rect, p.bin_hist, p.range, p.status,
+                                                p.value);
   }
   {
-    Timed t(f, kRanges, st);
+    Timed t(f, kWorkOrder, st);
     k_work_order<<<1, 1024, 0, st>>>(p.range, f->n_views, (int)f->tiles_per_view, f->tile_bits, p.status, p.order);
   }
   return cudaGetLastError();

@@ -333,7 +333,7 @@ cudaError_t launch_render_fwd(xg_frame* f, float* image, uint32_t* n_contrib, cu
   const int threads = f->cfg.tile_w * f->cfg.tile_h / ppt;
 #define XG_FWD(B, P)                                                                                       \
   k_render_fwd<B, P><<<grid, threads, 0, st>>>(p.range, p.order, (int)f->tiles_per_view,                  \
-                                               p.value[f->sorted_buf], p.rec, f->n, f->width,            \
+                                               p.value, p.rec, f->n, f->width,            \
                                                f->height, f->tiles_x, (int64_t)1 << f->tile_bits, f->cfg.tile_w,   \
                                                f->cfg.tile_h, p.cam, p.status, image, n_contrib, p.tfinal, \
                                                p.last)
@@ -542,7 +542,7 @@ cudaError_t launch_render_bwd(xg_frame* f, const float* grad_image, cudaStream_t
   const int threads = f->cfg.tile_w * f->cfg.tile_h / ppt;
 #define XG_BWD(B, P)                                                                                            \
   k_render_bwd<B, P><<<grid, threads, 0, st>>>(p.range, p.order, (int)f->tiles_per_view,                       \
-                                               p.value[f->sorted_buf], p.rec, f->n, f->n_views,               \
+                                               p.value, p.rec, f->n, f->n_views,               \
                                                f->width, f->height, f->tiles_x, (int64_t)1 << f->tile_bits,             \
                                                f->cfg.tile_w, f->cfg.tile_h, p.cam, p.status, grad_image,      \
                                                p.tfinal, p.last, p.grad2d)

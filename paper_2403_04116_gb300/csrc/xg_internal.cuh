@@ -22,6 +22,10 @@ constexpr int kSortBlocks = kSortCtasPerSM * kNumSMs;  // grid of the scan and r
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;         // keys per thread per radix tile
 constexpr int kSortTile = kSortThreads * kSortItems;
+// pair scatter: a CTA takes one unit of sorted entries and one group of tile rows whose
+// tiles (at most kBinGroupTiles) keep their next output position in shared memory
+constexpr int kBinThreads = 256;
+constexpr int kBinGroupTiles = 1024;
 // iteration limit of every spin-wait in a kernel; on expiry the kernel records
 // XG_ERR_CHECK in the status word and returns
 constexpr uint32_t kSpinLimit = 1u << 22;
@@ -151,14 +155,13 @@ struct FramePtrs {
   float* depth;       // [V*n]
   ushort4* rect;      // [V*n]
   uint32_t* count;    // [V*n]
-  uint32_t* offset;   // [V*n], in (view, depth) order of the entries
-  unsigned long long* scan_part;  // [kSortBlocks + 1]
   uint32_t* ent_view[2];   // stage-1 sort of the V*n entries (ping-pong)
   uint32_t* ent_depth[2];
   uint32_t* ent_gid[2];
-  uint32_t* key_tile[2];   // pairs (ping-pong)
-  uint32_t* value[2];
+  uint32_t* value;    // [capacity]: Gaussian index of every pair, in (tile, view, depth) order
   uint32_t* hist;     // [kSortBlocks + 1][256]: per-block digit counts, then digit totals
+  uint32_t* bin_hist;   // [V][J][T]: pairs of each unit of entries per tile, then their prefix
+  uint32_t* bin_total;  // [T][V]: pairs per (tile, view)
   uint2* range;       // [V << tile_bits]
   uint32_t* order;    // [V*T] (view, tile) work items, longest tile lists first
   float* tfinal;      // [V*H*W]
@@ -183,7 +186,7 @@ struct SortArrays {
 
 namespace xg {
 enum KernelId {
-  kProject, kScanReduce, kScanTop, kScanDown, kEmit, kRadixHist, kRadixScan, kRadixScatter, kRanges,
+  kProject, kBinCount, kBinColscan, kBinBase, kBinScatter, kRadixHist, kRadixScan, kRadixScatter, kWorkOrder,
   kRenderFwd, kRenderBwd, kProjectBwd, kMemset, kNumKernels
 };
 struct TimingRec {
@@ -206,8 +209,10 @@ struct xg_frame {
   int32_t tile_bits;     // bits of a tile index within its view: pair key = view << tile_bits | tile
   int64_t range_keys;    // n_views << tile_bits: entries of the range array
   int32_t entry_passes;  // stage-1 passes: 4 depth bytes + view bytes
-  int32_t tile_passes;   // stage-3 passes over the pairs (the tile bits only)
-  int32_t sorted_buf;    // which ping-pong buffer holds the sorted pairs
+  int32_t bin_unit;      // E: sorted entries per unit of the pair scatter
+  int32_t bin_units;     // J: units per view, ceil(n / E)
+  int32_t bin_rows;      // R: tile rows per group (R * tiles_x <= kBinGroupTiles)
+  int32_t bin_groups;    // G: ceil(tiles_y / R)
   void* workspace;
   size_t workspace_bytes;
   xg_layout layout;

@@ -143,8 +143,7 @@ class Frame:
         P = self.V * self.H * self.W
         spec = {
             "records": (torch.float32, (VN, 8)), "depth": (torch.float32, (VN,)), "rect": (torch.int16, (VN, 4)),
-            "count": (torch.int32, (VN,)), "offset": (torch.int32, (VN,)), "key_tile": (torch.int32, (cap,)),
-            "value": (torch.int32, (cap,)),
+            "count": (torch.int32, (VN,)), "value": (torch.int32, (cap,)),
             "range": (torch.int32, (self.V * self.range_stride, 2)), "tfinal": (torch.float32, (P,)),
             "last": (torch.int32, (P,)), "grad2d": (torch.float32, (VN, 8)),
         }

@@ -39,16 +39,31 @@ def run_forward(g: dict, views, tile=(16, 16), capacity=None, near_mm=0.2, batch
     torch.cuda.synchronize()
     M = int(st.pairs) if st.code == B.XG_OK else 0
     out = {**proj, "status": st, "M": M, "frame": f, "dev": dev,
-           "key_tile": f.array("key_tile")[:M].cpu().numpy().view(np.uint32),
            "value": f.array("value")[:M].cpu().numpy(),
            "range": f.array("range").cpu().numpy().view(np.uint32),
            "image": image.cpu().numpy(), "ncontrib": ncon.cpu().numpy(),
            "tfinal": f.array("tfinal").cpu().numpy().reshape(f.V, f.H, f.W),
            "last": f.array("last").cpu().numpy().reshape(f.V, f.H, f.W)}
-    # depth key of every sorted pair, looked up from its (view, Gaussian)
+    # key view * S + tile of every pair, from the ranges (which must tile [0, M) exactly),
+    # and its depth key, looked up from its (view, Gaussian)
+    out["key_tile"] = keys_from_ranges(out["range"], M)
     views_of = out["key_tile"].astype(np.int64) // f.range_stride
     out["key_depth"] = proj["depth"].view(np.uint32)[views_of * n + out["value"].astype(np.int64)]
     return out
+
+
+def keys_from_ranges(rng: np.ndarray, M: int) -> np.ndarray:
+    """The key (index into ``rng``) of each of the M pairs; every pair must lie in exactly
+    one non-empty range."""
+    key = np.full(M, 0xFFFFFFFF, np.uint32)
+    hits = np.zeros(M, np.int64)
+    for q in np.nonzero(rng[:, 1] > rng[:, 0])[0]:
+        a, b = int(rng[q, 0]), int(rng[q, 1])
+        assert b <= M, (q, a, b, M)
+        key[a:b] = q
+        hits[a:b] += 1
+    assert (hits == 1).all(), "ranges overlap or leave pairs out"
+    return key
 
 
 def run_backward(fwd: dict, grad_image: np.ndarray) -> dict:

@@ -1,6 +1,6 @@
 """Parity of the large-scan inference form: 1,000,000 Gaussians, 360 views 1 degree apart,
-1024 x 1024 detector, rendered 16 views per pass through one workspace (22 full passes
-and a ragged pass of 8), every pass captured in one CUDA graph.
+1024 x 1024 detector, rendered 16 views per pass (22 full passes and a ragged pass of 8)
+through two workspaces that alternate on two streams, every pass captured in one CUDA graph.
 
 * view 200 (pass 12) and view 359 (the ragged pass): image, transmittance and last
   contributor bit-exact against the FP32 replica; tile list lengths equal;
@@ -47,6 +47,7 @@ def scan():
 def test_every_pass_ok_and_ragged_tail(scan):
     sc = scan["scan"]
     assert sc.starts == list(range(0, V, VPP)) and len(sc.starts) == 23
+    assert len(sc.frames) == 2 and sc.frames[1].V == VPP
     st = sc.statuses()
     assert all(c == B.XG_OK for c, _, _, _ in st)
     assert all(p > 0 for _, p, _, _ in st)
@@ -84,7 +85,7 @@ def test_view_bit_exact_against_replica(scan, v):
 
 def test_single_view_frames_match_the_scan(scan):
     sc = scan["scan"]
-    for v in (1, 17, 352):
+    for v in (1, 17, 352):  # passes 0, 1 and 22: both workspaces
         cap = int(sc.frame.pair_capacity // VPP * 2)
         f = Frame(N, [scan["views"][v]], CFG, cap)
         f.project(*scan["dev"])

@@ -5,7 +5,8 @@ the GPU's memory pool, a real-time pipeline that forbids allocation after start-
 their (tile, depth, Gaussian) pairs with xg_sort_pairs_noalloc, whose scratch lives in a
 static device array inside the library.  These tests feed it the pairs xg_bin_sort emits
 and require xg_bin_sort's sorted output bit for bit, on two different calls in a row (the
-static array is shared by every call and keeps the previous call's contents).
+static array is shared by every call and keeps the previous call's contents).  The
+frame's pair keys are read off its ranges.
 
 The file is named so that pytest collects it last.
 """
@@ -17,6 +18,7 @@ torch = pytest.importorskip("torch")
 from paper_2403_04116_gb300 import binding as B  # noqa: E402
 from paper_2403_04116_gb300 import synth  # noqa: E402
 from paper_2403_04116_gb300.render import Frame, FrameConfig  # noqa: E402
+from tests.gpu_util import keys_from_ranges  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -83,7 +85,7 @@ def test_noalloc_sort_matches_bin_sort_twice(first, second):
         keys = f.V * f.tiles_per_view
         tile_bits = int(np.ceil(np.log2(keys))) if keys > 1 else 0
         got = _sort_noalloc(kt, kd, val, tile_bits)
-        key = f.array("key_tile")[:M].cpu().numpy().view(np.uint32).astype(np.int64)
+        key = keys_from_ranges(f.array("range").cpu().numpy().view(np.uint32), M).astype(np.int64)
         view, tile = key // f.range_stride, key % f.range_stride
         val_s = f.array("value")[:M].cpu().numpy().view(np.uint32)
         dbits = f.array("depth").cpu().numpy().view(np.uint32)
