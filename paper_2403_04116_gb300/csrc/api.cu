@@ -55,10 +55,8 @@ bool sizes_of(const xg_config* cfg, int64_t n, int64_t n_views, int32_t W, int32
   while (((int64_t)1 << bits) < s->tiles_per_view) ++bits;
   s->range_keys = n_views << bits;
   if (s->range_keys >= ((int64_t)1 << 31)) return false;
-  int vbits = 0;
-  while (((int64_t)1 << vbits) < n_views) ++vbits;
   s->tile_bits = bits;
-  s->entry_passes = 4 + (vbits + 7) / 8;
+  s->entry_passes = 4;
   // Pair scatter: groups of at most kBinGroupTiles tiles (whole rows), and units of sorted
   // entries sized for about 16 CTAs (unit, group) per SM, fewer where the per-(unit, tile)
   // counts would pass 2^24 words; every unit lies inside one view.
@@ -78,7 +76,7 @@ bool sizes_of(const xg_config* cfg, int64_t n, int64_t n_views, int32_t W, int32
 // Byte offsets of every array in the workspace, public and private, in allocation order.
 struct Offsets {
   size_t status, cameras, records, depth, rect, count;
-  size_t ent_view[2], ent_depth[2], ent_gid[2], value, hist, bin_hist, bin_total, range, order, tfinal, last, grad2d;
+  size_t ent_depth[2], ent_gid[2], value, hist, bin_hist, bin_total, range, order, tfinal, last, grad2d;
   size_t total;
 };
 
@@ -101,11 +99,11 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t n_scan, in
   o->depth = take(4 * VN);
   o->rect = take(8 * VN);
   o->count = take(4 * VN);
-  for (int b = 0; b < 2; ++b) o->ent_view[b] = take(4 * VN);
   for (int b = 0; b < 2; ++b) o->ent_depth[b] = take(4 * VN);
   for (int b = 0; b < 2; ++b) o->ent_gid[b] = take(4 * VN);
   o->value = take(4 * cap);
-  o->hist = take(4 * 256 * ((size_t)xg::kSortBlocks + 1));
+  // radix blocks of a pass of V' <= V views: V' * ceil(kSortBlocks / V') < kSortBlocks + V'
+  o->hist = take(4 * 256 * ((size_t)xg::kSortBlocks + (size_t)V + 1));
   o->bin_hist = take(4 * (size_t)V * (size_t)s->bin_units * (size_t)s->tiles_per_view);
   o->bin_total = take(4 * (size_t)V * (size_t)s->tiles_per_view);
   o->range = take(8 * (size_t)s->range_keys);
@@ -248,7 +246,6 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   p.rect = (ushort4*)(base + o.rect);
   p.count = (uint32_t*)(base + o.count);
   for (int k = 0; k < 2; ++k) {
-    p.ent_view[k] = (uint32_t*)(base + o.ent_view[k]);
     p.ent_depth[k] = (uint32_t*)(base + o.ent_depth[k]);
     p.ent_gid[k] = (uint32_t*)(base + o.ent_gid[k]);
   }

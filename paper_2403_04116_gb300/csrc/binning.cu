@@ -3,9 +3,10 @@
 //
 // The (tile, view, depth) order of the pairs is built without sorting the pairs:
 //
-//   1. the V*n (view, Gaussian) entries are sorted by (view, bits of t_z) with a stable LSD
-//      radix sort -- 4 depth passes and ceil(log2(V)/8) view passes over V*n entries
-//      (k_project writes the keys), so view v's entries are [v*n, (v+1)*n) in depth order;
+//   1. the V*n (view, Gaussian) entries, written by k_project at v*n + Gaussian, are sorted
+//      within each view by the bits of t_z with a stable LSD radix sort (4 passes of 8 bits
+//      over the (depth key, Gaussian) words, every view a segment of its own), so view v's
+//      entries [v*n, (v+1)*n) come out in (depth, index) order;
 //   2. each view's sorted entries are cut into units of E; per unit, the pairs falling on
 //      every tile are counted from the entries' tile rectangles with a 2-D difference array;
 //   3. a prefix over the units of each (view, tile) and a scan of the (view, tile) totals in
@@ -17,9 +18,9 @@
 //      of every (view, tile) comes out in (depth, index) order, contiguous, with no key
 //      array and no pass over the pairs other than the one that writes them.
 //
-// The radix passes run on a fixed grid of kSortBlocks CTAs that split the work into
-// contiguous chunks computed on the device from the item count; the binning grids depend
-// only on the frame's sizes.  The host never needs to know the pair count, so the whole
+// The radix passes run on about kSortBlocks CTAs, each view's segment split among
+// ceil(kSortBlocks / V) of them; these grids and the binning grids depend only on the
+// frame's sizes.  The host never needs to know the pair count, so the whole
 // sequence can be captured in a CUDA graph, and no CTA waits on another.
 #include <stdlib.h>
 
@@ -29,16 +30,17 @@ namespace xg {
 
 constexpr int kWarps = kSortThreads / 32;
 
-__device__ __forceinline__ int64_t chunk_of(int64_t total) {
-  // per-CTA chunk: ceil(total / kSortBlocks) rounded up to whole radix tiles
-  const int64_t c = (total + kSortBlocks - 1) / kSortBlocks;
-  return (c + kSortTile - 1) / kSortTile * kSortTile;
-}
-
-// Item count of a sort: `fixed` if it is >= 0, else the pairs recorded in the status word.
-__device__ __forceinline__ int64_t items_of(const DevStatus* st, int64_t fixed) {
-  if (fixed >= 0) return fixed;
-  return st->code == XG_OK ? st->pairs : 0;
+// Items [beg, end) of this CTA in a segmented radix pass: segment s = blockIdx.x / per_seg
+// holds items [s * seg_len, (s + 1) * seg_len) and is split among its per_seg CTAs in chunks
+// of whole radix tiles.
+__device__ __forceinline__ void sort_range(const SortGeom& g, int& seg, int64_t& beg, int64_t& end) {
+  seg = (int)(blockIdx.x / (unsigned)g.per_seg);
+  const int64_t j = blockIdx.x - (int64_t)seg * g.per_seg;
+  int64_t c = (g.seg_len + g.per_seg - 1) / g.per_seg;
+  c = (c + kSortTile - 1) / kSortTile * kSortTile;
+  const int64_t s0 = (int64_t)seg * g.seg_len, s1 = s0 + g.seg_len;
+  beg = min(s1, s0 + j * c);
+  end = min(s1, beg + c);
 }
 
 // exclusive scan of one value per thread across a block of NT threads; returns the total
@@ -76,15 +78,14 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T& total) {
 // digit totals.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ word, int shift, uint32_t mask,
-                                                             const DevStatus* __restrict__ st, int64_t fixed_count,
-                                                             uint32_t* __restrict__ hist) {
+                                                             SortGeom geom, uint32_t* __restrict__ hist) {
   __shared__ uint32_t s_h[kWarps][256];
   const int warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&s_h[0][0])[i] = 0;
   __syncthreads();
-  const int64_t total = items_of(st, fixed_count);
-  const int64_t chunk = chunk_of(total);
-  const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
+  int seg;
+  int64_t beg, end;
+  sort_range(geom, seg, beg, end);
   for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&s_h[warp][(word[i] >> shift) & mask], 1u);
   __syncthreads();
   uint32_t c = 0;
@@ -93,30 +94,25 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
   hist[blockIdx.x * 256 + threadIdx.x] = c;
 }
 
-// Per digit, the exclusive prefix over blocks of hist[block][digit], in place, and the
-// digit's total in hist[kSortBlocks][digit].  One CTA per digit; the scatter turns the totals
-// into digit bases itself.
-__global__ void __launch_bounds__(256) k_radix_colscan(uint32_t* __restrict__ hist) {
-  constexpr int kPer = (kSortBlocks + 255) / 256;
+// Per digit, the exclusive prefix over all blocks of hist[block][digit], in place, and the
+// digit's total in hist[blocks][digit] (counts wrap modulo 2^32; the scatter only takes
+// differences inside one segment).  One CTA per digit; the scatter turns the prefixes into
+// positions inside its segment itself.
+__global__ void __launch_bounds__(256) k_radix_colscan(uint32_t* __restrict__ hist, int blocks) {
   __shared__ uint32_t s_warp[kWarps];
   const int d = blockIdx.x;
-  const int b0 = threadIdx.x * kPer;
-  uint32_t c[kPer];
+  const int per = (blocks + 255) / 256;
+  const int b0 = min(blocks, (int)threadIdx.x * per), b1 = min(blocks, b0 + per);
   uint32_t local = 0;
-#pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    c[k] = b0 + k < kSortBlocks ? hist[(b0 + k) * 256 + d] : 0u;
-    local += c[k];
-  }
+  for (int b = b0; b < b1; ++b) local += hist[b * 256 + d];
   uint32_t total;
   uint32_t run = block_exclusive_scan<256>(local, s_warp, total);
-#pragma unroll
-  for (int k = 0; k < kPer; ++k)
-    if (b0 + k < kSortBlocks) {
-      hist[(b0 + k) * 256 + d] = run;
-      run += c[k];
-    }
-  if (threadIdx.x == 0) hist[kSortBlocks * 256 + d] = total;
+  for (int b = b0; b < b1; ++b) {
+    const uint32_t c = hist[b * 256 + d];
+    hist[b * 256 + d] = run;
+    run += c;
+  }
+  if (threadIdx.x == 0) hist[blocks * 256 + d] = total;
 }
 
 // ---- bulk asynchronous copies into shared memory, completed on an mbarrier ----------------
@@ -170,7 +166,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 template <int WORDS, int DW>
 __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(SortArrays<WORDS> arr, int shift,
                                                                                 uint32_t mask, uint32_t spin,
-                                                                DevStatus* __restrict__ st, int64_t fixed_count,
+                                                                DevStatus* __restrict__ st, SortGeom geom,
                                                                 const uint32_t* __restrict__ hist) {
   extern __shared__ __align__(128) uint32_t s_dyn[];  // [2][WORDS][kSortTile]
   // per warp and digit: the tile's count, then the digit's first slot in the reordered tile
@@ -183,22 +179,27 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const int64_t total = items_of(st, fixed_count);
-  const int64_t chunk = chunk_of(total);
-  const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(total, beg + chunk);
+  int seg;
+  int64_t beg, end;
+  sort_range(geom, seg, beg, end);
   if (beg >= end) return;
-  bool aligned = true;
+  const int64_t seg_base = (int64_t)seg * geom.seg_len;
+  bool aligned = true;  // every tile of the chunk starts 16-byte aligned in every array
 #pragma unroll
-  for (int w = 0; w < WORDS; ++w) aligned &= ((uintptr_t)arr.in[w] & 15u) == 0;
+  for (int w = 0; w < WORDS; ++w) aligned &= ((uintptr_t)(arr.in[w] + beg) & 15u) == 0;
 #define BULK_TILE(b) (aligned && end - (b) >= kSortTile)
 #define BUF(j, w) (s_dyn + (((j) & 1) * WORDS + (w)) * kSortTile)
   constexpr uint32_t kTileBytes = (uint32_t)(WORDS * kSortTile * sizeof(uint32_t));
-  // thread `tid` owns digit `tid`: its next output position for this CTA
+  // thread `tid` owns digit `tid`: its next output position for this CTA, counted from the
+  // start of the segment (prefix differences taken modulo 2^32 are exact: a segment holds
+  // fewer than 2^32 items)
   uint32_t bofs;
   {
+    const uint32_t first = hist[(seg * geom.per_seg) * 256 + tid];
+    const uint32_t in_seg = hist[((seg + 1) * geom.per_seg) * 256 + tid] - first;
     uint32_t all;
-    const uint32_t digit_base = block_exclusive_scan<kSortThreads>(hist[kSortBlocks * 256 + tid], s_warp, all);
-    bofs = digit_base + hist[blockIdx.x * 256 + tid];
+    const uint32_t digit_base = block_exclusive_scan<kSortThreads>(in_seg, s_warp, all);
+    bofs = digit_base + (hist[blockIdx.x * 256 + tid] - first);
   }
   for (int i = tid; i < kWarps * 128; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
   if (tid == 0) {
@@ -290,12 +291,12 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
     for (int i = tid; i < n_tile; i += kSortThreads) {
       const uint32_t d = (BUF(j, DW)[i] >> shift) & mask;
       const uint32_t pos = s_delta[d] + (uint32_t)i;
-      if ((int64_t)pos >= total) {  // cannot happen when the histograms are right
+      if ((int64_t)pos >= geom.seg_len) {  // cannot happen when the histograms are right
         st->code = XG_ERR_CHECK;
         continue;
       }
 #pragma unroll
-      for (int w = 0; w < WORDS; ++w) arr.out[w][pos] = BUF(j, w)[i];
+      for (int w = 0; w < WORDS; ++w) arr.out[w][seg_base + pos] = BUF(j, w)[i];
     }
     fence_proxy_async_smem();  // this buffer receives tile j+2 by bulk copy
     bofs += tile_count;
@@ -541,6 +542,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
   __shared__ __align__(16) uint32_t s_buf[8][TG];  // [slot][tile]
   __shared__ uint2 s_ent[2][kBinThreads];
   __shared__ uint32_t s_gid[2][kBinThreads];
+  __shared__ uint4 s_cmp[kW][32];  // per warp: its entries with pairs, compacted (prefix, packed, 1/width, Gaussian)
   if (st->code != XG_OK) return;
   const int64_t pairs = st->pairs;
   const BinWork w = bin_work(g);
@@ -582,23 +584,27 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
       const uint32_t pre = incl - cnt;
       const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
       if (tot == 0u) continue;
-      // local first row, first column and width - 1 (each < 512) in one word
-      const uint32_t packed = (uint32_t)(yf - w.r0) | (uint32_t)x0 << 10 | (wdt - 1u) << 20;
-      const float rcp = __frcp_rn((float)wdt);
+      // the entries with pairs, compacted in order: entry c's pairs are [pre_c, pre_c + cnt_c)
+      {
+        const uint32_t has = __ballot_sync(0xffffffffu, cnt > 0u);
+        if (cnt > 0u)  // local first row, first column and width - 1 (each < 512) in one word
+          s_cmp[warp][__popc(has & lt_mask)] =
+              make_uint4(pre, (uint32_t)(yf - w.r0) | (uint32_t)x0 << 10 | (wdt - 1u) << 20,
+                         __float_as_uint(__frcp_rn((float)wdt)), s_gid[buf][sub * 32 + lane]);
+        __syncwarp();
+      }
+      int last = -1;  // compacted entry holding the position before the round
       for (uint32_t p0 = 0; p0 < tot; p0 += 32) {
         const uint32_t p = p0 + lane;
-        // the last entry whose prefix is <= p (entries without pairs share the next prefix)
-        int ei = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int cand = min(ei + step, 31);
-          const uint32_t pc = __shfl_sync(0xffffffffu, pre, cand);
-          if (ei + step <= 31 && pc <= p) ei = cand;
-        }
-        const uint32_t e_pre = __shfl_sync(0xffffffffu, pre, ei);
-        const uint32_t e_pk = __shfl_sync(0xffffffffu, packed, ei);
-        const float e_rcp = __shfl_sync(0xffffffffu, rcp, ei);
-        const uint32_t e_gid = s_gid[buf][sub * 32 + ei];
+        // the round's entry starts as a bit mask over its positions; a lane's entry is the
+        // previous round's last one plus the starts at or before its position
+        const uint32_t starts =
+            __reduce_or_sync(0xffffffffu, cnt > 0u && pre - p0 < 32u ? 1u << (pre - p0) : 0u);
+        const int ei = last + __popc(starts & (0xffffffffu >> (31 - lane)));
+        last = __shfl_sync(0xffffffffu, ei, 31);
+        const uint4 ce = s_cmp[warp][ei];
+        const uint32_t e_pre = ce.x, e_pk = ce.y, e_gid = ce.w;
+        const float e_rcp = __uint_as_float(ce.z);
         const uint32_t k = p - e_pre, ew = (e_pk >> 20) + 1u;
         // k / ew: the quotient is below 64 and (k + 1/2) / ew is at least 1/(2 ew) >= 2^-10
         // away from an integer, far above the 2^-23 relative error of the two roundings
@@ -733,7 +739,7 @@ cudaError_t scatter_attrs() {
 cudaError_t radix_prepare() {
   static cudaError_t once = [] {
     cudaError_t e = scatter_attrs<2, 0>();
-    if (e == cudaSuccess) e = scatter_attrs<2, 1>();
+    if (e == cudaSuccess) e = scatter_attrs<2, 1>();  // instantiated by radix_pass<2>, unused
     if (e == cudaSuccess) e = scatter_attrs<3, 0>();
     if (e == cudaSuccess) e = scatter_attrs<3, 1>();
     return e;
@@ -743,54 +749,53 @@ cudaError_t radix_prepare() {
 
 template <int WORDS>
 cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, uint32_t mask,
-                       int64_t fixed_count,
-                       DevStatus* status, uint32_t* hist, cudaStream_t st) {
+                       const SortGeom& geom, DevStatus* status, uint32_t* hist, cudaStream_t st) {
   const cudaError_t prep = radix_prepare();
   if (prep != cudaSuccess) return prep;
+  const int blocks = geom.segments * geom.per_seg;
   {
     Timed t(f, kRadixHist, st);
-    k_radix_hist<<<kSortBlocks, kSortThreads, 0, st>>>(arr.in[digit_word], shift, mask, status, fixed_count, hist);
+    k_radix_hist<<<blocks, kSortThreads, 0, st>>>(arr.in[digit_word], shift, mask, geom, hist);
   }
   {
     Timed t(f, kRadixScan, st);
-    k_radix_colscan<<<256, 256, 0, st>>>(hist);
+    k_radix_colscan<<<256, 256, 0, st>>>(hist, blocks);
   }
   {
     Timed t(f, kRadixScatter, st);
     constexpr size_t smem = scatter_smem<WORDS>();
     if (digit_word == 0)
-      k_radix_scatter<WORDS, 0><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status,
-                                                                          fixed_count, hist);
+      k_radix_scatter<WORDS, 0><<<blocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status, geom,
+                                                                     hist);
     else
-      k_radix_scatter<WORDS, 1><<<kSortBlocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status,
-                                                                          fixed_count, hist);
+      k_radix_scatter<WORDS, 1><<<blocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status, geom,
+                                                                     hist);
   }
   return cudaGetLastError();
 }
 
-template cudaError_t radix_pass<2>(xg_frame*, const SortArrays<2>&, int, int, uint32_t, int64_t, DevStatus*, uint32_t*,
-                                    cudaStream_t);
-template cudaError_t radix_pass<3>(xg_frame*, const SortArrays<3>&, int, int, uint32_t, int64_t, DevStatus*, uint32_t*,
-                                    cudaStream_t);
+template cudaError_t radix_pass<2>(xg_frame*, const SortArrays<2>&, int, int, uint32_t, const SortGeom&, DevStatus*,
+                                    uint32_t*, cudaStream_t);
+template cudaError_t radix_pass<3>(xg_frame*, const SortArrays<3>&, int, int, uint32_t, const SortGeom&, DevStatus*,
+                                    uint32_t*, cudaStream_t);
 
 cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   const FramePtrs& p = f->p;
-  const int64_t VN = (int64_t)f->n_views * f->n;
   // every binning starts from a clean code (a failed check of an earlier call does not stick)
   {
     Timed t(f, kMemset, st);
     const cudaError_t e = cudaMemsetAsync(&p.status->code, 0, sizeof(p.status->code), st);
     if (e != cudaSuccess) return e;
   }
-  // stage 1: (view, depth) order of the V*n entries; words: view, depth bits, Gaussian
+  // stage 1: every view's n entries, [v*n, (v+1)*n), sorted by the depth bits as a segment
+  // of its own; words: depth bits, Gaussian
+  const SortGeom sg = sort_geom(f->n, f->n_views);
   int cur = 0;
   for (int pass = 0; pass < f->entry_passes; ++pass) {
-    const int digit_word = pass < 4 ? 1 : 0;
-    const int shift = pass < 4 ? 8 * pass : 8 * (pass - 4);
-    SortArrays<3> arr;
-    arr.in[0] = p.ent_view[cur], arr.in[1] = p.ent_depth[cur], arr.in[2] = p.ent_gid[cur];
-    arr.out[0] = p.ent_view[cur ^ 1], arr.out[1] = p.ent_depth[cur ^ 1], arr.out[2] = p.ent_gid[cur ^ 1];
-    const cudaError_t e = radix_pass<3>(f, arr, digit_word, shift, 255u, VN, p.status, p.hist, st);
+    SortArrays<2> arr;
+    arr.in[0] = p.ent_depth[cur], arr.in[1] = p.ent_gid[cur];
+    arr.out[0] = p.ent_depth[cur ^ 1], arr.out[1] = p.ent_gid[cur ^ 1];
+    const cudaError_t e = radix_pass<2>(f, arr, 0, 8 * pass, 255u, sg, p.status, p.hist, st);
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }

@@ -92,7 +92,8 @@ extern "C" xg_status xg_sort_pairs_noalloc(const uint32_t* key_tile, const uint3
       arr.in[w] = src[w];
       arr.out[w] = dst[w];
     }
-    if (radix_pass<3>(nullptr, arr, digit_word ? 0 : 1, shift, 255u, count, status, hist, st) != cudaSuccess)
+    if (radix_pass<3>(nullptr, arr, digit_word ? 0 : 1, shift, 255u, sort_geom(count, 1), status, hist, st) !=
+        cudaSuccess)
       return XG_ERR_CUDA;
     src[0] = dst[0];
     src[1] = dst[1];

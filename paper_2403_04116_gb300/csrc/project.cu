@@ -18,8 +18,8 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ mean,
                                                  const Camera* __restrict__ cams, int W, int H, int tw, int th,
                                                  float near_mm, float4* __restrict__ rec, float* __restrict__ depth,
                                                  ushort4* __restrict__ rect, uint32_t* __restrict__ count,
-                                                 uint32_t* __restrict__ ent_view, uint32_t* __restrict__ ent_depth,
-                                                 uint32_t* __restrict__ ent_gid, DevStatus* __restrict__ status) {
+                                                 uint32_t* __restrict__ ent_depth, uint32_t* __restrict__ ent_gid,
+                                                 DevStatus* __restrict__ status) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
   const int v = blockIdx.y;
@@ -137,8 +137,7 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ mean,
   depth[vg] = dz;
   rect[vg] = rc;
   count[vg] = cnt;
-  // keys of the (view, depth) sort of the entries
-  ent_view[vg] = (uint32_t)v;
+  // keys of the per-view depth sort of the entries
   ent_depth[vg] = __float_as_uint(dz);
   ent_gid[vg] = (uint32_t)g;
 }
@@ -149,7 +148,7 @@ cudaError_t launch_project(xg_frame* f, const xg_gaussians* g, cudaStream_t st) 
   Timed t(f, kProject, st);
   k_project<<<grid, 256, 0, st>>>(g->mean, g->scale, g->quat, g->opacity, g->intensity, n, f->p.cam, f->width,
                                   f->height, f->cfg.tile_w, f->cfg.tile_h, f->cfg.near_mm, f->p.rec, f->p.depth,
-                                  f->p.rect, f->p.count, f->p.ent_view[0], f->p.ent_depth[0], f->p.ent_gid[0],
+                                  f->p.rect, f->p.count, f->p.ent_depth[0], f->p.ent_gid[0],
                                   f->p.status);
   return cudaGetLastError();
 }

@@ -15,7 +15,7 @@
 
 namespace xg {
 
-constexpr int kMaxViews = 1 << 16;
+constexpr int kMaxViews = 65535;  // views of a frame (a grid dimension of the projection)
 constexpr int kNumSMs = 152;
 constexpr int kSortCtasPerSM = 4;
 constexpr int kSortBlocks = kSortCtasPerSM * kNumSMs;  // grid of the scan and radix-sort passes
@@ -155,11 +155,10 @@ struct FramePtrs {
   float* depth;       // [V*n]
   ushort4* rect;      // [V*n]
   uint32_t* count;    // [V*n]
-  uint32_t* ent_view[2];   // stage-1 sort of the V*n entries (ping-pong)
-  uint32_t* ent_depth[2];
+  uint32_t* ent_depth[2];  // stage-1 sort of the V*n entries (ping-pong): depth key, Gaussian
   uint32_t* ent_gid[2];
   uint32_t* value;    // [capacity]: Gaussian index of every pair, in (tile, view, depth) order
-  uint32_t* hist;     // [kSortBlocks + 1][256]: per-block digit counts, then digit totals
+  uint32_t* hist;     // [radix blocks + 1][256]: per-block digit counts, then digit totals
   uint32_t* bin_hist;   // [V][J][T]: pairs of each unit of entries per tile, then their prefix
   uint32_t* bin_total;  // [T][V]: pairs per (tile, view)
   uint2* range;       // [V << tile_bits]
@@ -174,6 +173,22 @@ struct AdamGroups {
   xg_adam_group g[XG_ADAM_MAX_GROUPS];
   int count;
 };
+
+// Segments of a radix pass: `segments` runs of seg_len items, [s*seg_len, (s+1)*seg_len),
+// each sorted on its own by per_seg CTAs (grid segments * per_seg).
+struct SortGeom {
+  int64_t seg_len;
+  int32_t segments, per_seg;
+};
+
+// About kSortBlocks CTAs over `segments` runs of seg_len items.
+inline SortGeom sort_geom(int64_t seg_len, int32_t segments) {
+  SortGeom g;
+  g.seg_len = seg_len;
+  g.segments = segments;
+  g.per_seg = (kSortBlocks + segments - 1) / segments;
+  return g;
+}
 
 // Input and output arrays of one radix pass, passed by value.
 template <int WORDS>
@@ -208,7 +223,7 @@ struct xg_frame {
   int64_t tiles_per_view;
   int32_t tile_bits;     // bits of a tile index within its view: pair key = view << tile_bits | tile
   int64_t range_keys;    // n_views << tile_bits: entries of the range array
-  int32_t entry_passes;  // stage-1 passes: 4 depth bytes + view bytes
+  int32_t entry_passes;  // stage-1 passes: the 4 depth bytes
   int32_t bin_unit;      // E: sorted entries per unit of the pair scatter
   int32_t bin_units;     // J: units per view, ceil(n / E)
   int32_t bin_rows;      // R: tile rows per group (R * tiles_x <= kBinGroupTiles)
@@ -247,12 +262,12 @@ cudaError_t launch_loss_l1(const float* image, const float* target, int64_t coun
                            float* loss, cudaStream_t st);
 
 // One LSD radix pass (histogram, digit scan, stable scatter; binning.cu) over WORDS arrays,
-// the digit (arr.in[digit_word] >> shift) & mask (mask <= 255).  The item count is
-// `fixed_count` when it is >= 0, else the pair count in the status word.  `f` may be NULL
+// the digit (arr.in[digit_word] >> shift) & mask (mask <= 255), every segment of `geom`
+// sorted on its own.  `hist` holds (segments * per_seg + 1) * 256 words.  `f` may be NULL
 // (no timing).
 template <int WORDS>
 cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, uint32_t mask,
-                       int64_t fixed_count, DevStatus* status, uint32_t* hist, cudaStream_t st);
+                       const SortGeom& geom, DevStatus* status, uint32_t* hist, cudaStream_t st);
 // Sets the scatter kernels' shared-memory attributes (once per process); call outside
 // stream capture before the first radix_pass.
 cudaError_t radix_prepare();
