@@ -523,12 +523,13 @@ __device__ __forceinline__ uint2 stage_entry(const BinGeom& g, const BinWork& w,
 // r0 + w + 8, ... of its rectangle, 32 pairs at a time.  Two pairs of one round on the same
 // tile come from different entries; match_any ranks them in lane (= entry) order.
 //
-// Stores are combined per 32-byte sector of the output: a tile's values wait in an 8-slot
-// shared buffer (slot = position mod 8) until the sector is complete, and then leave as two
-// 16-byte stores; a sector filled within one round is stored by its 8 lanes directly.  Only
-// the sectors a unit shares with its neighbours at the ends of a tile's run are written
-// value by value (the slots before the run hold kNoValue).
+// Stores are combined per kSlots values (16 bytes) of the output: a tile's values wait in a
+// kSlots-entry shared buffer (slot = position mod kSlots) until the run of kSlots is
+// complete, and then leave in one 16-byte store; a run filled within one round is stored by
+// its lanes directly.  Only the runs a unit shares with its neighbours at the ends of a
+// tile's list are written value by value (the slots before the list hold kNoValue).
 constexpr uint32_t kNoValue = 0xffffffffu;
+constexpr uint32_t kSlots = 4;
 
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const uint32_t* __restrict__ ent_gid,
                                                              const uint32_t* __restrict__ count,
@@ -537,9 +538,10 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
                                                              const uint2* __restrict__ range,
                                                              DevStatus* __restrict__ st, uint32_t* __restrict__ value) {
   constexpr int kW = kBinThreads / 32;  // warps; warp w owns the rows congruent to w mod kW
-  constexpr int TG = kBinGroupTiles;
-  __shared__ uint32_t s_pos[TG];
-  __shared__ __align__(16) uint32_t s_buf[8][TG];  // [slot][tile]
+  extern __shared__ uint32_t s_dyn[];  // next position of each tile, then [slot][tile] buffers
+  const int ntg = g.rows * g.tiles_x;   // tiles of a full group
+  uint32_t* const s_pos = s_dyn;
+  uint32_t* const s_buf = s_dyn + ntg;
   __shared__ uint2 s_ent[2][kBinThreads];
   __shared__ uint32_t s_gid[2][kBinThreads];
   __shared__ uint4 s_cmp[kW][32];  // per warp: its entries with pairs, compacted (prefix, packed, 1/width, Gaussian)
@@ -556,7 +558,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
     for (int k = threadIdx.x; k < nt; k += kBinThreads) {
       const uint32_t p = rng[k].x + hst[k];
       s_pos[k] = p;
-      for (uint32_t q = 0; q < (p & 7u); ++q) s_buf[q][k] = kNoValue;
+      for (uint32_t q = 0; q < (p & (kSlots - 1)); ++q) s_buf[q * ntg + k] = kNoValue;
     }
   }
   bool bad = false;  // a position past the pair count (cannot happen when the counts are right)
@@ -620,34 +622,34 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
           bad = true;
           valid = false;
         }
-        const bool done = valid && (pos | 7u) < end;     // its sector is complete after this round
-        const bool merge = done && (pos & ~7u) < old;    // ... and holds values of earlier rounds
+        constexpr uint32_t kLow = kSlots - 1u;
+        const bool done = valid && (pos | kLow) < end;   // its run of kSlots is complete after this round
+        const bool merge = done && (pos & ~kLow) < old;  // ... and holds values of earlier rounds
         __syncwarp();
         if (valid && lane == __ffs(peers) - 1) s_pos[tl] = end;
-        if (merge) s_buf[pos & 7u][tl] = e_gid;
+        if (merge) s_buf[(pos & kLow) * ntg + tl] = e_gid;
         __syncwarp();
-        if (merge && (pos & 7u) == 7u) {
-          uint32_t v[8];
+        if (merge && (pos & kLow) == kLow) {
+          uint32_t v[kSlots];
           bool whole = true;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            v[q] = s_buf[q][tl];
+          for (int q = 0; q < (int)kSlots; ++q) {
+            v[q] = s_buf[q * ntg + tl];
             whole &= v[q] != kNoValue;
           }
-          uint32_t* dst = value + (pos & ~7u);
+          uint32_t* dst = value + (pos & ~kLow);
           if (whole) {
-            reinterpret_cast<uint4*>(dst)[0] = make_uint4(v[0], v[1], v[2], v[3]);
-            reinterpret_cast<uint4*>(dst)[1] = make_uint4(v[4], v[5], v[6], v[7]);
+            *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
           } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
+            for (int q = 0; q < (int)kSlots; ++q)
               if (v[q] != kNoValue) dst[q] = v[q];
           }
         } else if (done && !merge) {
-          value[pos] = e_gid;  // the sector's 8 lanes store together
+          value[pos] = e_gid;  // the run's lanes store together
         }
         __syncwarp();
-        if (valid && !done) s_buf[pos & 7u][tl] = e_gid;
+        if (valid && !done) s_buf[(pos & kLow) * ntg + tl] = e_gid;
       }
     }
     if (more) {
@@ -656,12 +658,12 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
     }
     __syncthreads();
   }
-  // the last, incomplete sector of every tile's run
+  // the last, incomplete run of every tile's list
   for (int k = threadIdx.x; k < nt; k += kBinThreads) {
     const uint32_t p = s_pos[k];
-    uint32_t* dst = value + (p & ~7u);
-    for (uint32_t q = 0; q < (p & 7u); ++q) {
-      const uint32_t v = s_buf[q][k];
+    uint32_t* dst = value + (p & ~(kSlots - 1u));
+    for (uint32_t q = 0; q < (p & (kSlots - 1u)); ++q) {
+      const uint32_t v = s_buf[q * ntg + k];
       if (v != kNoValue) dst[q] = v;
     }
   }
@@ -734,11 +736,17 @@ cudaError_t scatter_attrs() {
   return e;
 }
 
+// Dynamic shared memory of the pair scatter: a position and kSlots buffer slots per tile of
+// a group.
+size_t bin_scatter_smem(int group_tiles) { return (size_t)(kSlots + 1) * 4 * (size_t)group_tiles; }
+
 // Dynamic shared memory of the scatter kernels, set once per process (the first call must
 // not be inside a stream capture; frame creation makes it).
 cudaError_t radix_prepare() {
   static cudaError_t once = [] {
-    cudaError_t e = scatter_attrs<2, 0>();
+    cudaError_t e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bin_scatter_smem(kBinGroupTiles));
+    if (e == cudaSuccess) e = scatter_attrs<2, 0>();
     if (e == cudaSuccess) e = scatter_attrs<2, 1>();  // instantiated by radix_pass<2>, unused
     if (e == cudaSuccess) e = scatter_attrs<3, 0>();
     if (e == cudaSuccess) e = scatter_attrs<3, 1>();
@@ -819,8 +827,8 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   }
   {
     Timed t(f, kBinScatter, st);
-    k_bin_scatter<<<ctas, kBinThreads, 0, st>>>(g, ent_gid, p.count, p.rect, p.bin_hist, p.range, p.status,
-                                                p.value);
+    k_bin_scatter<<<ctas, kBinThreads, bin_scatter_smem(f->bin_rows * f->tiles_x), st>>>(
+        g, ent_gid, p.count, p.rect, p.bin_hist, p.range, p.status, p.value);
   }
   {
     Timed t(f, kWorkOrder, st);

@@ -25,7 +25,7 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 // pair scatter: a CTA takes one unit of sorted entries and one group of tile rows whose
 // tiles (at most kBinGroupTiles) keep their next output position in shared memory
 constexpr int kBinThreads = 256;
-constexpr int kBinGroupTiles = 1024;
+constexpr int kBinGroupTiles = 2048;
 // iteration limit of every spin-wait in a kernel; on expiry the kernel records
 // XG_ERR_CHECK in the status word and returns
 constexpr uint32_t kSpinLimit = 1u << 22;
