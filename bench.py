@@ -68,10 +68,16 @@ SMS, FP32_LANES = 152, 128
 # DRAM traffic per launch from an ncu capture (profiles/k_render_train50k.md), valid while
 # the kernel source is unchanged (sha256 prefix of the .cu file) and for the configuration
 # it was taken with.
-TRAFFIC = {"k_render_bwd": {"bytes_per_launch": 329.0e6, "source_sha": "0c7af2037a1bc4a0",
-                            "config": (16, 16, 128, 2), "workload": "train50k"},
-           "k_render_fwd": {"bytes_per_launch": 131.0e6, "source_sha": "0c7af2037a1bc4a0",
-                            "config": (16, 16, 128, 2), "workload": "train50k"}}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels the
+# roofline line may name, from one ncu capture each (profiles/), valid only for the kernel
+# source (sha256 prefix of its .cu file), workload and (tile_w, tile_h, batch,
+# pixels_per_thread) they were taken with.
+TRAFFIC = [
+    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "cb0feed9d61363fb",
+     "bytes_per_launch": 350.8e6},
+    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "cb0feed9d61363fb",
+     "bytes_per_launch": 141.3e6},
+]
 
 
 def _args():
@@ -437,10 +443,9 @@ def run_ours(args) -> None:
     roof["frac"] = roof["achieved"] / roof["peak"]
     src = {"k_render_bwd": "render.cu", "k_render_fwd": "render.cu", "k_radix_scatter": "binning.cu",
            "k_project": "project.cu", "k_bin_scatter": "binning.cu", "k_project_bwd": "project.cu"}.get(dom)
-    tr = TRAFFIC.get(dom)
-    same = (tr and src and tr["source_sha"] == _source_sha(src) and tr["workload"] == args.workload
-            and tr["config"] == (tile[0], tile[1], batch, ppt))
-    roof["traffic"] = tr["bytes_per_launch"] if same else None
+    tr = next((t for t in TRAFFIC if t["kernel"] == dom and src and t["source_sha"] == _source_sha(src)
+               and t["workload"] == args.workload and t["config"] == (tile[0], tile[1], batch, ppt)), None)
+    roof["traffic"] = tr["bytes_per_launch"] if tr else None
     roof["kernel"] = dom
     roof["peak_source"] = (f"{SMS} SMs x {FP32_LANES} FP32 lanes x {clock_mhz:.0f} MHz" if roof["bound"] == "alu"
                            else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")
