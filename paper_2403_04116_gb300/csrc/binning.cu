@@ -521,7 +521,8 @@ __device__ __forceinline__ uint2 stage_entry(const BinGeom& g, const BinWork& w,
 // staged in shared memory (the next block's loads are in flight while one is processed);
 // warp w walks every entry of the block in order, but only over the tile rows r0 + w,
 // r0 + w + 8, ... of its rectangle, 32 pairs at a time.  Two pairs of one round on the same
-// tile come from different entries; match_any ranks them in lane (= entry) order.
+// tile come from different entries; a per-tile lane mask built with shared atomics ranks
+// them in lane (= entry) order.
 //
 // Stores are combined per kSlots values (16 bytes) of the output: a tile's values wait in a
 // kSlots-entry shared buffer (slot = position mod kSlots) until the run of kSlots is
@@ -538,10 +539,11 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
                                                              const uint2* __restrict__ range,
                                                              DevStatus* __restrict__ st, uint32_t* __restrict__ value) {
   constexpr int kW = kBinThreads / 32;  // warps; warp w owns the rows congruent to w mod kW
-  extern __shared__ uint32_t s_dyn[];  // next position of each tile, then [slot][tile] buffers
+  extern __shared__ uint32_t s_dyn[];  // per tile: next position, lane mask, then [slot][tile] buffers
   const int ntg = g.rows * g.tiles_x;   // tiles of a full group
   uint32_t* const s_pos = s_dyn;
-  uint32_t* const s_buf = s_dyn + ntg;
+  uint32_t* const s_mask = s_dyn + ntg;
+  uint32_t* const s_buf = s_dyn + 2 * ntg;
   __shared__ uint2 s_ent[2][kBinThreads];
   __shared__ uint32_t s_gid[2][kBinThreads];
   __shared__ uint4 s_cmp[kW][32];  // per warp: its entries with pairs, compacted (prefix, packed, 1/width, Gaussian)
@@ -558,6 +560,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
     for (int k = threadIdx.x; k < nt; k += kBinThreads) {
       const uint32_t p = rng[k].x + hst[k];
       s_pos[k] = p;
+      s_mask[k] = 0u;
       for (uint32_t q = 0; q < (p & (kSlots - 1)); ++q) s_buf[q * ntg + k] = kNoValue;
     }
   }
@@ -614,7 +617,11 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
         const uint32_t col = k - row * ew;
         const uint32_t tl = ((e_pk & 1023u) + row * kW) * (uint32_t)g.tiles_x + ((e_pk >> 10) & 1023u) + col;
         bool valid = p < tot;
-        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? tl : 0xffffffffu);
+        // the lanes of this round on the same tile, as a bit mask: earlier lanes hold earlier
+        // entries, so a lane's rank among them is the count of lower bits
+        if (valid) atomicOr(&s_mask[tl], 1u << lane);
+        __syncwarp();
+        const uint32_t peers = valid ? s_mask[tl] : 0u;
         const uint32_t old = valid ? s_pos[tl] : 0u;
         const uint32_t pos = old + (uint32_t)__popc(peers & lt_mask);
         const uint32_t end = old + (uint32_t)__popc(peers);
@@ -626,7 +633,10 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
         const bool done = valid && (pos | kLow) < end;   // its run of kSlots is complete after this round
         const bool merge = done && (pos & ~kLow) < old;  // ... and holds values of earlier rounds
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) s_pos[tl] = end;
+        if (valid && lane == __ffs(peers) - 1) {
+          s_pos[tl] = end;
+          s_mask[tl] = 0u;
+        }
         if (merge) s_buf[(pos & kLow) * ntg + tl] = e_gid;
         __syncwarp();
         if (merge && (pos & kLow) == kLow) {
@@ -736,9 +746,9 @@ cudaError_t scatter_attrs() {
   return e;
 }
 
-// Dynamic shared memory of the pair scatter: a position and kSlots buffer slots per tile of
-// a group.
-size_t bin_scatter_smem(int group_tiles) { return (size_t)(kSlots + 1) * 4 * (size_t)group_tiles; }
+// Dynamic shared memory of the pair scatter: a position, a lane mask and kSlots buffer
+// slots per tile of a group.
+size_t bin_scatter_smem(int group_tiles) { return (size_t)(kSlots + 2) * 4 * (size_t)group_tiles; }
 
 // Dynamic shared memory of the scatter kernels, set once per process (the first call must
 // not be inside a stream capture; frame creation makes it).

@@ -95,22 +95,26 @@ __device__ __forceinline__ float xg_exp(float x) {
 }
 
 // Packed two-lane FP32 (the f32x2 instructions of sm_100 and later): each lane is rounded
-// exactly as the scalar operation, so packed and scalar sequences give the same bits.
+// exactly as the scalar operation, so packed and scalar sequences give the same bits as
+// long as no packed multiply feeds a packed add that the compiler may fuse with it.
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// xg_exp of two values, lane for lane bit-identical to it: rint is taken by adding and
-// subtracting 1.5 * 2^23 (exact, ties to even, for |x log2 e| < 2^22), whose sum also holds
-// the integer k in its low mantissa bits.
+// xg_exp of two values, lane for lane bit-identical to it.  The integer k = rint(x log2 e)
+// is rounded per lane with rintf from the rounded product: forming it as
+// (x log2 e + 1.5 * 2^23) - 1.5 * 2^23 with packed instructions let the multiply and the
+// add be evaluated with a single rounding, which moves k by one (and the result by a few
+// ulps) where x log2 e lies within a rounding of a half-integer.  Adding 1.5 * 2^23 to the
+// integer k afterwards is exact and puts k in the low mantissa bits for the scale.
 __device__ __forceinline__ float2 xg_exp2v(float2 x) {
   constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
   constexpr int kRoundBits = 0x4B400000;
   x.x = fmaxf(x.x, -80.0f);
   x.y = fmaxf(x.y, -80.0f);
-  const float2 m = fadd2(fmul2(x, f2(kLog2e)), f2(kRound));
-  const float2 k = fadd2(m, f2(-kRound));
+  const float2 xl = fmul2(x, f2(kLog2e));
+  const float2 k = make_float2(rintf(xl.x), rintf(xl.y));
   float2 r = ffma2(k, f2(-kLn2Hi), x);
   r = ffma2(k, f2(-kLn2Lo), r);
   float2 p = ffma2(r, f2((float)(1.0 / 720.0)), f2((float)(1.0 / 120.0)));
@@ -119,6 +123,7 @@ __device__ __forceinline__ float2 xg_exp2v(float2 x) {
   p = ffma2(p, r, f2(0.5f));
   p = ffma2(p, r, f2(1.0f));
   p = ffma2(p, r, f2(1.0f));
+  const float2 m = fadd2(k, f2(kRound));
   const float2 scale = make_float2(__int_as_float((__float_as_int(m.x) - kRoundBits + 127) << 23),
                                    __int_as_float((__float_as_int(m.y) - kRoundBits + 127) << 23));
   return fmul2(p, scale);

@@ -1,0 +1,90 @@
+"""Binning paths that the small parity scenes do not reach, bit-exact against the FP32
+replica (the same expected index as test_gpu_parity.py: the replica's per-view tile lists
+laid out in (tile, view) order):
+
+* tile grids larger than one group of the pair scatter (2,048 tiles, whole rows): 8x8
+  tiles on 512x512 (4,096 tiles, two groups of 32 rows) and on 1024x512 (8,192 tiles,
+  four groups of 16 rows);
+* Gaussian counts that are not a multiple of 4, so the sorted entries of every view after
+  the first start off a 16-byte boundary (the radix scatter loads those chunks directly
+  instead of by bulk copy), and views cut into many units of sorted entries;
+* a scan whose last pass has fewer views but more radix blocks than a full pass: 36 views,
+  19 per pass (608 blocks) and a last pass of 17 (612 blocks); every view equals the same
+  view rendered by a frame of its own, and the last one equals the replica.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2403_04116_gb300 import binding as B  # noqa: E402
+from paper_2403_04116_gb300 import synth  # noqa: E402
+from paper_2403_04116_gb300.render import Frame, FrameConfig  # noqa: E402
+from tests.gpu_util import run_forward, to_device  # noqa: E402
+from tests.test_gpu_parity import _expected_index  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+# (Gaussians, views, W, H, tile, workload id)
+CASES = {
+    "two_groups_512_8x8": (20_001, 3, 512, 512, (8, 8), 21),
+    "four_groups_1024x512_8x8": (12_003, 2, 1024, 512, (8, 8), 22),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2403_04116_gb300 import build
+    build.build()
+    oracle.lib()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_large_tile_grids_bit_exact(name):
+    n, V, W, H, tile, cid = CASES[name]
+    g = synth.gaussians(n, synth.scene_side_mm(min(W, H)), synth.rng(cid, 0))
+    views = synth.circular_views(V, W, H, first_rad=0.1 * cid)
+    gpu = run_forward(g, views, tile)
+    f = gpu["frame"]
+    T = f.tiles_per_view
+    assert T > 2048  # more than one group of tile rows
+    reps, idx = _expected_index(g, views, tile)
+    assert gpu["status"].code == B.XG_OK
+    assert gpu["M"] == idx["M"] > 100_000
+    np.testing.assert_array_equal(gpu["key_tile"], idx["key_tile"])
+    np.testing.assert_array_equal(gpu["value"], idx["value"])
+    np.testing.assert_array_equal(gpu["range"], idx["range"])
+    for v, r in enumerate(reps):
+        np.testing.assert_array_equal(gpu["image"][v].view(np.uint32), r["image"].view(np.uint32))
+        np.testing.assert_array_equal(gpu["last"][v].view(np.uint32), r["last"])
+
+
+def test_ragged_pass_with_more_radix_blocks():
+    n, V, W, VPP = 4_001, 36, 96, 19
+    g = synth.gaussians(n, synth.scene_side_mm(W), synth.rng(23, 0))
+    views = synth.circular_views(V, W, W)
+    dev = to_device(g)
+    cfg = FrameConfig(16, 16)
+    f = Frame(n, views, cfg, 1 << 21, views_per_pass=VPP)
+    image = torch.full((V, W, W), -1.0, device="cuda")
+    for first in (0, VPP):
+        nv = f.select(first)
+        assert nv == (VPP if first == 0 else V - VPP)
+        f.project(*dev)
+        f.bin_sort()
+        f.render_fwd(image[first:first + nv])
+        assert f.status().code == B.XG_OK
+    f.select(0)
+    for v in (0, 18, 19, 27, 35):
+        one = Frame(n, [views[v]], cfg, 1 << 19)
+        one.project(*dev)
+        one.bin_sort()
+        img = torch.empty(1, W, W, device="cuda")
+        one.render_fwd(img)
+        assert one.status().code == B.XG_OK
+        assert torch.equal(img[0], image[v]), v
+    rep = oracle.replica_full(g, views[35], (16, 16))
+    np.testing.assert_array_equal(image[35].cpu().numpy().view(np.uint32), rep["image"].view(np.uint32))
