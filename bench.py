@@ -70,13 +70,13 @@ SMS, FP32_LANES = 152, 128
 # it was taken with.
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels the
 # roofline line may name, from one ncu capture each (profiles/), valid only for the kernel
-# source (sha256 prefix of its .cu file), workload and (tile_w, tile_h, batch,
-# pixels_per_thread) they were taken with.
+# source (sha256 prefix of its .cu file and the shared header), workload and (tile_w,
+# tile_h, batch, pixels_per_thread) they were taken with.
 TRAFFIC = [
-    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "cb0feed9d61363fb",
-     "bytes_per_launch": 350.8e6},
-    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "cb0feed9d61363fb",
-     "bytes_per_launch": 141.3e6},
+    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "1cf7cb480ae58a0c",
+     "bytes_per_launch": 350.7e6},
+    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "1cf7cb480ae58a0c",
+     "bytes_per_launch": 141.1e6},
 ]
 
 
@@ -198,8 +198,12 @@ def throughput(views_per_step: int, steps: int, world: int, total_ms: float) -> 
 
 
 def _source_sha(kernel_file: str) -> str:
-    path = os.path.join(ROOT, "paper_2403_04116_gb300", "csrc", kernel_file)
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    """sha256 prefix of a kernel's source file and the header every kernel includes."""
+    h = hashlib.sha256()
+    for name in (kernel_file, "xg_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2403_04116_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 # ------------------------------------------------------------------------------------------

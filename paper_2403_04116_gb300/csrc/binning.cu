@@ -517,8 +517,8 @@ __device__ __forceinline__ uint2 stage_entry(const BinGeom& g, const BinWork& w,
 }
 
 // Stage 4: the unit's pairs at their places.  The CTA's tiles keep their next output
-// position in shared memory (range start + the unit's prefix).  Blocks of 256 entries are
-// staged in shared memory (the next block's loads are in flight while one is processed);
+// position in shared memory (range start + the unit's prefix).  Blocks of kBinStage entries
+// are staged in shared memory (the next block's loads are in flight while one is processed);
 // warp w walks every entry of the block in order, but only over the tile rows r0 + w,
 // r0 + w + 8, ... of its rectangle, 32 pairs at a time.  Two pairs of one round on the same
 // tile come from different entries; a per-tile lane mask built with shared atomics ranks
@@ -531,6 +531,7 @@ __device__ __forceinline__ uint2 stage_entry(const BinGeom& g, const BinWork& w,
 // tile's list are written value by value (the slots before the list hold kNoValue).
 constexpr uint32_t kNoValue = 0xffffffffu;
 constexpr uint32_t kSlots = 4;
+constexpr int kBinStage = 256;  // sorted entries staged per block (one per thread)
 
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const uint32_t* __restrict__ ent_gid,
                                                              const uint32_t* __restrict__ count,
@@ -544,8 +545,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
   uint32_t* const s_pos = s_dyn;
   uint32_t* const s_mask = s_dyn + ntg;
   uint32_t* const s_buf = s_dyn + 2 * ntg;
-  __shared__ uint2 s_ent[2][kBinThreads];
-  __shared__ uint32_t s_gid[2][kBinThreads];
+  __shared__ uint2 s_ent[2][kBinStage];
+  __shared__ uint32_t s_gid[2][kBinStage];
   __shared__ uint4 s_cmp[kW][32];  // per warp: its entries with pairs, compacted (prefix, packed, 1/width, Gaussian)
   if (st->code != XG_OK) return;
   const int64_t pairs = st->pairs;
@@ -565,16 +566,21 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
     }
   }
   bool bad = false;  // a position past the pair count (cannot happen when the counts are right)
-  uint32_t gid_next;
-  uint2 ent_next = stage_entry(g, w, w.beg + threadIdx.x, ent_gid, count, rect, st, gid_next);
-  s_ent[0][threadIdx.x] = ent_next;
-  s_gid[0][threadIdx.x] = gid_next;
+  const bool stager = threadIdx.x < kBinStage;
+  uint32_t gid_next = 0u;
+  uint2 ent_next = make_uint2(0u, 1u);
+  if (stager) {
+    ent_next = stage_entry(g, w, w.beg + threadIdx.x, ent_gid, count, rect, st, gid_next);
+    s_ent[0][threadIdx.x] = ent_next;
+    s_gid[0][threadIdx.x] = gid_next;
+  }
   __syncthreads();
   int buf = 0;
-  for (int64_t blk = w.beg; blk < w.end; blk += kBinThreads, buf ^= 1) {
-    const bool more = blk + kBinThreads < w.end;
-    if (more) ent_next = stage_entry(g, w, blk + kBinThreads + threadIdx.x, ent_gid, count, rect, st, gid_next);
-    for (int sub = 0; sub < kBinThreads / 32; ++sub) {
+  for (int64_t blk = w.beg; blk < w.end; blk += kBinStage, buf ^= 1) {
+    const bool more = blk + kBinStage < w.end;
+    if (more && stager)
+      ent_next = stage_entry(g, w, blk + kBinStage + threadIdx.x, ent_gid, count, rect, st, gid_next);
+    for (int sub = 0; sub < kBinStage / 32; ++sub) {
       const uint2 e = s_ent[buf][sub * 32 + lane];
       const int x0 = (int)(e.x & 0xffffu), x1 = (int)(e.x >> 16), ya = (int)(e.y & 0xffffu), yb = (int)(e.y >> 16);
       const int yf = ya + ((warp - (ya - w.r0)) & (kW - 1));  // this warp's first row at or after ya
@@ -662,7 +668,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
         if (valid && !done) s_buf[(pos & kLow) * ntg + tl] = e_gid;
       }
     }
-    if (more) {
+    if (more && stager) {
       s_ent[buf ^ 1][threadIdx.x] = ent_next;
       s_gid[buf ^ 1][threadIdx.x] = gid_next;
     }
@@ -756,6 +762,9 @@ cudaError_t radix_prepare() {
   static cudaError_t once = [] {
     cudaError_t e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bin_scatter_smem(kBinGroupTiles));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess) e = scatter_attrs<2, 0>();
     if (e == cudaSuccess) e = scatter_attrs<2, 1>();  // instantiated by radix_pass<2>, unused
     if (e == cudaSuccess) e = scatter_attrs<3, 0>();
