@@ -533,6 +533,9 @@ constexpr uint32_t kNoValue = 0xffffffffu;
 constexpr uint32_t kSlots = 4;
 constexpr int kBinStage = 256;  // sorted entries staged per block (one per thread)
 
+// Words of a per-tile shared array of `tiles` tiles padded by one word every 32 tiles.
+__host__ __device__ __forceinline__ int bin_padded(int tiles) { return tiles + (tiles >> 5) + 1; }
+
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const uint32_t* __restrict__ ent_gid,
                                                              const uint32_t* __restrict__ count,
                                                              const ushort4* __restrict__ rect,
@@ -540,11 +543,14 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
                                                              const uint2* __restrict__ range,
                                                              DevStatus* __restrict__ st, uint32_t* __restrict__ value) {
   constexpr int kW = kBinThreads / 32;  // warps; warp w owns the rows congruent to w mod kW
-  extern __shared__ uint32_t s_dyn[];  // per tile: next position, lane mask, then [slot][tile] buffers
-  const int ntg = g.rows * g.tiles_x;   // tiles of a full group
+  // per tile: next position, lane mask, then [slot][tile] buffers; tile t sits at
+  // t + t / 32 so that tiles a multiple of 32 apart (a warp's rows) use different banks
+  extern __shared__ uint32_t s_dyn[];
+  const int ntg = g.rows * g.tiles_x;  // tiles of a full group
+  const int npad = bin_padded(ntg);
   uint32_t* const s_pos = s_dyn;
-  uint32_t* const s_mask = s_dyn + ntg;
-  uint32_t* const s_buf = s_dyn + 2 * ntg;
+  uint32_t* const s_mask = s_dyn + npad;
+  uint32_t* const s_buf = s_dyn + 2 * npad;
   __shared__ uint2 s_ent[2][kBinStage];
   __shared__ uint32_t s_gid[2][kBinStage];
   __shared__ uint4 s_cmp[kW][32];  // per warp: its entries with pairs, compacted (prefix, packed, 1/width, Gaussian)
@@ -560,9 +566,10 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
     const uint32_t* hst = bin_hist + w.u * g.tiles + t0;
     for (int k = threadIdx.x; k < nt; k += kBinThreads) {
       const uint32_t p = rng[k].x + hst[k];
-      s_pos[k] = p;
-      s_mask[k] = 0u;
-      for (uint32_t q = 0; q < (p & (kSlots - 1)); ++q) s_buf[q * ntg + k] = kNoValue;
+      const int kp = k + (k >> 5);
+      s_pos[kp] = p;
+      s_mask[kp] = 0u;
+      for (uint32_t q = 0; q < (p & (kSlots - 1)); ++q) s_buf[q * npad + kp] = kNoValue;
     }
   }
   bool bad = false;  // a position past the pair count (cannot happen when the counts are right)
@@ -621,7 +628,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
         // away from an integer, far above the 2^-23 relative error of the two roundings
         const uint32_t row = __float2uint_rz(__fmul_rn(__uint2float_rn(k) + 0.5f, e_rcp));
         const uint32_t col = k - row * ew;
-        const uint32_t tl = ((e_pk & 1023u) + row * kW) * (uint32_t)g.tiles_x + ((e_pk >> 10) & 1023u) + col;
+        const uint32_t tl0 = ((e_pk & 1023u) + row * kW) * (uint32_t)g.tiles_x + ((e_pk >> 10) & 1023u) + col;
+        const uint32_t tl = tl0 + (tl0 >> 5);  // padded index of the tile
         bool valid = p < tot;
         // the lanes of this round on the same tile, as a bit mask: earlier lanes hold earlier
         // entries, so a lane's rank among them is the count of lower bits
@@ -643,14 +651,14 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
           s_pos[tl] = end;
           s_mask[tl] = 0u;
         }
-        if (merge) s_buf[(pos & kLow) * ntg + tl] = e_gid;
+        if (merge) s_buf[(pos & kLow) * npad + tl] = e_gid;
         __syncwarp();
         if (merge && (pos & kLow) == kLow) {
           uint32_t v[kSlots];
           bool whole = true;
 #pragma unroll
           for (int q = 0; q < (int)kSlots; ++q) {
-            v[q] = s_buf[q * ntg + tl];
+            v[q] = s_buf[q * npad + tl];
             whole &= v[q] != kNoValue;
           }
           uint32_t* dst = value + (pos & ~kLow);
@@ -665,7 +673,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
           value[pos] = e_gid;  // the run's lanes store together
         }
         __syncwarp();
-        if (valid && !done) s_buf[(pos & kLow) * ntg + tl] = e_gid;
+        if (valid && !done) s_buf[(pos & kLow) * npad + tl] = e_gid;
       }
     }
     if (more && stager) {
@@ -676,10 +684,11 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
   }
   // the last, incomplete run of every tile's list
   for (int k = threadIdx.x; k < nt; k += kBinThreads) {
-    const uint32_t p = s_pos[k];
+    const int kp = k + (k >> 5);
+    const uint32_t p = s_pos[kp];
     uint32_t* dst = value + (p & ~(kSlots - 1u));
     for (uint32_t q = 0; q < (p & (kSlots - 1u)); ++q) {
-      const uint32_t v = s_buf[q * ntg + k];
+      const uint32_t v = s_buf[q * npad + kp];
       if (v != kNoValue) dst[q] = v;
     }
   }
@@ -754,7 +763,7 @@ cudaError_t scatter_attrs() {
 
 // Dynamic shared memory of the pair scatter: a position, a lane mask and kSlots buffer
 // slots per tile of a group.
-size_t bin_scatter_smem(int group_tiles) { return (size_t)(kSlots + 2) * 4 * (size_t)group_tiles; }
+size_t bin_scatter_smem(int group_tiles) { return (size_t)(kSlots + 2) * 4 * (size_t)bin_padded(group_tiles); }
 
 // Dynamic shared memory of the scatter kernels, set once per process (the first call must
 // not be inside a stream capture; frame creation makes it).
