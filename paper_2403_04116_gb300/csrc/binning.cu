@@ -521,8 +521,9 @@ __device__ __forceinline__ uint2 stage_entry(const BinGeom& g, const BinWork& w,
 // are staged in shared memory (the next block's loads are in flight while one is processed);
 // warp w walks every entry of the block in order, but only over the tile rows r0 + w,
 // r0 + w + 8, ... of its rectangle, 32 pairs at a time.  Two pairs of one round on the same
-// tile come from different entries; a per-tile lane mask built with shared atomics ranks
-// them in lane (= entry) order.
+// tile come from different entries and are ranked in lane (= entry) order, by a per-tile
+// lane mask built with shared atomics (kMaskRank; cheaper on large dense groups, whose full
+// rounds hold 32 distinct tiles) or by match_any (cheaper on small groups).
 //
 // Stores are combined per kSlots values (16 bytes) of the output: a tile's values wait in a
 // kSlots-entry shared buffer (slot = position mod kSlots) until the run of kSlots is
@@ -532,10 +533,12 @@ __device__ __forceinline__ uint2 stage_entry(const BinGeom& g, const BinWork& w,
 constexpr uint32_t kNoValue = 0xffffffffu;
 constexpr uint32_t kSlots = 4;
 constexpr int kBinStage = 256;  // sorted entries staged per block (one per thread)
+constexpr int kBinMaskRankTiles = 1024;  // groups above this many tiles rank by lane mask
 
 // Words of a per-tile shared array of `tiles` tiles padded by one word every 32 tiles.
 __host__ __device__ __forceinline__ int bin_padded(int tiles) { return tiles + (tiles >> 5) + 1; }
 
+template <bool kMaskRank>
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const uint32_t* __restrict__ ent_gid,
                                                              const uint32_t* __restrict__ count,
                                                              const ushort4* __restrict__ rect,
@@ -633,9 +636,14 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
         bool valid = p < tot;
         // the lanes of this round on the same tile, as a bit mask: earlier lanes hold earlier
         // entries, so a lane's rank among them is the count of lower bits
-        if (valid) atomicOr(&s_mask[tl], 1u << lane);
-        __syncwarp();
-        const uint32_t peers = valid ? s_mask[tl] : 0u;
+        uint32_t peers;
+        if constexpr (kMaskRank) {
+          if (valid) atomicOr(&s_mask[tl], 1u << lane);
+          __syncwarp();
+          peers = valid ? s_mask[tl] : 0u;
+        } else {
+          peers = __match_any_sync(0xffffffffu, valid ? tl : 0xffffffffu);
+        }
         const uint32_t old = valid ? s_pos[tl] : 0u;
         const uint32_t pos = old + (uint32_t)__popc(peers & lt_mask);
         const uint32_t end = old + (uint32_t)__popc(peers);
@@ -649,7 +657,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
         __syncwarp();
         if (valid && lane == __ffs(peers) - 1) {
           s_pos[tl] = end;
-          s_mask[tl] = 0u;
+          if constexpr (kMaskRank) s_mask[tl] = 0u;
         }
         if (merge) s_buf[(pos & kLow) * npad + tl] = e_gid;
         __syncwarp();
@@ -769,11 +777,10 @@ size_t bin_scatter_smem(int group_tiles) { return (size_t)(kSlots + 2) * 4 * (si
 // not be inside a stream capture; frame creation makes it).
 cudaError_t radix_prepare() {
   static cudaError_t once = [] {
-    cudaError_t e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bin_scatter_smem(kBinGroupTiles));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared);
+    cudaError_t e = cudaSuccess;
+    for (const void* k : {(const void*)k_bin_scatter<true>, (const void*)k_bin_scatter<false>})
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_scatter_smem(kBinGroupTiles));
     if (e == cudaSuccess) e = scatter_attrs<2, 0>();
     if (e == cudaSuccess) e = scatter_attrs<2, 1>();  // instantiated by radix_pass<2>, unused
     if (e == cudaSuccess) e = scatter_attrs<3, 0>();
@@ -855,8 +862,13 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   }
   {
     Timed t(f, kBinScatter, st);
-    k_bin_scatter<<<ctas, kBinThreads, bin_scatter_smem(f->bin_rows * f->tiles_x), st>>>(
-        g, ent_gid, p.count, p.rect, p.bin_hist, p.range, p.status, p.value);
+    const int group_tiles = f->bin_rows * f->tiles_x;
+    if (group_tiles > kBinMaskRankTiles)
+      k_bin_scatter<true><<<ctas, kBinThreads, bin_scatter_smem(group_tiles), st>>>(
+          g, ent_gid, p.count, p.rect, p.bin_hist, p.range, p.status, p.value);
+    else
+      k_bin_scatter<false><<<ctas, kBinThreads, bin_scatter_smem(group_tiles), st>>>(
+          g, ent_gid, p.count, p.rect, p.bin_hist, p.range, p.status, p.value);
   }
   {
     Timed t(f, kWorkOrder, st);
