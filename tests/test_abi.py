@@ -49,6 +49,16 @@ def test_workspace_bytes_host_checks(lib):
         assert B.xg_workspace_bytes(bad, 10, 1, 64, 64) == 0
 
 
+def test_pairs_cost_one_index_each(lib):
+    # the pairs are written once, as 4-byte Gaussian indices at their final place: no key
+    # array and no second buffer, so pair capacity costs exactly 4 bytes a pair
+    def ws(cap, tile=(16, 16), W=64):
+        return B.xg_workspace_bytes(B.XgConfig(tile[0], tile[1], 0.2, 0, cap), 1000, 3, W, W)
+    for tile, W in (((16, 16), 64), ((8, 8), 1024), ((32, 16), 512)):
+        assert ws((1 << 20) + 4096, tile, W) - ws(1 << 20, tile, W) == 4 * 4096
+        assert ws((1 << 24) + 64, tile, W) - ws(1 << 24, tile, W) == 4 * 64
+
+
 def test_workspace_of_a_scan_rendered_in_passes(lib):
     def ws(V, per_pass):
         return B.xg_workspace_bytes(B.XgConfig(16, 16, 0.2, 0, 1 << 20, 2, per_pass), 1000, V, 64, 64)
