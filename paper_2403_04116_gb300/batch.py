@@ -282,7 +282,7 @@ def build_scan(n: int, views, cfg: FrameConfig, views_per_pass: int, gaussians: 
     return scan
 
 
-def autotune_scan(n: int, views, gaussians: tuple, tiles=((16, 16), (32, 16)), passes=(8, 16, 30),
+def autotune_scan(n: int, views, gaussians: tuple, tiles=((16, 16), (32, 16)), passes=(8, 12, 16, 30),
                   shapes=((128, 2), (256, 2), (256, 1)), reps: int = 3) -> tuple:
     """Tile shape and views per pass, then staging batch and pixels per thread, with the
     fastest replay of the captured scan; returns (FrameConfig, views_per_pass, ms)."""
