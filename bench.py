@@ -120,7 +120,7 @@ def _config(name: str, w: dict, n_gpus: int) -> dict:
     if w.get("forward_only"):
         return {"workload": name, "gaussians": w["n"], "views": w["views"], "detector": [w["W"], w["H"]],
                 "step": "forward projection of every view",
-                "l2": "inputs larger than L2 (pairs of each pass: several GB)", "parallelism": f"replicas x{n_gpus}"}
+                "l2": "inputs larger than L2 (the pair list of one pass alone exceeds it)", "parallelism": f"replicas x{n_gpus}"}
     return {"workload": name, "gaussians": w["n"], "views": w["views"], "detector": [w["W"], w["H"]],
             "loss": "L1 vs FP64 ellipsoid-phantom projections",
             "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{n_gpus}"}
