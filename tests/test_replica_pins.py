@@ -21,6 +21,24 @@ def test_exp_accuracy(oracle_lib):
     assert oracle.replica_exp(np.float32([0.0]))[0] == 1.0
 
 
+def test_exp_at_the_reduction_boundaries(oracle_lib):
+    # x log2 e within a few ulps of k + 1/2: the remainder is near +-ln2/2, the polynomial's
+    # worst case, and rint switches k there.  Every float in a window around each boundary
+    # above the clamp at x = -80 (k = -114 .. 0): within the error bound of FP64 exp, and
+    # non-decreasing across the switch
+    xs = []
+    for k in range(-114, 1):
+        c = np.float32((k - 0.5) / np.log2(np.e))
+        b = c.view(np.uint32).astype(np.int64)
+        xs.append(np.arange(b - 40, b + 41).astype(np.uint32).view(np.float32))
+    for x in xs:
+        x = np.sort(x)
+        y = oracle.replica_exp(x)
+        ref = np.exp(x.astype(np.float64))
+        assert np.max(np.abs(y.astype(np.float64) / ref - 1)) < 4e-7
+        assert np.all(np.diff(y.astype(np.float64)) >= 0), x[0]
+
+
 def test_log_accuracy(oracle_lib):
     x = np.concatenate([np.linspace(1, 255, 200001, dtype=np.float32), np.float32([1.0, 1.4142135, 1.4142137, 2])])
     y = oracle.replica_log(x).astype(np.float64)
