@@ -215,6 +215,13 @@ xg_status xg_frame_copy_status(const xg_frame* frame, xg_device_status* out, voi
 /* Byte offsets of the frame's arrays inside its workspace. */
 xg_status xg_frame_layout(const xg_frame* frame, xg_layout* out);
 
+/* The FP32 exponential the compositing kernels use in their opacity decisions (Cody-Waite
+ * reduction by ln 2, degree-6 polynomial, argument clamped at -80), evaluated on the device
+ * in its scalar form into y_scalar and in its two-lane packed form into y_packed, for tests
+ * that hold both to an independent implementation bit for bit.  x, y_scalar, y_packed:
+ * device float[n].  Errors: XG_ERR_INVALID_ARG (null pointer, n < 1 or n > 2^38), XG_ERR_CUDA. */
+xg_status xg_exp_check(const float* x, float* y_scalar, float* y_packed, int64_t n, void* stream);
+
 /* L1 term of the training objective (Eq. 11):
  *   *loss = scale * sum_i |image[i] - target[i]|,  grad[i] = scale * sign(image[i] - target[i])
  * image, target, grad: device float[count]; loss: one device float, overwritten.  Use

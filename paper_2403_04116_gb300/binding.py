@@ -21,7 +21,7 @@ XG_ERR_CHECK = 5
 EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_frame_select_views", "xg_fdk_workspace_bytes", "xg_fdk", "xg_densify_stats", "xg_densify_workspace_bytes",
            "xg_densify_plan", "xg_densify_apply", "xg_opacity_reset", "xg_acui_count", "xg_acui_points", "xg_frame_copy_status", "xg_project",
            "xg_bin_sort",
-           "xg_render_fwd", "xg_render_bwd", "xg_frame_read_status", "xg_frame_layout", "xg_loss_l1",
+           "xg_render_fwd", "xg_render_bwd", "xg_frame_read_status", "xg_frame_layout", "xg_exp_check", "xg_loss_l1",
            "xg_frame_set_timing", "xg_frame_read_timing", "xg_activate", "xg_activate_bwd",
            "xg_loss_workspace_bytes", "xg_loss_l1_ssim", "xg_adam_step", "xg_psnr", "xg_sort_pairs_noalloc",
            "xg_status_str")
@@ -153,6 +153,8 @@ def lib(build_if_missing: bool = False):
     L.xg_frame_layout.restype = ctypes.c_int
     L.xg_loss_l1.argtypes = [P, P, ctypes.c_int64, ctypes.c_float, P, P, P]
     L.xg_loss_l1.restype = ctypes.c_int
+    L.xg_exp_check.argtypes = [P, P, P, ctypes.c_int64, P]
+    L.xg_exp_check.restype = ctypes.c_int
     L.xg_frame_set_timing.argtypes = [P, ctypes.c_int32]
     L.xg_frame_set_timing.restype = ctypes.c_int
     L.xg_frame_read_timing.argtypes = [P, ctypes.POINTER(XgKernelTime), ctypes.c_int32,
@@ -270,6 +272,10 @@ def xg_frame_layout(frame: int) -> XgLayout:
     L = XgLayout()
     _check(lib().xg_frame_layout(frame, ctypes.byref(L)), "xg_frame_layout")
     return L
+
+
+def xg_exp_check(x: int, y_scalar: int, y_packed: int, n: int, stream: int) -> None:
+    _check(lib().xg_exp_check(x, y_scalar, y_packed, n, stream), "xg_exp_check")
 
 
 def xg_loss_l1(image: int, target: int, count: int, scale: float, grad: int, loss: int, stream: int) -> None:

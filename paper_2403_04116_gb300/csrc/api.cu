@@ -378,6 +378,11 @@ xg_status xg_loss_l1(const float* image, const float* target, int64_t count, flo
              : XG_ERR_CUDA;
 }
 
+xg_status xg_exp_check(const float* x, float* y_scalar, float* y_packed, int64_t n, void* stream) {
+  if (!x || !y_scalar || !y_packed || n < 1 || n > ((int64_t)1 << 38)) return XG_ERR_INVALID_ARG;
+  return xg::launch_exp_check(x, y_scalar, y_packed, n, (cudaStream_t)stream) == cudaSuccess ? XG_OK : XG_ERR_CUDA;
+}
+
 static bool valid_gaussians(const xg_frame* f, const xg_gaussians* g) {
   return g && g->n == f->n && g->mean && g->scale && g->quat && g->opacity && g->intensity;
 }

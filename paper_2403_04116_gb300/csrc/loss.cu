@@ -52,4 +52,27 @@ cudaError_t launch_loss_l1(const float* image, const float* target, int64_t coun
   return cudaGetLastError();
 }
 
+// The decision exponential, scalar and packed, for tests: thread i takes x[2i] and x[2i+1]
+// (the second lane repeats the first when n is odd).
+__global__ void __launch_bounds__(256) k_exp_check(const float* __restrict__ x, float* __restrict__ ys,
+                                                   float* __restrict__ yp, int64_t n) {
+  const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n) return;
+  const bool two = i + 1 < n;
+  const float a = x[i], b = two ? x[i + 1] : a;
+  const float2 p = xg_exp2v(make_float2(a, b));
+  ys[i] = xg_exp(a);
+  yp[i] = p.x;
+  if (two) {
+    ys[i + 1] = xg_exp(b);
+    yp[i + 1] = p.y;
+  }
+}
+
+cudaError_t launch_exp_check(const float* x, float* ys, float* yp, int64_t n, cudaStream_t st) {
+  const int64_t pairs = (n + 1) / 2;
+  k_exp_check<<<(unsigned)((pairs + 255) / 256), 256, 0, st>>>(x, ys, yp, n);
+  return cudaGetLastError();
+}
+
 }  // namespace xg

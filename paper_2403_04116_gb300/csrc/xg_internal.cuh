@@ -265,6 +265,7 @@ cudaError_t launch_render_bwd(xg_frame* f, const float* grad_image, cudaStream_t
 cudaError_t launch_project_bwd(xg_frame* f, const xg_gaussians* g, const xg_grads* out, cudaStream_t st);
 cudaError_t launch_loss_l1(const float* image, const float* target, int64_t count, float scale, float* grad,
                            float* loss, cudaStream_t st);
+cudaError_t launch_exp_check(const float* x, float* ys, float* yp, int64_t n, cudaStream_t st);
 
 // One LSD radix pass (histogram, digit scan, stable scatter; binning.cu) over WORDS arrays,
 // the digit (arr.in[digit_word] >> shift) & mask (mask <= 255), every segment of `geom`
