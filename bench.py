@@ -73,9 +73,9 @@ SMS, FP32_LANES = 152, 128
 # source (sha256 prefix of its .cu file and the shared header), workload and (tile_w,
 # tile_h, batch, pixels_per_thread) they were taken with.
 TRAFFIC = [
-    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "1cf7cb480ae58a0c",
+    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "b9be39cdea390350",
      "bytes_per_launch": 350.7e6},
-    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "1cf7cb480ae58a0c",
+    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "b9be39cdea390350",
      "bytes_per_launch": 141.1e6},
 ]
 
