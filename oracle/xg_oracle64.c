@@ -24,8 +24,9 @@
  *     Eq. 9, 8, 7 and Sigma = R S S^T R^T to mean, scale, quaternion, opacity, intensity.
  *
  * The Gaussian-pixel cost is brute force.  The only acceleration is a bounding-box
- * prefilter that cannot drop an included Gaussian: inclusion needs
- * |d|^2 <= 2 ln(255 o) lambda_max(Sigma''), and the box is that radius with a margin.
+ * prefilter that cannot drop an included Gaussian, nor one within the ambiguity margin of
+ * the inclusion threshold: sigma >= (1 - m)/255 needs |d|^2 <= 2 ln(255 o / (1 - m))
+ * lambda_max(Sigma''), and the box is that radius with a margin.
  */
 #include <math.h>
 #include <stdint.h>
@@ -166,10 +167,13 @@ static void project_one(int64_t n, int64_t g, const double* mean, const double* 
   pg->K[2] = A / det;
   pg->o = o;
   pg->i = in;
-  if (!(o * 255.0 >= 1.0)) return; /* sigma can never reach 1/255 */
+  /* Candidates are the Gaussians whose sigma can reach the inclusion threshold or come
+   * within the ambiguity margin below it: those below the threshold are never blended,
+   * but a pixel where one sits within the margin is flagged. */
+  if (!(o * 255.0 >= 1.0 - XO_MARGIN_ALPHA)) return;
   double mid = 0.5 * (A + C);
   double lam = mid + sqrt(fmax(mid * mid - det, 0.0));
-  double r = sqrt(2.0 * log(255.0 * o) * lam) * (1.0 + 1e-9) + 1e-9;
+  double r = sqrt(2.0 * log(255.0 * o / (1.0 - XO_MARGIN_ALPHA)) * lam) * (1.0 + 1e-9) + 1e-9;
   if (!isfinite(r) || !isfinite(pg->u[0]) || !isfinite(pg->u[1])) return;
   pg->bx0 = pg->u[0] - r;
   pg->bx1 = pg->u[0] + r;
