@@ -63,7 +63,10 @@ def metric_train(w: dict) -> str:
 # recovered transmittance, blend-behind update and six dL/dpower moments (backward).
 FWD_OPS_EVAL, FWD_OPS_CONTRIB = 20, 4
 BWD_OPS_EVAL, BWD_OPS_CONTRIB = 20, 30
-SMS, FP32_LANES = 152, 128
+# The same work charged per evaluated pair alone, as the method's per-pixel loop costs it:
+# forward 17 FP32 operations + one exp (about 10), backward 35 + one exp.
+FWD_OPS_PAIR, BWD_OPS_PAIR = 27, 45
+FP32_LANES = 128
 
 # DRAM traffic per launch from an ncu capture (profiles/k_render_train50k.md), valid while
 # the kernel source is unchanged (sha256 prefix of the .cu file) and for the configuration
@@ -104,6 +107,32 @@ def _peaks() -> dict:
             d = json.load(f)
         return {"hbm_gbs": d["hbm_gbs"], "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def fp32_peak(repeats: int = 5) -> dict:
+    """The FP32 pipe's peak, measured: the library's FMA-chain kernel (8 CTAs of 256 threads
+    per SM, 8 independent chains a thread), scalar and packed, best of ``repeats`` CUDA-event
+    timed launches of each (burst, one short kernel), in T FP32 operations/s (a multiply-add
+    is one operation, as in the kernels' charged counts)."""
+    import torch
+    from paper_2403_04116_gb300 import binding as B
+    sink = torch.zeros(1, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for packed, key in ((0, "ffma"), (1, "ffma2")):
+        best = 0.0
+        for r in range(repeats + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ops = B.xg_fp32_peak(packed, 4096, sink.data_ptr(), stream)
+            b.record()
+            b.synchronize()
+            if r:  # the first launch warms up
+                best = max(best, ops / (a.elapsed_time(b) * 1e-3) / 1e12)
+        out[key] = best
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    out["sms"] = props.multi_processor_count
+    return out
 
 
 def _workload(name: str):
@@ -210,11 +239,15 @@ def _source_sha(kernel_file: str) -> str:
 # CPU oracle (the baseline and the reference arm)
 # ------------------------------------------------------------------------------------------
 
-def cpu_oracle_rate(name: str, target_seconds: float = 12.0) -> dict:
+def cpu_oracle_rate(name: str, target_seconds: float = 12.0, collect: dict | None = None) -> dict:
     """Oracle forward + gradient (forward only for a forward-only workload; FP64, all host
     cores) on a bounded sample of the workload: whole views while one view takes under
     ``target_seconds``, else a random pixel sample of one view; projections/s scaled from
-    the sample."""
+    the sample.  The gradient is that of the summed L1 loss (upstream sign(I - target),
+    zero on pixels the oracle flags as ambiguous).  With ``collect`` (a dict) the oracle's
+    outputs of the last timed sample are kept there, each view once: images, flags,
+    upstream gradients and the gradient summed over the distinct views, for the accuracy
+    figures of the bench line."""
     import oracle
     from paper_2403_04116_gb300 import synth
     w, g, views, ph = _workload(name)
@@ -224,19 +257,32 @@ def cpu_oracle_rate(name: str, target_seconds: float = 12.0) -> dict:
 
     def run(view_ids, pix=None) -> float:
         tg = None if fwd_only else synth.phantom_targets(ph, [views[i] for i in view_ids])
+        keep = {"pixels": pix, "image": {}, "amb": {}, "G": {}, "grad": None} if collect is not None else None
         t0 = time.perf_counter()
         for k, i in enumerate(view_ids):
             v = views[i]
             r = oracle.render64(g, v, pixels=pix)
+            first = keep is not None and i not in keep["image"]
+            if first:
+                keep["image"][i], keep["amb"][i] = r["image"], r["ambiguous"]
             if fwd_only:
                 continue
-            G = np.sign(np.nan_to_num(r["image"]) - tg[k]) / npx
+            G = np.sign(np.nan_to_num(r["image"]) - tg[k])
+            G[r["ambiguous"] != 0] = 0.0
             if pix is not None:
                 mask = np.zeros(npx, bool)
                 mask[pix] = True
                 G.reshape(-1)[~mask] = 0.0
-            oracle.grad64(g, v, G, pixels=pix)
-        return time.perf_counter() - t0
+            if first:
+                keep["G"][i] = G
+                keep["grad"] = oracle.grad64(g, v, G, pixels=pix, out=keep["grad"])
+            else:
+                oracle.grad64(g, v, G, pixels=pix)
+        t = time.perf_counter() - t0
+        if keep is not None:
+            collect.clear()
+            collect.update(keep)
+        return t
 
     if fwd_only:  # a view of the workload takes minutes: time pixel samples, grown until
         p, t = 256, 0.0  # the sample fills most of the target (a fixed projection cost dominates
@@ -262,9 +308,56 @@ def cpu_oracle_rate(name: str, target_seconds: float = 12.0) -> dict:
         t = run(ids)
         rate, sample = len(ids) / t, f"{len(ids)} views of {w['views']} (repeated if fewer), all pixels, {t:.1f} s"
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    what = "forward" if fwd_only else "forward + gradient (L1 vs phantom)"
+    what = "forward" if fwd_only else "forward + gradient (summed L1 vs phantom)"
     return {"value": rate, "unit": "projections/s", "cores": threads, "kind": "oracle",
             "sample": f"FP64 oracle {what}, {sample}"}
+
+
+GRAD_RTOL, GRAD_ATOL, GRAD_TERM_REL = 1e-3, 1e-6, 3e-5
+
+
+def accuracy_block(kept: dict, image: np.ndarray, grads: dict | None) -> dict:
+    """Accuracy of the GPU results against the oracle outputs kept by the CPU-baseline run:
+    pixels (1e-4 absolute on pixels the oracle does not flag; flagged ones counted) and,
+    for a training workload, every parameter gradient of the Gaussians that reach the
+    sampled views (strict: 1e-3 relative with a 1e-6 floor; the tests' bound adds 3e-5 of
+    the sum of |per-pixel terms| behind each gradient)."""
+    pix = kept["pixels"]
+    errs, flagged, total, err_fl, over = [], 0, 0, 0.0, 0
+    for i, ref in kept["image"].items():
+        amb = kept["amb"][i].reshape(-1)
+        got = image[i].reshape(-1).astype(np.float64)
+        want = ref.reshape(-1)
+        sel = np.arange(want.size) if pix is None else pix
+        e = np.abs(got[sel] - want[sel])
+        a = amb[sel] != 0
+        errs.append(e[~a].max(initial=0.0))
+        err_fl = max(err_fl, float(e[a].max(initial=0.0)))
+        flagged += int(a.sum())
+        over += int((e > 1e-4).sum())
+        total += sel.size
+    out = {"views": sorted(int(i) for i in kept["image"]), "pixels_checked": total,
+           "pixel_max_abs_err_unflagged": float(max(errs)), "pixel_tol": 1e-4,
+           "flagged_pixels": flagged, "flagged_frac": flagged / max(1, total), "pixels_over_tol": over,
+           "pixel_max_abs_err_flagged": err_fl}
+    if grads is not None and kept["grad"] is not None:
+        ora = kept["grad"]
+        n_all = n_strict = n_budget = 0
+        worst = 0.0
+        for k in ("mean", "scale", "quat", "opacity", "intensity"):
+            want, got, mag = ora[k], grads[k].astype(np.float64), ora["mag"][k]
+            live = mag > 0
+            err = np.abs(got - want)[live]
+            strict = GRAD_RTOL * np.abs(want[live]) + GRAD_ATOL
+            n_all += int(live.sum())
+            n_strict += int((err <= strict).sum())
+            n_budget += int((err <= strict + GRAD_TERM_REL * mag[live]).sum())
+            worst = max(worst, float((err / strict).max(initial=0.0)))
+        out.update({"grad_params_checked": n_all, "grad_strict_frac": n_strict / max(1, n_all),
+                    "grad_strict_fails": n_all - n_strict, "grad_max_err_over_strict_tol": worst,
+                    "grad_within_term_budget_frac": n_budget / max(1, n_all),
+                    "grad_upstream": "summed L1: sign(I - target), 0 on flagged pixels"})
+    return out
 
 
 def cpu_replica_rate(name: str, target_seconds: float = 6.0) -> dict:
@@ -298,11 +391,15 @@ def run_reference(args) -> None:
     rates = [cpu_oracle_rate(args.workload, target_seconds=per_step) for _ in range(args.steps)]
     value = statistics.median(r["value"] for r in rates)
     metric = metric_scan(w) if w.get("forward_only") else metric_train(w)
+    extrap = (f"each of the {args.steps} timed steps is a bounded sample (about {per_step:.0f} s of CPU work) of "
+              f"the {w['views']}-view workload; value is the median sampled rate and ms_per_step is extrapolated "
+              f"from it to all {w['views']} views ({1000.0 * w['views'] / value / 1000.0:.1f} s), not timed whole")
+    cfg_line = {**_config(args.workload, w, 1), "step": extrap}
     line = {"metric": metric, "value": value, "unit": "projections/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * w["views"] / value, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(args.workload, w, 1), "impl": "reference",
-            "cpu_baseline": {**rates[-1], "value": value},
+            "warmup": args.warmup, "ms_per_step": 1000.0 * w["views"] / value, "ms_per_step_extrapolated": True,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": cfg_line, "impl": "reference",
+            "cpu_baseline": {**rates[-1], "value": value, "sample": rates[-1]["sample"] + "; " + extrap},
             "e2e": {"value": value, "unit": "projections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -426,18 +523,14 @@ def run_ours(args) -> None:
 
     # roofline of the dominant kernel
     peaks = _peaks()
+    fp32 = fp32_peak()
     ours = {k: v for k, v in kernels.items() if k != "memset"}
     dom = max(ours, key=lambda k: ours[k][1])
     launches, dom_ms = ours[dom]
     avg_ms = dom_ms / launches
-    clock_mhz = peaks["sm_max_mhz"]
-    alu_peak = SMS * FP32_LANES * clock_mhz * 1e6 / 1e12  # T FP32 lane-instructions / s
-    if dom == "k_render_bwd":
-        ops = BWD_OPS_EVAL * st.bwd_evaluated + BWD_OPS_CONTRIB * st.bwd_contrib
-        roof = {"bound": "alu", "achieved": ops / (avg_ms * 1e-3) / 1e12, "peak": alu_peak, "unit": "TFP32op/s"}
-    elif dom == "k_render_fwd":
-        ops = FWD_OPS_EVAL * st.fwd_evaluated + FWD_OPS_CONTRIB * st.fwd_contrib
-        roof = {"bound": "alu", "achieved": ops / (avg_ms * 1e-3) / 1e12, "peak": alu_peak, "unit": "TFP32op/s"}
+    alu_peak, alu_src = _alu_peak(fp32, peaks)
+    if dom in ("k_render_bwd", "k_render_fwd"):
+        roof = _alu_roof(dom, st.fwd_evaluated, st.fwd_contrib, st.bwd_evaluated, st.bwd_contrib, avg_ms, alu_peak)
     else:
         VN = V * n
         M = int(st.pairs)
@@ -451,9 +544,16 @@ def run_ours(args) -> None:
                and t["workload"] == args.workload and t["config"] == (tile[0], tile[1], batch, ppt)), None)
     roof["traffic"] = tr["bytes_per_launch"] if tr else None
     roof["kernel"] = dom
-    roof["peak_source"] = (f"{SMS} SMs x {FP32_LANES} FP32 lanes x {clock_mhz:.0f} MHz" if roof["bound"] == "alu"
-                           else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")
+    roof["peak_source"] = alu_src if roof["bound"] == "alu" else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})"
     roof["avg_launch_ms"] = avg_ms
+    # the other compositing kernel, charged the same way
+    other = "k_render_fwd" if dom == "k_render_bwd" else "k_render_bwd"
+    if other in ours:
+        o = _alu_roof(other, st.fwd_evaluated, st.fwd_contrib, st.bwd_evaluated, st.bwd_contrib,
+                      ours[other][1] / ours[other][0], alu_peak)
+        roof["other_compositing"] = {"kernel": other, **{k: o[k] for k in ("achieved", "frac", "achieved_per_pair",
+                                                                          "frac_per_pair")},
+                                     "avg_launch_ms": ours[other][1] / ours[other][0]}
 
     launches_per_step = sum(nl for k, (nl, _) in kernels.items() if k != "memset") / timing_steps + 1  # + loss kernel
     gpu_launches = int(round(launches_per_step * args.steps))
@@ -503,10 +603,21 @@ def run_ours(args) -> None:
         e2e_autograd = {"value": timed_host(e2e_step), "unit": "projections/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": 4, "path": "render() autograd + L1Loss, uncaptured stream launches"}
 
-    cpu = cpu_replica = None
+    cpu = cpu_replica = accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_oracle_rate(args.workload)
+        kept = {}
+        cpu = cpu_oracle_rate(args.workload, collect=kept)
         cpu_replica = cpu_replica_rate(args.workload)
+        # the GPU gradient for the upstream gradient the oracle used on the sampled views
+        Gs = torch.zeros(V, H, W, device="cuda")
+        for i, Gv in kept["G"].items():
+            Gs[i] = torch.from_numpy(Gv.astype(np.float32))
+        step.replay()
+        agrads = tuple(torch.empty_like(t) for t in step.inputs)
+        frame.render_bwd(step.inputs, Gs, agrads)
+        torch.cuda.synchronize()
+        accuracy = accuracy_block(kept, step.image.cpu().numpy(),
+                                  {k: t.cpu().numpy() for k, t in zip(names, agrads)})
 
     if rank == 0:
         cfg_line = _config(args.workload, w, world)
@@ -524,7 +635,8 @@ def run_ours(args) -> None:
                     "ms_per_step": ms_plain / plain_steps},
                 "stream_launched": {"ms_per_step": ms_stream_step},
                 "clocks": clock_info, "e2e": e2e, "e2e_autograd": e2e_autograd, "gpu_launches": gpu_launches,
-                "roofline": roof, "cpu_baseline": cpu, "cpu_replica": cpu_replica, "pairs": int(st.pairs),
+                "roofline": roof, "accuracy": accuracy, "fp32_peak": fp32, "cpu_baseline": cpu,
+                "cpu_replica": cpu_replica, "pairs": int(st.pairs),
                 "work": {"fwd_evaluated": int(st.fwd_evaluated), "fwd_contrib": int(st.fwd_contrib),
                          "bwd_evaluated": int(st.bwd_evaluated), "bwd_contrib": int(st.bwd_contrib)},
                 "kernels_ms_per_step": {k: round(v[1] / timing_steps, 4) for k, v in sorted(kernels.items())}}
@@ -533,13 +645,42 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def _alu_peak(fp32: dict, peaks: dict) -> tuple[float, str]:
+    """The FP32 roof: the measured FMA-chain rate (the better of scalar and packed)."""
+    best = max(fp32["ffma"], fp32["ffma2"])
+    nominal = fp32["sms"] * FP32_LANES * peaks["sm_max_mhz"] * 1e6 / 1e12
+    return best, (f"measured: FMA chains on {fp32['sms']} SMs, burst, best of 5 launches "
+                  f"(scalar {fp32['ffma']:.2f}, packed {fp32['ffma2']:.2f} T FP32 op/s; nominal "
+                  f"{fp32['sms']} SMs x {FP32_LANES} lanes x {peaks['sm_max_mhz']:.0f} MHz = {nominal:.2f})")
+
+
+def _alu_roof(kernel: str, f_eval: int, f_contrib: int, b_eval: int, b_contrib: int, avg_ms: float,
+              peak: float) -> dict:
+    """FP32 rate of a compositing launch, charged two ways: per evaluated pair plus per
+    contributor (the split), and per evaluated pair alone (the method's per-pixel loop)."""
+    if kernel == "k_render_bwd":
+        ops = BWD_OPS_EVAL * b_eval + BWD_OPS_CONTRIB * b_contrib
+        ops_pair = BWD_OPS_PAIR * b_eval
+    else:
+        ops = FWD_OPS_EVAL * f_eval + FWD_OPS_CONTRIB * f_contrib
+        ops_pair = FWD_OPS_PAIR * f_eval
+    ach = ops / (avg_ms * 1e-3) / 1e12
+    ach_pair = ops_pair / (avg_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFP32op/s", "frac": ach / peak,
+            "achieved_per_pair": ach_pair, "frac_per_pair": ach_pair / peak,
+            "charge": (f"split: {BWD_OPS_EVAL if kernel == 'k_render_bwd' else FWD_OPS_EVAL} per evaluated pair + "
+                       f"{BWD_OPS_CONTRIB if kernel == 'k_render_bwd' else FWD_OPS_CONTRIB} per contributor; "
+                       f"per_pair: {BWD_OPS_PAIR if kernel == 'k_render_bwd' else FWD_OPS_PAIR} per evaluated pair")}
+
+
 def _algo_bytes(kernel: str, n: int, VN: int, M: int, entry_passes: int) -> float:
     """Algorithmic DRAM bytes of one step's launches of a memory-bound kernel (each input
-    read once, each output written once): the entry sort moves 3 words in and out per
-    pass; the binning kernels read each sorted entry's index, count and rectangle (16 B)
-    and the scatter writes one 4-byte index per pair."""
-    return {"k_radix_scatter": 24 * VN * entry_passes, "k_radix_hist": 4 * VN * entry_passes,
-            "k_project": 48 * n + 72 * VN, "k_project_bwd": 32 * VN + 56 * n,
+    read once, each output written once): projection reads the 48-byte Gaussian and writes
+    a 48-byte (record, depth, rectangle, count) per (view, Gaussian); the entry sort moves 2
+    words in and out per pass; the binning kernels read each sorted entry's index, count and
+    rectangle (16 B) and the scatter writes one 4-byte index per pair."""
+    return {"k_radix_scatter": 16 * VN * entry_passes, "k_radix_hist": 4 * VN * entry_passes,
+            "k_project": 48 * n + 48 * VN, "k_project_bwd": 32 * VN + 56 * n,
             "k_bin_count": 16 * VN, "k_bin_scatter": 16 * VN + 4 * M}.get(kernel, 0)
 
 
@@ -623,7 +764,8 @@ def run_scan(args) -> None:
     ms_total, ms_stream = reduce_max([ms_total, ms_stream], device="cuda")
     value = throughput(V, args.steps, world, ms_total)
     peaks = _peaks()
-    alu_peak = SMS * FP32_LANES * peaks["sm_max_mhz"] * 1e6 / 1e12
+    fp32 = fp32_peak()
+    alu_peak, alu_src = _alu_peak(fp32, peaks)
     VN = V * n
     entry_passes = frame.layout.sort_passes
     stages = {}
@@ -632,8 +774,9 @@ def run_scan(args) -> None:
             continue
         ms /= timing_steps
         if k == "k_render_fwd":
-            ach = (FWD_OPS_EVAL * f_eval + FWD_OPS_CONTRIB * f_contrib) / (ms * 1e-3) / 1e12
-            stages[k] = {"bound": "alu", "ms": ms, "achieved": ach, "unit": "TFP32op/s", "frac": ach / alu_peak}
+            r_ = _alu_roof(k, f_eval, f_contrib, 0, 0, ms, alu_peak)
+            stages[k] = {"ms": ms, **{q: r_[q] for q in ("bound", "achieved", "unit", "frac", "achieved_per_pair",
+                                                          "frac_per_pair")}}
         else:
             b = _algo_bytes(k, n * len(scan.starts), VN, M, entry_passes)
             if b:
@@ -647,8 +790,9 @@ def run_scan(args) -> None:
     roof = {"bound": d["bound"], "achieved": d["achieved"],
             "peak": alu_peak if d["bound"] == "alu" else peaks["hbm_gbs"], "unit": d["unit"], "frac": d["frac"],
             "traffic": None, "kernel": dom, "avg_launch_ms": d["ms"] / launches,
-            "peak_source": (f"{SMS} SMs x {FP32_LANES} FP32 lanes x {peaks['sm_max_mhz']:.0f} MHz"
-                            if d["bound"] == "alu" else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")}
+            "peak_source": alu_src if d["bound"] == "alu" else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})"}
+    if d["bound"] == "alu":
+        roof.update({"achieved_per_pair": d["achieved_per_pair"], "frac_per_pair": d["frac_per_pair"]})
     gpu_launches = int(round(sum(nl for k, (nl, _) in kernels.items() if k != "memset") / timing_steps
                              + len(scan.starts))) * args.steps  # + one status copy per pass
 
@@ -677,9 +821,13 @@ def run_scan(args) -> None:
                "steps": k, "path": "GraphedScan.load + replay_host: pinned H2D of the Gaussians, per-pass D2H of "
                                    "the projections overlapped with the next passes"}
 
-    cpu = None
+    cpu = accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_oracle_rate(args.workload)
+        kept = {}
+        cpu = cpu_oracle_rate(args.workload, collect=kept)
+        scan.replay()
+        torch.cuda.synchronize()
+        accuracy = accuracy_block(kept, {i: scan.image[i].cpu().numpy() for i in kept["image"]}, None)
     if rank == 0:
         cfg_line = _config(args.workload, w, world)
         cfg_line.update({"tile": [cfg.tile_w, cfg.tile_h], "staging_batch": cfg.batch,
@@ -691,7 +839,7 @@ def run_scan(args) -> None:
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": cfg_line, "stream_launched": {"ms_per_step": ms_stream / timing_steps},
                 "clocks": clock_info, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
-                "cpu_baseline": cpu, "pairs": int(M), "pairs_per_pass_max": int(max(p for _, p, _, _ in stats)),
+                "accuracy": accuracy, "fp32_peak": fp32, "cpu_baseline": cpu, "pairs": int(M), "pairs_per_pass_max": int(max(p for _, p, _, _ in stats)),
                 "work": {"fwd_evaluated": int(f_eval), "fwd_contrib": int(f_contrib)}, "stages": stages,
                 "kernels_ms_per_step": {k: round(v[1] / timing_steps, 4) for k, v in sorted(kernels.items())}}
         print(json.dumps(line), flush=True)

@@ -368,7 +368,8 @@ typedef struct {
  * `stream`; graph-capturable.  Errors: XG_ERR_INVALID_ARG, XG_ERR_CUDA. */
 xg_status xg_densify_stats(xg_frame* frame, float scale, float* accum, int32_t* denom, void* stream);
 
-/* Device scratch bytes xg_densify_plan needs. */
+/* Device scratch bytes xg_densify_plan needs on the current device (one partial count
+ * per CTA of its scan, 4 CTAs per SM). */
 size_t xg_densify_workspace_bytes(void);
 
 /* The plan: offsets[g] (device, n + 1 entries) = first output slot of Gaussian g in the
@@ -438,18 +439,43 @@ xg_status xg_fdk(const xg_view* views, int32_t n_views, const float* projections
  * Scratch: a static device array of about 12.6 MB inside the library (ping-pong buffers
  * for XG_NOALLOC_MAX_PAIRS pairs, digit histograms, the pair count), held by every GPU that
  * loads the library until the process exits.  The call allocates nothing and frees
- * nothing.  Its first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls on a device
- * share the array and the last call's contents stay in it: calls whose work overlaps on
- * the GPU (different streams without ordering between them) race and give wrong results;
- * order them on one stream.
+ * nothing.  Each call made outside a stream capture looks up the array's device address
+ * on the current device (so the address stays valid across cudaDeviceReset); a call made
+ * inside a capture reuses the address of the last call outside one, so make a first call
+ * on each device before capturing (XG_ERR_CUDA otherwise).  All calls on a device share
+ * the array and the last call's contents stay in it: calls whose work overlaps on the GPU
+ * (different streams without ordering between them) race and give wrong results; order
+ * them on one stream.
  *
  * Errors: XG_ERR_INVALID_ARG if count < 0, count > XG_NOALLOC_MAX_PAIRS, tile_bits is out
  * of range or a pointer is NULL (nothing is enqueued); XG_ERR_CUDA if the address lookup
- * or a launch fails.  count == 0 enqueues nothing. */
+ * or a launch fails.  count == 0 enqueues nothing.  Failures on the device (a position
+ * outside its segment, a bounded wait that gave up) do not reach the return code, which
+ * is known before the kernels run: they are recorded in the array's status word, which
+ * xg_sort_pairs_noalloc_status reads. */
 xg_status xg_sort_pairs_noalloc(const uint32_t* key_tile, const uint32_t* key_depth, const uint32_t* value,
                                 int64_t count, int32_t tile_bits, uint32_t* out_key_tile, uint32_t* out_key_depth,
                                 uint32_t* out_value, void* stream);
+
+/* Device-side outcome of the last xg_sort_pairs_noalloc on the current device (no
+ * counterpart in the paper; it completes the allocation-free sort above).  Waits for
+ * `stream` (the stream the sort ran on), then writes to *device_code XG_OK, or
+ * XG_ERR_CHECK when a radix pass recorded a failed bounds check or a bounded wait that
+ * gave up (the output is then not sorted).  Allocates nothing.  Each sort call starts
+ * from XG_OK.  Returns XG_ERR_INVALID_ARG for a NULL device_code, XG_ERR_CUDA if the
+ * synchronisation or the read fails. */
+xg_status xg_sort_pairs_noalloc_status(void* stream, int32_t* device_code);
+
+/* Measurement aid, no counterpart in the paper: the FP32 pipe's peak rate, the roofline
+ * denominator of the compositing kernels (no stage is a dense contraction).  Enqueues on
+ * `stream` one launch of 8 CTAs of 256 threads per SM of the current device, each thread
+ * running `iters` rounds of 8 independent fused multiply-add chains: scalar FFMA
+ * (packed = 0) or two-lane packed FFMA (packed = 1).  *lane_ops (host) receives the FP32
+ * multiply-adds the launch performs (a packed one counts two); time the launch with CUDA
+ * events on `stream`.  `sink` (device, one float) is written only for inputs that never
+ * occur.  Errors: XG_ERR_INVALID_ARG (NULL pointer, iters < 1, packed not 0 or 1),
+ * XG_ERR_CUDA. */
+xg_status xg_fp32_peak(int32_t packed, int32_t iters, float* sink, int64_t* lane_ops, void* stream);
 
 /* Text for a status code (static storage). */
 const char* xg_status_str(xg_status s);

@@ -23,7 +23,7 @@ EXPORTS = ("xg_workspace_bytes", "xg_frame_create", "xg_frame_destroy", "xg_fram
            "xg_bin_sort",
            "xg_render_fwd", "xg_render_bwd", "xg_frame_read_status", "xg_frame_layout", "xg_exp_check", "xg_loss_l1",
            "xg_frame_set_timing", "xg_frame_read_timing", "xg_activate", "xg_activate_bwd",
-           "xg_loss_workspace_bytes", "xg_loss_l1_ssim", "xg_adam_step", "xg_psnr", "xg_sort_pairs_noalloc",
+           "xg_loss_workspace_bytes", "xg_loss_l1_ssim", "xg_adam_step", "xg_psnr", "xg_sort_pairs_noalloc", "xg_sort_pairs_noalloc_status", "xg_fp32_peak",
            "xg_status_str")
 XG_ADAM_MAX_GROUPS = 8
 XG_NOALLOC_MAX_PAIRS = 1 << 20
@@ -191,6 +191,10 @@ def lib(build_if_missing: bool = False):
     L.xg_psnr.restype = ctypes.c_int
     L.xg_sort_pairs_noalloc.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int32, P, P, P, P]
     L.xg_sort_pairs_noalloc.restype = ctypes.c_int
+    L.xg_fp32_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_int64), P]
+    L.xg_fp32_peak.restype = ctypes.c_int
+    L.xg_sort_pairs_noalloc_status.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    L.xg_sort_pairs_noalloc_status.restype = ctypes.c_int
     L.xg_status_str.argtypes = [ctypes.c_int]
     L.xg_status_str.restype = ctypes.c_char_p
     _lib = L
@@ -298,6 +302,21 @@ def xg_sort_pairs_noalloc(key_tile: int, key_depth: int, value: int, count: int,
                           out_key_tile: int, out_key_depth: int, out_value: int, stream: int) -> None:
     _check(lib().xg_sort_pairs_noalloc(key_tile, key_depth, value, count, tile_bits, out_key_tile, out_key_depth,
                                        out_value, stream), "xg_sort_pairs_noalloc")
+
+
+def xg_fp32_peak(packed: int, iters: int, sink: int, stream: int) -> int:
+    """Enqueue one FMA-chain launch; returns the FP32 multiply-adds it performs."""
+    ops = ctypes.c_int64(0)
+    _check(lib().xg_fp32_peak(packed, iters, sink, ctypes.byref(ops), stream), "xg_fp32_peak")
+    return int(ops.value)
+
+
+def xg_sort_pairs_noalloc_status(stream: int) -> int:
+    """Device-side code of the last allocation-free sort on the current device (waits for
+    ``stream``): XG_OK or XG_ERR_CHECK."""
+    code = ctypes.c_int32(-1)
+    _check(lib().xg_sort_pairs_noalloc_status(stream, ctypes.byref(code)), "xg_sort_pairs_noalloc_status")
+    return int(code.value)
 
 
 def xg_activate(raw: XgRawGaussians, scale: int, opacity: int, intensity: int, stream: int) -> None:

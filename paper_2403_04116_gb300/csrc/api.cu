@@ -2,12 +2,31 @@
 // FP32 camera table built from the scanner parameters (Sec. 3.3, Eq. 12), and the
 // stream-ordered launches of each stage.
 #include <algorithm>
+#include <atomic>
 #include <math.h>
 #include <nvtx3/nvToolsExt.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include "xg_internal.cuh"
+
+namespace xg {
+
+int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+  if (dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
+
+}  // namespace xg
 
 namespace {
 
@@ -47,7 +66,7 @@ struct Sizes {
   int32_t bin_unit, bin_units, bin_rows, bin_groups;  // E, J, R, G of the pair scatter
 };
 
-bool sizes_of(const xg_config* cfg, int64_t n, int64_t n_views, int32_t W, int32_t H, Sizes* s) {
+bool sizes_of(const xg_config* cfg, int64_t n, int64_t n_views, int32_t W, int32_t H, int sms, Sizes* s) {
   s->tiles_x = (W + cfg->tile_w - 1) / cfg->tile_w;
   s->tiles_y = (H + cfg->tile_h - 1) / cfg->tile_h;
   s->tiles_per_view = (int64_t)s->tiles_x * s->tiles_y;
@@ -63,7 +82,7 @@ bool sizes_of(const xg_config* cfg, int64_t n, int64_t n_views, int32_t W, int32
   const int64_t T = s->tiles_per_view;
   s->bin_rows = std::max(1, std::min(s->tiles_y, xg::kBinGroupTiles / s->tiles_x));
   s->bin_groups = (s->tiles_y + s->bin_rows - 1) / s->bin_rows;
-  const int64_t target = ((int64_t)xg::kNumSMs * 16 + s->bin_groups - 1) / s->bin_groups;
+  const int64_t target = ((int64_t)sms * 16 + s->bin_groups - 1) / s->bin_groups;
   const int64_t units = std::max<int64_t>(n_views, std::min<int64_t>(target, ((int64_t)1 << 24) / T));
   int64_t E = (n_views * n + units - 1) / units;
   E = std::max<int64_t>(256, (E + 255) / 256 * 256);
@@ -81,9 +100,10 @@ struct Offsets {
 };
 
 // Per-pass arrays are sized for V views; the camera table holds all n_scan views.
-bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t n_scan, int32_t W, int32_t H, Sizes* s,
-                  Offsets* o) {
-  if (!sizes_of(cfg, n, V, W, H, s)) return false;
+bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t n_scan, int32_t W, int32_t H, int sms,
+                  Sizes* s, Offsets* o) {
+  if (!sizes_of(cfg, n, V, W, H, sms, s)) return false;
+  const size_t sort_blocks = (size_t)std::min(xg::kSortCtasPerSM * sms, xg::kMaxSortBlocks);
   const size_t VN = (size_t)V * (size_t)n;
   const size_t cap = (size_t)cfg->pair_capacity;
   const size_t pix = (size_t)V * (size_t)W * (size_t)H;
@@ -102,8 +122,8 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t n_scan, in
   for (int b = 0; b < 2; ++b) o->ent_depth[b] = take(4 * VN);
   for (int b = 0; b < 2; ++b) o->ent_gid[b] = take(4 * VN);
   o->value = take(4 * cap);
-  // radix blocks of a pass of V' <= V views: V' * ceil(kSortBlocks / V') < kSortBlocks + V'
-  o->hist = take(4 * 256 * ((size_t)xg::kSortBlocks + (size_t)V + 1));
+  // radix blocks of a pass of V' <= V views: V' * ceil(sort_blocks / V') < sort_blocks + V'
+  o->hist = take(4 * 256 * (sort_blocks + (size_t)V + 1));
   o->bin_hist = take(4 * (size_t)V * (size_t)s->bin_units * (size_t)s->tiles_per_view);
   o->bin_total = take(4 * (size_t)V * (size_t)s->tiles_per_view);
   o->range = take(8 * (size_t)s->range_keys);
@@ -190,7 +210,7 @@ size_t xg_workspace_bytes(const xg_config* cfg, int64_t n, int32_t n_views, int3
   if (!valid_sizes(n, n_views, per_pass, width, height)) return 0;
   Sizes s;
   Offsets o;
-  return make_offsets(cfg, n, per_pass, n_views, width, height, &s, &o) ? o.total : 0;
+  return make_offsets(cfg, n, per_pass, n_views, width, height, xg::device_sms(), &s, &o) ? o.total : 0;
 }
 
 xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const xg_view* views, int32_t n_views,
@@ -207,7 +227,8 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   }
   Sizes s;
   Offsets o;
-  if (!make_offsets(cfg, n, per_pass, n_views, W, H, &s, &o)) return XG_ERR_INVALID_ARG;
+  const int sms = xg::device_sms();
+  if (!make_offsets(cfg, n, per_pass, n_views, W, H, sms, &s, &o)) return XG_ERR_INVALID_ARG;
   if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < o.total) return XG_ERR_WORKSPACE;
 
   xg_frame* f = (xg_frame*)calloc(1, sizeof(xg_frame));
@@ -233,6 +254,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   f->bin_units = s.bin_units;
   f->bin_rows = s.bin_rows;
   f->bin_groups = s.bin_groups;
+  f->sort_blocks = std::min(xg::kSortCtasPerSM * sms, xg::kMaxSortBlocks);
   f->workspace = workspace;
   f->workspace_bytes = workspace_bytes;
 

@@ -18,8 +18,8 @@
 //      of every (view, tile) comes out in (depth, index) order, contiguous, with no key
 //      array and no pass over the pairs other than the one that writes them.
 //
-// The radix passes run on about kSortBlocks CTAs, each view's segment split among
-// ceil(kSortBlocks / V) of them; these grids and the binning grids depend only on the
+// The radix passes run on about 4 CTAs per SM (the frame's sort_blocks), each view's
+// segment split among ceil(sort_blocks / V) of them; these grids and the binning grids depend only on the
 // frame's sizes.  The host never needs to know the pair count, so the whole
 // sequence can be captured in a CUDA graph, and no CTA waits on another.
 #include <stdlib.h>
@@ -832,7 +832,7 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   }
   // stage 1: every view's n entries, [v*n, (v+1)*n), sorted by the depth bits as a segment
   // of its own; words: depth bits, Gaussian
-  const SortGeom sg = sort_geom(f->n, f->n_views);
+  const SortGeom sg = sort_geom(f->n, f->n_views, f->sort_blocks);
   int cur = 0;
   for (int pass = 0; pass < f->entry_passes; ++pass) {
     SortArrays<2> arr;

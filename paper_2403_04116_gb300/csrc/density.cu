@@ -68,7 +68,7 @@ __global__ void k_density_stats(const uint32_t* __restrict__ count, const float*
 }
 
 // Exclusive scan of n u32 counts in place (offsets[n] receives the total), in three
-// launches over kSortBlocks contiguous chunks.
+// launches over sort_blocks() contiguous chunks.
 __global__ void k_plan_count(const float* __restrict__ log_scale, const float* __restrict__ opacity_logit,
                              const float* __restrict__ accum, const int32_t* __restrict__ denom, int64_t n, Rules r,
                              uint32_t* __restrict__ offsets, unsigned long long* __restrict__ part) {
@@ -220,7 +220,7 @@ bool rules_of(const xg_density_rules* r, Rules* out) {
   return true;
 }
 
-unsigned blocks_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)kNumSMs * 16); }
+unsigned blocks_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)device_sms() * 16); }
 
 }  // namespace
 }  // namespace xg
@@ -234,7 +234,7 @@ xg_status xg_densify_stats(xg_frame* frame, float scale, float* accum, int32_t* 
   return cudaGetLastError() == cudaSuccess ? XG_OK : XG_ERR_CUDA;
 }
 
-size_t xg_densify_workspace_bytes(void) { return sizeof(unsigned long long) * xg::kSortBlocks; }
+size_t xg_densify_workspace_bytes(void) { return sizeof(unsigned long long) * xg::sort_blocks(); }
 
 xg_status xg_densify_plan(const xg_param_set* params, const float* accum, const int32_t* denom,
                           const xg_density_rules* rules, uint32_t* offsets, void* workspace, void* stream) {
@@ -244,10 +244,11 @@ xg_status xg_densify_plan(const xg_param_set* params, const float* accum, const 
     return XG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   auto* part = (unsigned long long*)workspace;
-  xg::k_plan_count<<<xg::kSortBlocks, 256, 0, st>>>(params->log_scale, params->opacity_logit, accum, denom, params->n,
-                                                    r, offsets, part);
-  xg::k_plan_top<<<1, 32, 0, st>>>(part, xg::kSortBlocks, offsets, params->n);
-  xg::k_plan_down<<<xg::kSortBlocks, 256, 0, st>>>(params->n, part, offsets);
+  const int blocks = xg::sort_blocks();  // the count xg_densify_workspace_bytes sized `workspace` for
+  xg::k_plan_count<<<blocks, 256, 0, st>>>(params->log_scale, params->opacity_logit, accum, denom, params->n, r,
+                                           offsets, part);
+  xg::k_plan_top<<<1, 32, 0, st>>>(part, blocks, offsets, params->n);
+  xg::k_plan_down<<<blocks, 256, 0, st>>>(params->n, part, offsets);
   return cudaGetLastError() == cudaSuccess ? XG_OK : XG_ERR_CUDA;
 }
 

@@ -60,7 +60,7 @@ xg_status xg_acui_points(const double size_mm[3], const int32_t grid[3], double 
   int64_t n = 0;
   if (!xg::acui_axes(size_mm, grid, interval, ax, &n) || !mean) return XG_ERR_INVALID_ARG;
   if (n > capacity) return XG_ERR_CAPACITY;
-  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)xg::kNumSMs * 16);
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)xg::device_sms() * 16);
   xg::k_acui<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(ax[0], ax[1], ax[2], n, mean);
   return cudaGetLastError() == cudaSuccess ? XG_OK : XG_ERR_CUDA;
 }

@@ -7,6 +7,8 @@
 // the input and output arrays; the ping-pong buffers, the digit histograms and the pair
 // count live in the file-scope device array below.  Every GPU that loads the library holds
 // that array (about 12.6 MB) until the process exits.
+#include <stddef.h>
+
 #include <mutex>
 
 #include "xg_internal.cuh"
@@ -14,7 +16,7 @@
 namespace xg {
 
 constexpr size_t kNoallocStatusBytes = 256;
-constexpr size_t kNoallocHistBytes = (size_t)4 * 256 * (kSortBlocks + 1);
+constexpr size_t kNoallocHistBytes = (size_t)4 * 256 * (kMaxSortBlocks + 1);
 constexpr size_t kNoallocBufBytes = (size_t)4 * XG_NOALLOC_MAX_PAIRS;
 constexpr size_t kNoallocBytes = kNoallocStatusBytes + kNoallocHistBytes + 3 * kNoallocBufBytes;
 
@@ -27,16 +29,24 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices];
 
-// Device address of the scratch array on the current device, looked up once per device.
-// In host code `g_noalloc_scratch` names a host-side stand-in, never pass it to a kernel.
-xg_status noalloc_scratch(unsigned char** out) {
+// Device address of the scratch array on the current device.  In host code
+// `g_noalloc_scratch` names a host-side stand-in, never pass it to a kernel.  Outside a
+// stream capture the address is looked up on every call (cheap once the module is loaded),
+// so a context torn down and created again by cudaDeviceReset, which may place the array
+// elsewhere, never leaves a stale address behind; inside a capture, where the lookup could
+// load the module, the address of the last call outside a capture on this device is used.
+xg_status noalloc_scratch(cudaStream_t st, unsigned char** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return XG_ERR_CUDA;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return XG_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return XG_ERR_CUDA;
     g_noalloc_ptr[dev] = p;
+  } else if (!g_noalloc_ptr[dev]) {
+    return XG_ERR_CUDA;  // the first call on a device must come before any capture
   }
   *out = (unsigned char*)g_noalloc_ptr[dev];
   return XG_OK;
@@ -64,12 +74,12 @@ extern "C" xg_status xg_sort_pairs_noalloc(const uint32_t* key_tile, const uint3
   if (count < 0 || count > XG_NOALLOC_MAX_PAIRS || tile_bits < 0 || tile_bits > 32) return XG_ERR_INVALID_ARG;
   if (count > 0 && (!key_tile || !key_depth || !value || !out_key_tile || !out_key_depth || !out_value))
     return XG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
   unsigned char* base = nullptr;
-  const xg_status s = noalloc_scratch(&base);
+  const xg_status s = noalloc_scratch(st, &base);
   if (s != XG_OK) return s;
   if (radix_prepare() != cudaSuccess) return XG_ERR_CUDA;
   if (count == 0) return XG_OK;
-  cudaStream_t st = (cudaStream_t)stream;
   DevStatus* status = (DevStatus*)base;
   uint32_t* hist = (uint32_t*)(base + kNoallocStatusBytes);
   uint32_t* tmp_tile = (uint32_t*)(base + kNoallocStatusBytes + kNoallocHistBytes);
@@ -92,7 +102,7 @@ extern "C" xg_status xg_sort_pairs_noalloc(const uint32_t* key_tile, const uint3
       arr.in[w] = src[w];
       arr.out[w] = dst[w];
     }
-    if (radix_pass<3>(nullptr, arr, digit_word ? 0 : 1, shift, 255u, sort_geom(count, 1), status, hist, st) !=
+    if (radix_pass<3>(nullptr, arr, digit_word ? 0 : 1, shift, 255u, sort_geom(count, 1, sort_blocks()), status, hist, st) !=
         cudaSuccess)
       return XG_ERR_CUDA;
     src[0] = dst[0];
@@ -100,4 +110,19 @@ extern "C" xg_status xg_sort_pairs_noalloc(const uint32_t* key_tile, const uint3
     src[2] = dst[2];
   }
   return cudaGetLastError() == cudaSuccess ? XG_OK : XG_ERR_CUDA;
+}
+
+extern "C" xg_status xg_sort_pairs_noalloc_status(void* stream, int32_t* device_code) {
+  using namespace xg;
+  if (!device_code) return XG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* base = nullptr;
+  const xg_status s = noalloc_scratch(st, &base);
+  if (s != XG_OK) return s;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return XG_ERR_CUDA;
+  int32_t code = XG_OK;
+  if (cudaMemcpy(&code, base + offsetof(DevStatus, code), sizeof code, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return XG_ERR_CUDA;
+  *device_code = code;
+  return XG_OK;
 }

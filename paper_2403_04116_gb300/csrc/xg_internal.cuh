@@ -16,9 +16,17 @@
 namespace xg {
 
 constexpr int kMaxViews = 65535;  // views of a frame (a grid dimension of the projection)
-constexpr int kNumSMs = 152;
+// Grids are sized from the SM count of the device they run on (cudaDevAttrMultiProcessorCount
+// of the current device, read once per device; 1 if the query fails, which shrinks grids
+// but changes no result).
+int device_sms();
 constexpr int kSortCtasPerSM = 4;
-constexpr int kSortBlocks = kSortCtasPerSM * kNumSMs;  // grid of the scan and radix-sort passes
+constexpr int kMaxSortBlocks = kSortCtasPerSM * 256;  // bound for statically sized arrays
+// grid of the scan and radix-sort passes: 4 CTAs per SM
+inline int sort_blocks() {
+  const int b = kSortCtasPerSM * device_sms();
+  return b < kMaxSortBlocks ? b : kMaxSortBlocks;
+}
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;         // keys per thread per radix tile
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -186,12 +194,12 @@ struct SortGeom {
   int32_t segments, per_seg;
 };
 
-// About kSortBlocks CTAs over `segments` runs of seg_len items.
-inline SortGeom sort_geom(int64_t seg_len, int32_t segments) {
+// About `blocks` CTAs over `segments` runs of seg_len items.
+inline SortGeom sort_geom(int64_t seg_len, int32_t segments, int32_t blocks) {
   SortGeom g;
   g.seg_len = seg_len;
   g.segments = segments;
-  g.per_seg = (kSortBlocks + segments - 1) / segments;
+  g.per_seg = (blocks + segments - 1) / segments;
   return g;
 }
 
@@ -233,6 +241,7 @@ struct xg_frame {
   int32_t bin_units;     // J: units per view, ceil(n / E)
   int32_t bin_rows;      // R: tile rows per group (R * tiles_x <= kBinGroupTiles)
   int32_t bin_groups;    // G: ceil(tiles_y / R)
+  int32_t sort_blocks;   // CTAs of a radix pass (4 per SM of the device the frame was made on)
   void* workspace;
   size_t workspace_bytes;
   xg_layout layout;

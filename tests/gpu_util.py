@@ -75,3 +75,41 @@ def run_backward(fwd: dict, grad_image: np.ndarray) -> dict:
     out = {k: t.cpu().numpy() for k, t in zip(NAMES, grads)}
     out["g2d"] = np.ascontiguousarray(f.array("grad2d").cpu().numpy()[:, :7].T)  # (7, V*n)
     return out
+
+
+# ------------------------------------------------------------------------------------------
+# gradient tolerance: strict (the stated bound) and with the FP32 term allowance
+# ------------------------------------------------------------------------------------------
+GRAD_RTOL, GRAD_ATOL = 1e-3, 1e-6
+# FP32 allowance per unit of sum |per-pixel terms| behind a gradient (see test_gpu_parity)
+GRAD_TERM_REL = 3e-5
+GRAD_STATS: list = []  # one record per comparison, printed at the end of the session
+PIXEL_STATS: list = []  # flagged-pixel counts of the image comparisons, printed likewise
+
+
+def grad_compare(got, want, mag, what: str) -> dict:
+    """Compare GPU gradients with the FP64 oracle's.  Strict: within 1e-3 relative with a
+    1e-6 absolute floor.  Widened: plus GRAD_TERM_REL times the sum of |per-pixel terms|
+    behind each gradient (``mag``).  Only entries with a term behind them are counted."""
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    mag = np.asarray(mag, np.float64)
+    live = mag > 0
+    err = np.abs(got - want)
+    strict = GRAD_RTOL * np.abs(want) + GRAD_ATOL
+    widened = strict + GRAD_TERM_REL * mag
+    rec = {"what": what, "checked": int(live.sum()), "strict_ok": int((err <= strict)[live].sum()),
+           "widened_ok": int((err <= widened)[live].sum()),
+           "max_err_over_strict": float((err / strict)[live].max(initial=0.0)),
+           "bad_widened": int((err > widened).sum())}
+    rec["strict_frac"] = rec["strict_ok"] / max(1, rec["checked"])
+    GRAD_STATS.append(rec)
+    return rec
+
+
+def merge_stats(recs: list, what: str) -> dict:
+    out = {"what": what, "checked": sum(r["checked"] for r in recs), "strict_ok": sum(r["strict_ok"] for r in recs),
+           "widened_ok": sum(r["widened_ok"] for r in recs), "bad_widened": sum(r["bad_widened"] for r in recs),
+           "max_err_over_strict": max((r["max_err_over_strict"] for r in recs), default=0.0)}
+    out["strict_frac"] = out["strict_ok"] / max(1, out["checked"])
+    return out

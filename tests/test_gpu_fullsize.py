@@ -9,7 +9,13 @@ oracles can compute:
   and the image bit-exact against the FP32 replica, the tile lists too;
 * 4096 random pixels of every view: within 1e-4 of the FP64 oracle (ambiguous ones 1e-2);
 * the gradients of 40 random Gaussians (480 parameters): within tolerance of the FP64
-  oracle, with the same upstream gradient on both sides.
+  oracle, with the same upstream gradient on both sides;
+* every parameter gradient of every Gaussian under two coherent upstream gradients over
+  all 50 views, and 200 sampled parameters against central differences.
+
+Each gradient check counts how many entries meet 1e-3 relative / 1e-6 absolute on their own
+(the strict bound) and requires a minimum fraction; the rest must lie within the FP32 term
+allowance (GRAD_TERM_REL times the sum of |per-pixel terms| behind the gradient).
 """
 import numpy as np
 import pytest
@@ -19,12 +25,19 @@ torch = pytest.importorskip("torch")
 import oracle  # noqa: E402
 from paper_2403_04116_gb300 import synth  # noqa: E402
 from paper_2403_04116_gb300.batch import GraphedStep, autotune  # noqa: E402
-from tests.gpu_util import NAMES, to_device  # noqa: E402
+from tests.gpu_util import (GRAD_ATOL, GRAD_RTOL, GRAD_TERM_REL, NAMES, PIXEL_STATS, grad_compare,  # noqa: E402
+                            merge_stats, to_device)
 
 pytestmark = pytest.mark.gpu
 
 N, V, W = 50_000, 50, 256
-GRAD_RTOL, GRAD_ATOL, GRAD_TERM_REL = 1e-3, 1e-6, 3e-5
+# Fractions of gradients that must meet 1e-3 relative / 1e-6 absolute without the FP32 term
+# allowance: under a random +-1 upstream gradient (maximal cancellation) and under coherent
+# ones (the summed-L1 sign(I - target) of whole views, and all ones)
+STRICT_FRAC_RANDOM = 0.99
+STRICT_FRAC_COHERENT = 0.999
+# pixels beyond 1e-4 of the FP64 oracle (all of them flagged ambiguous), as a fraction
+OVER_TOL_FRAC_MAX = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -75,7 +88,7 @@ def test_sampled_views_bit_exact_against_replica(workload):
 def test_sampled_pixels_against_fp64_oracle(workload):
     image = workload["step"].image.cpu().numpy()
     gen = np.random.default_rng(3)
-    over = 0
+    over = flagged = 0
     for v, view in enumerate(workload["views"]):
         pix = np.sort(gen.choice(W * W, size=4096, replace=False))
         ref = oracle.render64(workload["g"], view, pixels=pix)
@@ -86,7 +99,12 @@ def test_sampled_pixels_against_fp64_oracle(workload):
         assert err[~amb].max() <= 1e-4, (v, err[~amb].max())
         assert err.max() <= 1e-2
         over += int((err > 1e-4).sum())
-    assert over <= 1e-3 * V * 4096
+        flagged += int(amb.sum())
+    PIXEL_STATS.append({"what": "train50k, 4096 random pixels of each of 50 views", "pixels": V * 4096,
+                        "flagged": flagged, "over_tol": over})
+    # In this dense scene about 6 % of the pixels hold a decision within the oracle's margins;
+    # FP32 and FP64 actually decide differently (a pixel beyond 1e-4) at about 7e-4 of them.
+    assert over <= OVER_TOL_FRAC_MAX * V * 4096
 
 
 def test_sampled_gradients_against_fp64_oracle(workload):
@@ -122,15 +140,18 @@ def test_sampled_gradients_against_fp64_oracle(workload):
     grads = tuple(torch.empty_like(t) for t in workload["dev"])
     f.render_bwd(workload["dev"], torch.from_numpy(G.astype(np.float32)).cuda(), grads)
     torch.cuda.synchronize()
-    checked = 0
+    checked, recs = 0, []
     for t, k in zip(grads, NAMES):
         got = t.cpu().numpy()[..., sample].astype(np.float64)
         want = ora[k][..., sample]
         mag = ora["mag"][k][..., sample]
-        bad = np.abs(got - want) > GRAD_RTOL * np.abs(want) + GRAD_ATOL + GRAD_TERM_REL * mag
-        assert not bad.any(), (k, got[bad][:4], want[bad][:4])
+        rec = grad_compare(got, want, mag, f"train50k sampled Gaussians {k}")
+        assert rec["bad_widened"] == 0, rec
+        recs.append(rec)
         checked += want.size
     assert checked == 40 * 12
+    tot = merge_stats(recs, "train50k 40 sampled Gaussians")
+    assert tot["strict_frac"] >= STRICT_FRAC_COHERENT, tot
     assert np.count_nonzero(np.abs(ora["mean"][:, sample]) > 1e-3) > 60  # gradients well above the floor
 
 
@@ -160,7 +181,7 @@ def test_gradients_against_central_differences_on_200_parameters(workload):
     proj = [oracle.project64(g, views[v]) for v in vids]
     visible = np.nonzero(proj[0][:, 0].astype(bool) & proj[1][:, 0].astype(bool))[0]
     g64 = {k: np.asarray(x, np.float64) for k, x in g.items()}
-    eps, checked, tried = 1e-4, 0, 0
+    eps, checked, tried, strict_ok = 1e-4, 0, 0, 0
     yy, xx = np.mgrid[0:W, 0:W]
     while checked < 200 and tried < 400:
         tried += 1
@@ -189,7 +210,43 @@ def test_gradients_against_central_differences_on_200_parameters(workload):
         fd = (vals[0] - vals[1]) / (2 * eps)
         got = gpu[key][idx]
         mag = ora["mag"][key][idx]
-        assert abs(got - fd) <= GRAD_RTOL * abs(fd) + GRAD_ATOL + GRAD_TERM_REL * mag + 1e-4 * abs(fd), \
-            (key, idx, got, fd, mag)
+        # the central difference itself carries O(eps^2) truncation: 1e-4 |fd| on top
+        strict = GRAD_RTOL * abs(fd) + GRAD_ATOL + 1e-4 * abs(fd)
+        assert abs(got - fd) <= strict + GRAD_TERM_REL * mag, (key, idx, got, fd, mag)
+        strict_ok += int(abs(got - fd) <= strict)
         checked += 1
     assert checked >= 150, (checked, tried)
+    from tests.gpu_util import GRAD_STATS
+    GRAD_STATS.append({"what": "train50k central differences, 200 parameters, random +-1 upstream",
+                       "checked": checked, "strict_ok": strict_ok, "widened_ok": checked,
+                       "strict_frac": strict_ok / checked, "max_err_over_strict": float("nan"), "bad_widened": 0})
+    assert strict_ok >= STRICT_FRAC_RANDOM * checked, (strict_ok, checked)
+
+
+@pytest.mark.parametrize("upstream", ["sign", "ones"])
+def test_coherent_upstream_gradients_meet_the_strict_tolerance(workload, upstream):
+    """Every parameter gradient of every Gaussian for a coherent upstream gradient over all
+    50 views -- the summed-L1 loss's sign(I - target), or all ones (the gradient of the sum
+    of the image) -- against the FP64 oracle: nearly all must meet 1e-3 relative / 1e-6
+    absolute on their own; the rest are held to the FP32 term allowance."""
+    g, views, step = workload["g"], workload["views"], workload["step"]
+    G = np.zeros((V, W, W))
+    ora = None
+    for v, view in enumerate(views):
+        r = oracle.render64(g, view)
+        Gv = np.sign(r["image"] - workload["target"][v]) if upstream == "sign" else np.ones((W, W))
+        Gv[r["ambiguous"] != 0] = 0.0
+        G[v] = Gv
+        ora = oracle.grad64(g, view, Gv, out=ora)
+    f = step.frame
+    grads = tuple(torch.empty_like(t) for t in workload["dev"])
+    f.render_bwd(workload["dev"], torch.from_numpy(G.astype(np.float32)).cuda(), grads)
+    torch.cuda.synchronize()
+    recs = []
+    for t, k in zip(grads, NAMES):
+        rec = grad_compare(t.cpu().numpy(), ora[k], ora["mag"][k], f"train50k all Gaussians, upstream {upstream}, {k}")
+        assert rec["bad_widened"] == 0, rec
+        recs.append(rec)
+    tot = merge_stats(recs, f"train50k all Gaussians, upstream {upstream}")
+    assert tot["checked"] > 500_000
+    assert tot["strict_frac"] >= STRICT_FRAC_COHERENT, tot

@@ -22,14 +22,19 @@ import oracle  # noqa: E402
 from paper_2403_04116_gb300 import binding as B  # noqa: E402
 from paper_2403_04116_gb300 import synth  # noqa: E402
 from paper_2403_04116_gb300.synth import View  # noqa: E402
-from tests.gpu_util import NAMES, run_backward, run_forward, to_device  # noqa: E402
+from tests.gpu_util import (NAMES, PIXEL_STATS, grad_compare, merge_stats, run_backward, run_forward,  # noqa: E402
+                            to_device)
 
 pytestmark = pytest.mark.gpu
 
 PIXEL_TOL = 1e-4
 AMBIGUOUS_TOL = 1e-2
-GRAD_RTOL, GRAD_ATOL = 1e-3, 1e-6
-GRAD_TERM_REL = 3e-5
+# pixels beyond 1e-4 of the FP64 oracle (all of them flagged ambiguous), as a fraction
+OVER_TOL_FRAC_MAX = 1e-3
+# Fraction of the gradients of these small scenes, under a random +-1 upstream gradient (the
+# input that maximises cancellation), that must meet 1e-3 relative / 1e-6 absolute on their
+# own, without the FP32 term allowance
+STRICT_FRAC_MIN = 0.99
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -121,7 +126,7 @@ def test_render_fwd_bit_exact_against_replica(case):
 
 def test_render_fwd_against_fp64_oracle(case):
     gpu = case["gpu"]
-    flagged = 0
+    over, flagged = 0, 0
     for v, view in enumerate(case["views"]):
         ref = oracle.render64(case["g"], view)
         amb = ref["ambiguous"] != 0
@@ -129,15 +134,17 @@ def test_render_fwd_against_fp64_oracle(case):
         assert err[~amb].max(initial=0.0) <= PIXEL_TOL
         assert err.max() <= AMBIGUOUS_TOL
         assert np.array_equal(gpu["ncontrib"][v][~amb], ref["ncontrib"][~amb])
-        flagged += int((err > PIXEL_TOL).sum())
-    assert flagged <= 1e-3 * gpu["image"].size
+        over += int((err > PIXEL_TOL).sum())
+        flagged += int(amb.sum())
+    PIXEL_STATS.append({"what": f"small case {case['name']}", "pixels": gpu["image"].size, "flagged": flagged,
+                        "over_tol": over})
+    assert over <= OVER_TOL_FRAC_MAX * gpu["image"].size
 
 
 def _grad_check(gpu, ora, what, mag):
-    err = np.abs(gpu.astype(np.float64) - ora)
-    bad = err > GRAD_RTOL * np.abs(ora) + GRAD_ATOL + GRAD_TERM_REL * mag
-    assert not bad.any(), (f"{what}: {bad.sum()} of {bad.size} outside tolerance; worst "
-                           f"gpu={gpu[bad][:5]}, oracle={ora[bad][:5]}")
+    rec = grad_compare(gpu, ora, mag, what)
+    assert rec["bad_widened"] == 0, f"{what}: {rec['bad_widened']} of {rec['checked']} outside tolerance"
+    return rec
 
 
 def _upstream(views, g, gen, pixels=None):
@@ -161,15 +168,18 @@ def test_render_bwd_against_fp64_oracle(name):
     ref = None
     n = g["intensity"].shape[0]
     VN = n * len(views)
+    recs2d = []
     for v, view in enumerate(views):
         ref = oracle.grad64(g, view, G[v], out=ref)
         g2 = ref["g2d"]
         gpu2 = gpu["g2d"][:, v * n:(v + 1) * n]
         for k, what in enumerate(("u_x", "u_y", "conic_a", "conic_b", "conic_c", "opacity", "intensity")):
-            _grad_check(gpu2[k], g2[k], f"view {v} d/d{what}", ref["mag2d"][k])
+            recs2d.append(_grad_check(gpu2[k], g2[k], f"{name} view {v} d/d{what}", ref["mag2d"][k]))
     assert gpu["g2d"].shape == (7, VN)
-    for k in NAMES:
-        _grad_check(gpu[k], ref[k], k, ref["mag"][k])
+    recs = [_grad_check(gpu[k], ref[k], f"{name} {k}", ref["mag"][k]) for k in NAMES]
+    for tot in (merge_stats(recs2d, f"{name} 2-D gradients"), merge_stats(recs, f"{name} parameter gradients")):
+        assert tot["checked"] > 1000
+        assert tot["strict_frac"] >= STRICT_FRAC_MIN, tot
 
 
 def test_autograd_function_matches_abi():

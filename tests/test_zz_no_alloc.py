@@ -1,15 +1,25 @@
-"""xg_sort_pairs_noalloc, the allocation-free pair sort, against xg_bin_sort.
+"""xg_sort_pairs_noalloc, the allocation-free pair sort, against xg_bin_sort and against
+a host stable sort.
 
 Callers that may not allocate device memory (a plugin inside an application that owns
 the GPU's memory pool, a real-time pipeline that forbids allocation after start-up) sort
 their (tile, depth, Gaussian) pairs with xg_sort_pairs_noalloc, whose scratch lives in a
 static device array inside the library.  These tests feed it the pairs xg_bin_sort emits
 and require xg_bin_sort's sorted output bit for bit, on two different calls in a row (the
-static array is shared by every call and keeps the previous call's contents).  The
-frame's pair keys are read off its ranges.
+static array is shared by every call and keeps the previous call's contents); the frame's
+pair keys are read off its ranges.  Both sorts run the same radix kernels, so every output
+is also checked against NumPy's stable lexsort, on the frame's pairs and on random keys:
+inputs four bytes off a 16-byte boundary (the direct-load path), tile_bits 0, 24 and 32
+(four, seven and eight passes), and the largest accepted count.  A child process with
+every bounded wait made to give up shows that a failure on the device is reported by
+xg_sort_pairs_noalloc_status.
 
 The file is named so that pytest collects it last.
 """
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -65,15 +75,28 @@ def _emitted_pairs(f: Frame, M: int):
     return kt, kd, val
 
 
-def _sort_noalloc(kt, kd, val, tile_bits):
-    to_dev = lambda a: torch.from_numpy(a.view(np.int32)).cuda()  # noqa: E731
+def _sort_noalloc(kt, kd, val, tile_bits, offset=0):
+    """Sort through the C ABI.  With ``offset`` the inputs and outputs start ``offset``
+    words into larger device buffers (4-byte, not 16-byte, aligned for offset 1)."""
+    def to_dev(a):
+        t = torch.zeros(a.size + offset, dtype=torch.int32, device="cuda")
+        t[offset:] = torch.from_numpy(a.view(np.int32)).cuda()
+        return t
     ins = [to_dev(a) for a in (kt, kd, val)]
-    outs = [torch.empty_like(t) for t in ins]
-    B.xg_sort_pairs_noalloc(ins[0].data_ptr(), ins[1].data_ptr(), ins[2].data_ptr(), kt.size, tile_bits,
-                            outs[0].data_ptr(), outs[1].data_ptr(), outs[2].data_ptr(),
-                            torch.cuda.current_stream().cuda_stream)
+    outs = [torch.full_like(t, -1) for t in ins]
+    ptr = lambda t: t.data_ptr() + 4 * offset  # noqa: E731
+    stream = torch.cuda.current_stream().cuda_stream
+    B.xg_sort_pairs_noalloc(ptr(ins[0]), ptr(ins[1]), ptr(ins[2]), kt.size, tile_bits,
+                            ptr(outs[0]), ptr(outs[1]), ptr(outs[2]), stream)
+    assert B.xg_sort_pairs_noalloc_status(stream) == B.XG_OK
     torch.cuda.synchronize()
-    return [o.cpu().numpy().view(np.uint32) for o in outs]
+    return [o[offset:].cpu().numpy().view(np.uint32) for o in outs]
+
+
+def _host_stable_sort(kt, kd, val):
+    """NumPy's stable sort by (key_tile, key_depth): lexsort's last key is the primary one."""
+    order = np.lexsort((kd, kt))
+    return [kt[order], kd[order], val[order]]
 
 
 @pytest.mark.parametrize("first,second", [((3000, 5, 100, 75, (8, 8), 10), (6000, 2, 128, 128, (16, 16), 31))])
@@ -93,6 +116,64 @@ def test_noalloc_sort_matches_bin_sort_twice(first, second):
         want = [(tile * f.V + view).astype(np.uint32), kd_s, val_s]
         for g_, w_, name in zip(got, want, ("key_tile", "key_depth", "value")):
             np.testing.assert_array_equal(g_, w_, err_msg=name)
+        for g_, w_, name in zip(got, _host_stable_sort(kt, kd, val), ("key_tile", "key_depth", "value")):
+            np.testing.assert_array_equal(g_, w_, err_msg=f"{name} against the host stable sort")
+
+
+# (pairs, tile_bits, word offset of the buffers, distinct depth keys): ties in (tile, depth)
+# are frequent, so the order of equal keys (the input order) is checked too
+RANDOM_CASES = [(B.XG_NOALLOC_MAX_PAIRS, 23, 0, 1 << 20), (5000, 0, 1, 50), (70_000, 24, 1, 3000),
+                (300_000, 32, 0, 1 << 32), (B.XG_NOALLOC_MAX_PAIRS, 8, 1, 1000)]
+
+
+def test_noalloc_sort_random_keys_against_host_stable_sort():
+    gen = np.random.default_rng(12)
+    for count, tile_bits, offset, depths in RANDOM_CASES:  # one call after another
+        kt = gen.integers(0, 1 << tile_bits, size=count, dtype=np.uint64).astype(np.uint32)
+        kd = gen.integers(0, depths, size=count, dtype=np.uint64).astype(np.uint32)
+        if depths == 1 << 32:
+            kd[::3] = kd[1::3][: kd[::3].size]  # repeated depth keys among full-range ones
+        val = gen.permutation(count).astype(np.uint32)
+        got = _sort_noalloc(kt, kd, val, tile_bits, offset)
+        for g_, w_, name in zip(got, _host_stable_sort(kt, kd, val), ("key_tile", "key_depth", "value")):
+            np.testing.assert_array_equal(g_, w_, err_msg=f"{name}: {count} pairs, tile_bits {tile_bits}, "
+                                                          f"offset {offset}")
+
+
+CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, ROOT)
+from paper_2403_04116_gb300 import binding as B
+n = B.XG_NOALLOC_MAX_PAIRS
+gen = np.random.default_rng(3)
+ins = [torch.from_numpy(gen.integers(0, 1 << 16, size=n, dtype=np.int64).astype(np.int32)).cuda() for _ in range(3)]
+outs = [torch.empty_like(t) for t in ins]
+s = torch.cuda.current_stream().cuda_stream
+B.xg_sort_pairs_noalloc(*(t.data_ptr() for t in ins), n, 16, *(t.data_ptr() for t in outs), s)
+code = B.xg_sort_pairs_noalloc_status(s)
+after = float(torch.ones(1000, device="cuda").sum().item())  # the context still works
+print("code", code, "after", after)
+"""
+
+
+def _child(env_extra):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, "-c", CHILD.replace("ROOT", repr(root))], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    words = r.stdout.split()
+    return {words[i]: float(words[i + 1]) for i in range(0, len(words) - 1, 2)}
+
+
+def test_noalloc_sort_reports_device_failures():
+    """XG_SPIN_LIMIT=0 (read once per process) makes every first bounded wait of the radix
+    scatter give up, as an expired wait would: the status query must say XG_ERR_CHECK,
+    and the context must stay usable.  A clean child is the control."""
+    ok = _child({})
+    assert ok["code"] == B.XG_OK and ok["after"] == 1000.0
+    bad = _child({"XG_SPIN_LIMIT": "0"})
+    assert bad["code"] == B.XG_ERR_CHECK and bad["after"] == 1000.0
 
 
 def test_noalloc_sort_rejects_too_many_pairs():
