@@ -284,7 +284,17 @@ static int64_t blend(const xo_pg* pg, const xo_cand* cand, int64_t m, double* C_
     prev_tz = c->tz;
     double Tn = T * (1.0 - c->alpha);
     if (fabs(Tn / XO_T_MIN - 1.0) < XO_MARGIN_T) flags |= 2;
-    if (Tn < XO_T_MIN) break;
+    if (Tn < XO_T_MIN) {
+      /* The candidates after the one that stops the blend are left out, but one within
+       * rounding of its depth may come before it in a float32 depth order (and be blended
+       * in its place): that order is ambiguous too. */
+      for (int64_t q = k + 1; q < m; ++q) {
+        if (!cand[q].pass && !cand[q].near_thr) continue;
+        if (fabs(cand[q].tz - c->tz) <= XO_MARGIN_DEPTH * cand[q].tz) flags |= 4;
+        break;
+      }
+      break;
+    }
     if (contrib) contrib[n] = k;
     if (Tb) Tb[n] = T;
     C += pg[c->id].i * c->alpha * T;

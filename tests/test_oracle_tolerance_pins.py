@@ -205,3 +205,31 @@ def test_single_pixel_magnitude_by_hand(oracle_lib, seed):
     scale = np.abs(want_mag).max()
     np.testing.assert_allclose(got_mag, want_mag, rtol=1e-5, atol=1e-7 * scale)
     np.testing.assert_allclose(got_grad, want_grad, rtol=1e-5, atol=1e-7 * scale)
+
+
+@pytest.mark.parametrize("rel,flagged", [(1e-8, True), (1e-7, True), (1e-5, False), (1e-2, False)])
+def test_depth_tie_with_the_candidate_after_the_stop(oracle_lib, rel, flagged):
+    """Three Gaussians take T to 1.5e-4, a fourth (opacity 0.5) would take it below 1e-4 and
+    stops the blend; a fifth lies behind the fourth by rel in depth.  Within 2^-22 of the
+    stopper's depth a float32 depth order may put the fifth first (and blend it instead), so
+    the pixel is flagged; farther behind it is not."""
+    x_stop = -10.0
+    x_next = 1000.0 - (1000.0 - x_stop) * (1.0 + rel)
+    g = _scene([20.0, 10.0, x_stop, x_next], [0.995, 0.985, 0.5, 0.2])
+    f = _flags(g)
+    assert bool(f & 4) == flagged, f
+    assert f & ~4 == 0
+    assert int(oracle.render64(g, _view())["ncontrib"].reshape(-1)[CENTRE]) == 2
+
+
+def test_flags_cover_every_decision_the_fp32_replica_takes_differently(oracle_lib):
+    """On a full view of the 50,000-Gaussian training scene (256 x 256), the FP32 replica of
+    the kernels' decision sequence and the FP64 oracle blend the same number of Gaussians at
+    every pixel the oracle does not flag."""
+    g = synth.gaussians(50_000, synth.scene_side_mm(256), synth.rng(1, 0))
+    view = synth.circular_views(50, 256, 256)[0]
+    rep = oracle.replica_full(g, view, (16, 16))
+    ref = oracle.render64(g, view)
+    amb = ref["ambiguous"] != 0
+    assert 0 < amb.mean() < 0.2
+    np.testing.assert_array_equal(rep["ncontrib"].astype(np.int64)[~amb], ref["ncontrib"][~amb])
