@@ -94,6 +94,7 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the one-view-per-launch form")
+    ap.add_argument("--persistent", type=int, default=0, help="with --config: 1 for the persistent launch form")
     ap.add_argument("--config", default=None, help="tile and kernel shape TWxTH:batch:pixels_per_thread "
                                                     "(e.g. 16x16:128:2; scan workloads add :views_per_pass) "
                                                     "instead of autotuning")
@@ -442,14 +443,17 @@ def run_ours(args) -> None:
         tw_th, b_s, p_s = args.config.split(":")
         tw_s, th_s = tw_th.split("x")
         from paper_2403_04116_gb300.batch import TuneResult
-        c0 = FrameConfig(int(tw_s), int(th_s), batch=int(b_s), pixels_per_thread=int(p_s))
-        tuned = TuneResult(c0.tile_w, c0.tile_h, c0.batch, c0.pixels_per_thread, 0.0, size_pairs(n, views, c0, dev))
+        c0 = FrameConfig(int(tw_s), int(th_s), batch=int(b_s), pixels_per_thread=int(p_s),
+                         persistent=int(args.persistent))
+        tuned = TuneResult(c0.tile_w, c0.tile_h, c0.batch, c0.pixels_per_thread, 0.0, size_pairs(n, views, c0, dev),
+                           c0.persistent)
     else:
         tuned = autotune(n, views, dev, target) if args.autotune else None
     tile = (tuned.tile_w, tuned.tile_h) if tuned else tuple(w["tile"])
-    batch = tuned.batch if tuned else 256
+    batch = tuned.batch if tuned else 64
     ppt = tuned.pixels_per_thread if tuned else 2
-    cfg = FrameConfig(tile[0], tile[1], batch=batch, pixels_per_thread=ppt)
+    persistent = tuned.persistent if tuned else 0
+    cfg = FrameConfig(tile[0], tile[1], batch=batch, pixels_per_thread=ppt, persistent=persistent)
     cap = tuned.pair_capacity if tuned else size_pairs(n, views, cfg, dev)
 
     step = GraphedStep(n, views, cfg, cap)
@@ -515,9 +519,23 @@ def run_ours(args) -> None:
         ms_plain = timed(lambda: plain.run(dev, target, pgrads), plain_steps)
         del plain
 
+    # the other launch form of the compositing kernels, graphed the same way (same images)
+    other_cfg = FrameConfig(tile[0], tile[1], batch=batch, pixels_per_thread=ppt, persistent=1 - persistent)
+    ms_other = float("nan")
+    try:
+        other = GraphedStep(n, views, other_cfg, cap)
+        other.load(dev, target)
+        other.capture()
+        for _ in range(args.warmup):
+            other.replay()
+        ms_other = timed(other.replay, args.steps)
+        del other
+    except ValueError:
+        pass
+
     # max over ranks
-    ms_total, ms_fwd, ms_plain, ms_stream_step = reduce_max([ms_total, ms_fwd, ms_plain, ms_stream / timing_steps],
-                                                            device="cuda")
+    ms_total, ms_fwd, ms_plain, ms_stream_step, ms_other = reduce_max(
+        [ms_total, ms_fwd, ms_plain, ms_stream / timing_steps, ms_other], device="cuda")
     ms_step = ms_total / args.steps
     value = throughput(V, args.steps, world, ms_total)
 
@@ -622,8 +640,10 @@ def run_ours(args) -> None:
     if rank == 0:
         cfg_line = _config(args.workload, w, world)
         cfg_line.update({"tile": list(tile), "staging_batch": batch, "pixels_per_thread": ppt,
+                         "launch": "persistent blocks, warps taking work items from a counter" if persistent
+                         else "one block per (view, tile)",
                          "graph": "whole step, one CUDA graph",
-                         "autotuned": bool(tuned)})
+                         "autotuned": bool(tuned and not args.config)})
         line = {"metric": metric_train(w), "value": value, "unit": "projections/s", "n_gpus": world,
                 "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -633,6 +653,10 @@ def run_ours(args) -> None:
                 "plain_one_view_per_launch": None if args.no_plain else {
                     "value": throughput(V, plain_steps, world, ms_plain), "unit": "projections/s",
                     "ms_per_step": ms_plain / plain_steps},
+                "other_launch_form": None if math.isnan(ms_other) else {
+                    "launch": "persistent" if not persistent else "one block per (view, tile)",
+                    "value": throughput(V, args.steps, world, ms_other), "unit": "projections/s",
+                    "ms_per_step": ms_other / args.steps},
                 "stream_launched": {"ms_per_step": ms_stream_step},
                 "clocks": clock_info, "e2e": e2e, "e2e_autograd": e2e_autograd, "gpu_launches": gpu_launches,
                 "roofline": roof, "accuracy": accuracy, "fp32_peak": fp32, "cpu_baseline": cpu,
@@ -712,12 +736,13 @@ def run_scan(args) -> None:
     if args.config:
         parts = args.config.split(":")
         tw_s, th_s = parts[0].split("x")
-        cfg = FrameConfig(int(tw_s), int(th_s), batch=int(parts[1]), pixels_per_thread=int(parts[2]))
+        cfg = FrameConfig(int(tw_s), int(th_s), batch=int(parts[1]), pixels_per_thread=int(parts[2]),
+                          persistent=int(args.persistent))
         vpp = int(parts[3]) if len(parts) > 3 else 16
     elif args.autotune:
         cfg, vpp, _ = autotune_scan(n, views, dev)
     else:
-        cfg, vpp = FrameConfig(16, 16, batch=128, pixels_per_thread=2), 16
+        cfg, vpp = FrameConfig(32, 16, batch=64, pixels_per_thread=2), 12
     scan = build_scan(n, views, cfg, vpp, dev)
     frame = scan.frame
 
@@ -831,7 +856,8 @@ def run_scan(args) -> None:
     if rank == 0:
         cfg_line = _config(args.workload, w, world)
         cfg_line.update({"tile": [cfg.tile_w, cfg.tile_h], "staging_batch": cfg.batch,
-                         "pixels_per_thread": cfg.pixels_per_thread, "views_per_pass": vpp,
+                         "pixels_per_thread": cfg.pixels_per_thread, "persistent": cfg.persistent,
+                         "views_per_pass": vpp,
                          "passes": len(scan.starts), "graph": "every pass in one CUDA graph",
                          "autotuned": bool(args.autotune and not args.config)})
         line = {"metric": metric_scan(w), "value": value, "unit": "projections/s", "n_gpus": world,

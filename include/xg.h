@@ -92,13 +92,17 @@ typedef struct {
 /* Frame configuration.  tile_w, tile_h in {8, 16, 32}; pixels_per_thread: pixels each
  * compositing thread owns, 1, 2 or 4 (0 selects 2), with tile_h a multiple of
  * 4 * pixels_per_thread and tile_w * tile_h <= 512 * pixels_per_thread; near_mm > 0;
- * batch: Gaussians staged in shared memory per round of the compositing kernels, one of
- * 64, 128, 256 (0 selects 256); 1 <= pair_capacity < 2^31 (pairs of one pass).
- * views_per_pass >= 0: views the per-pass arrays hold; 0, or a value >= the frame's view
- * count, renders every view in one pass.  A smaller value renders a long scan in passes
- * through one workspace (see xg_frame_select_views).  Tile shape, batch, pixels per thread
- * and views per pass change speed and memory only: images and gradients do not depend on
- * them. */
+ * batch: list entries (Gaussians) whose records each warp of the compositing kernels keeps
+ * in flight into shared memory, one of 64, 128, 256, 512 (0 selects 64); the shared memory
+ * this needs must fit one block (XG_ERR_INVALID_ARG otherwise); 1 <= pair_capacity < 2^31
+ * (pairs of one pass).  views_per_pass >= 0: views the per-pass arrays hold; 0, or a value
+ * >= the frame's view count, renders every view in one pass.  A smaller value renders a
+ * long scan in passes through one workspace (see xg_frame_select_views).  persistent: 0
+ * launches the compositing kernels with one block per (view, tile); 1 launches as many
+ * blocks as fit on the device at once, whose warps take (view, tile, pixel block) work
+ * items from a counter in the workspace, longest tile lists first.  Tile shape, batch,
+ * pixels per thread, views per pass and the launch form change speed and memory only:
+ * images and gradients do not depend on them. */
 typedef struct {
   int32_t tile_w;
   int32_t tile_h;
@@ -107,6 +111,8 @@ typedef struct {
   int64_t pair_capacity;
   int32_t pixels_per_thread;
   int32_t views_per_pass;
+  int32_t persistent;
+  int32_t reserved;  /* 0 */
 } xg_config;
 
 /* Device-side status of a frame, read back by xg_frame_read_status. */

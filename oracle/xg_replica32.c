@@ -98,7 +98,9 @@ static int all_finite(const float* v, int k) {
 
 /*
  * Projection of every Gaussian under one view.
- *   rec[8n]: (u_x, u_y, conic a, b, c, opacity, intensity, 0), u centred on the principal point
+ *   rec[8n]: (u_x, u_y, conic a, b, c, opacity, intensity, -ln(255 opacity) - 1e-4), u centred on
+ *   the principal point; the last field is the exponent below which sigma stays under 1/255
+ *   with a margin (a skip test that never changes a decision)
  *   depth[n]: t_z;  rect[4n]: tile rectangle (x0, y0, x1, y1), inclusive;  count[n]: tiles touched
  * Everything is zero where count is zero.  Returns the number of Gaussians with a
  * non-finite attribute.
@@ -212,6 +214,7 @@ int64_t xr_project(int64_t n, const float* mean, const float* scale, const float
     rg[4] = cc;
     rg[5] = o;
     rg[6] = in;
+    rg[7] = -lg - 1e-4f; /* exponent below which sigma < 1/255 for sure (the kernels' skip test) */
     depth[g] = tz;
     rect[4 * g + 0] = tx0;
     rect[4 * g + 1] = ty0;

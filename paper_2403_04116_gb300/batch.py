@@ -24,7 +24,7 @@ from .render import Frame, FrameConfig, loss_l1_into
 
 _NAMES = ("mean", "scale", "quat", "opacity", "intensity")
 CANDIDATE_TILES = ((8, 8), (16, 16), (32, 16), (16, 8), (16, 32))
-CANDIDATE_BATCHES = (64, 128, 256)
+CANDIDATE_BATCHES = (64, 128, 256, 512)
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
@@ -260,9 +260,11 @@ class TuneResult:
     pixels_per_thread: int
     ms: float
     pair_capacity: int
+    persistent: int = 0
 
     def config(self) -> FrameConfig:
-        return FrameConfig(self.tile_w, self.tile_h, batch=self.batch, pixels_per_thread=self.pixels_per_thread)
+        return FrameConfig(self.tile_w, self.tile_h, batch=self.batch, pixels_per_thread=self.pixels_per_thread,
+                           persistent=self.persistent)
 
 
 def build_scan(n: int, views, cfg: FrameConfig, views_per_pass: int, gaussians: tuple,
@@ -283,7 +285,7 @@ def build_scan(n: int, views, cfg: FrameConfig, views_per_pass: int, gaussians: 
 
 
 def autotune_scan(n: int, views, gaussians: tuple, tiles=((16, 16), (32, 16)), passes=(8, 12, 16, 30),
-                  shapes=((128, 2), (256, 2), (256, 1)), reps: int = 3) -> tuple:
+                  shapes=((64, 2), (128, 2), (64, 1)), reps: int = 3) -> tuple:
     """Tile shape and views per pass, then staging batch and pixels per thread, with the
     fastest replay of the captured scan; returns (FrameConfig, views_per_pass, ms)."""
     def time_scan(cfg, vpp):
@@ -317,9 +319,20 @@ def autotune_scan(n: int, views, gaussians: tuple, tiles=((16, 16), (32, 16)), p
         if cfg0.tile_h % (4 * p):
             continue
         cfg = FrameConfig(cfg0.tile_w, cfg0.tile_h, batch=b, pixels_per_thread=p)
+        try:
+            ms = time_scan(cfg, vpp)
+        except (ValueError, B.XgError):
+            continue
+        if ms < best[2]:
+            best = (cfg, vpp, ms)
+    c = best[0]
+    cfg = FrameConfig(c.tile_w, c.tile_h, batch=c.batch, pixels_per_thread=c.pixels_per_thread, persistent=1)
+    try:
         ms = time_scan(cfg, vpp)
         if ms < best[2]:
             best = (cfg, vpp, ms)
+    except (ValueError, B.XgError):
+        pass
     return best
 
 
@@ -329,13 +342,34 @@ def _key(n: int, views) -> str:
     return f"n<={bucket}|V={len(views)}|{v0.width}x{v0.height}"
 
 
+def time_step(n: int, views, cfg: FrameConfig, cap: int, gaussians: tuple, target: torch.Tensor,
+              reps: int = 5) -> float:
+    """Median ms of the graphed fwd+bwd step in this configuration (ValueError if the
+    configuration is invalid, e.g. its compositing block needs too much shared memory)."""
+    step = GraphedStep(n, views, cfg, cap)
+    step.load(gaussians, target)
+    step.capture()
+    times = []
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        step.replay()
+        e.record()
+        torch.cuda.synchronize()
+        times.append(s.elapsed_time(e))
+    del step
+    return statistics.median(times)
+
+
 def autotune(n: int, views, gaussians: tuple, target: torch.Tensor, tiles=CANDIDATE_TILES,
              batches=CANDIDATE_BATCHES, ppts=(1, 2, 4), reps: int = 5, use_cache: bool = True) -> TuneResult:
-    """Pick the tile shape, staging batch and pixels per thread with the fastest graphed step
-    (cached on disk).
+    """Pick the tile shape, pixels per thread, staging batch and launch form (one block per
+    tile or persistent blocks) with the fastest graphed step (cached on disk): first tile
+    shape and pixels per thread at the smallest batch, then batch and launch form for the
+    best of those.
 
-    Every candidate computes the same image (tiles and batch are pure acceleration), so the
-    choice never changes results."""
+    Every candidate computes the same image (tiles, batch and launch form are pure
+    acceleration), so the choice never changes results."""
     key = _key(n, views)
     cache = {}
     if use_cache and os.path.exists(_CACHE):
@@ -349,24 +383,29 @@ def autotune(n: int, views, gaussians: tuple, target: torch.Tensor, tiles=CANDID
             except TypeError:
                 pass
     best = None
+    caps = {}
     for tw, th in tiles:
-        cap = size_pairs(n, views, FrameConfig(tw, th), gaussians)
-        for b, ppt in [(b, p) for b in batches for p in ppts if th % (4 * p) == 0]:
-            step = GraphedStep(n, views, FrameConfig(tw, th, batch=b, pixels_per_thread=ppt), cap)
-            step.load(gaussians, target)
-            step.capture()
-            times = []
-            for _ in range(reps):
-                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                s.record()
-                step.replay()
-                e.record()
-                torch.cuda.synchronize()
-                times.append(s.elapsed_time(e))
-            ms = statistics.median(times)
+        caps[(tw, th)] = size_pairs(n, views, FrameConfig(tw, th), gaussians)
+        for ppt in [p for p in ppts if th % (4 * p) == 0]:
+            try:
+                ms = time_step(n, views, FrameConfig(tw, th, batch=batches[0], pixels_per_thread=ppt),
+                               caps[(tw, th)], gaussians, target, reps)
+            except ValueError:
+                continue
             if best is None or ms < best.ms:
-                best = TuneResult(tw, th, b, ppt, ms, cap)
-            del step
+                best = TuneResult(tw, th, batches[0], ppt, ms, caps[(tw, th)])
+    b0 = best
+    for b in batches:
+        for pers in (0, 1):
+            if b == b0.batch and pers == 0:
+                continue
+            cfg = FrameConfig(b0.tile_w, b0.tile_h, batch=b, pixels_per_thread=b0.pixels_per_thread, persistent=pers)
+            try:
+                ms = time_step(n, views, cfg, b0.pair_capacity, gaussians, target, reps)
+            except ValueError:
+                continue
+            if ms < best.ms:
+                best = TuneResult(b0.tile_w, b0.tile_h, b, b0.pixels_per_thread, ms, b0.pair_capacity, pers)
     cache[key] = asdict(best)
     if use_cache:
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)

@@ -48,7 +48,7 @@ class XgGrads(ctypes.Structure):
 class XgConfig(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("near_mm", ctypes.c_float),
                 ("batch", ctypes.c_int32), ("pair_capacity", ctypes.c_int64), ("pixels_per_thread", ctypes.c_int32),
-                ("views_per_pass", ctypes.c_int32)]
+                ("views_per_pass", ctypes.c_int32), ("persistent", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class XgDeviceStatus(ctypes.Structure):

@@ -31,18 +31,20 @@ int device_sms() {
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr size_t kMaxBlockSmem = 227 * 1024;  // dynamic shared memory one block may use
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 bool valid_tile(int t) { return t == 8 || t == 16 || t == 32; }
 
-bool valid_batch(int b) { return b == 0 || b == 64 || b == 128 || b == 256; }
+bool valid_batch(int b) { return b == 0 || b == 64 || b == 128 || b == 256 || b == 512; }
 
 bool valid_config(const xg_config* cfg) {
   if (!cfg) return false;
   const int ppt = cfg->pixels_per_thread == 0 ? 2 : cfg->pixels_per_thread;
   return (ppt == 1 || ppt == 2 || ppt == 4) && valid_tile(cfg->tile_w) && valid_tile(cfg->tile_h) &&
          cfg->tile_h % (4 * ppt) == 0 && cfg->tile_w * cfg->tile_h <= 512 * ppt && valid_batch(cfg->batch) &&
+         (cfg->persistent == 0 || cfg->persistent == 1) && xg::render_smem_bytes(cfg) <= kMaxBlockSmem &&
          isfinite(cfg->near_mm) && cfg->near_mm > 0.f && cfg->pair_capacity >= 1 &&
          cfg->pair_capacity < ((int64_t)1 << 31) && cfg->views_per_pass >= 0;
 }
@@ -234,7 +236,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   xg_frame* f = (xg_frame*)calloc(1, sizeof(xg_frame));
   if (!f) return XG_ERR_INVALID_ARG;
   f->cfg = *cfg;
-  if (f->cfg.batch == 0) f->cfg.batch = 256;
+  if (f->cfg.batch == 0) f->cfg.batch = 64;
   if (f->cfg.pixels_per_thread == 0) f->cfg.pixels_per_thread = 2;
   f->cfg.views_per_pass = per_pass;
   f->n = n;
@@ -301,6 +303,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
 
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = xg::radix_prepare();  // kernel attributes, set outside any stream capture
+  if (e == cudaSuccess) e = xg::render_prepare(f);
   if (e == cudaSuccess) e = upload_cameras(f, views, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.status, 0, sizeof(xg::DevStatus), st);
   if (e == cudaSuccess) {  // the work order before any binning: every (view, tile) once

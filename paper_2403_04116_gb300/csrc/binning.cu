@@ -163,7 +163,9 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // asynchronous copy brings tile j+1 into the other, so every CTA keeps a tile of loads in
 // flight through its whole chunk.  Full tiles of 16-byte aligned arrays take that path;
 // the rest (a chunk's ragged last tile, unaligned caller arrays) are loaded directly.
-template <int WORDS, int DW>
+// IOTA1: word 1 is not read but generated, the item's index within its segment (the first
+// pass over the entries, whose Gaussian index is that position).
+template <int WORDS, int DW, bool IOTA1>
 __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(SortArrays<WORDS> arr, int shift,
                                                                                 uint32_t mask, uint32_t spin,
                                                                 DevStatus* __restrict__ st, SortGeom geom,
@@ -184,12 +186,13 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
   sort_range(geom, seg, beg, end);
   if (beg >= end) return;
   const int64_t seg_base = (int64_t)seg * geom.seg_len;
-  bool aligned = true;  // every tile of the chunk starts 16-byte aligned in every array
+  constexpr int LOADED = IOTA1 ? 1 : WORDS;  // words read from memory (the first LOADED)
+  bool aligned = true;  // every tile of the chunk starts 16-byte aligned in every array read
 #pragma unroll
-  for (int w = 0; w < WORDS; ++w) aligned &= ((uintptr_t)(arr.in[w] + beg) & 15u) == 0;
+  for (int w = 0; w < LOADED; ++w) aligned &= ((uintptr_t)(arr.in[w] + beg) & 15u) == 0;
 #define BULK_TILE(b) (aligned && end - (b) >= kSortTile)
 #define BUF(j, w) (s_dyn + (((j) & 1) * WORDS + (w)) * kSortTile)
-  constexpr uint32_t kTileBytes = (uint32_t)(WORDS * kSortTile * sizeof(uint32_t));
+  constexpr uint32_t kTileBytes = (uint32_t)(LOADED * kSortTile * sizeof(uint32_t));
   // thread `tid` owns digit `tid`: its next output position for this CTA, counted from the
   // start of the segment (prefix differences taken modulo 2^32 are exact: a segment holds
   // fewer than 2^32 items)
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
     if (BULK_TILE(beg)) {
       mbar_expect_tx(&s_bar, kTileBytes);
 #pragma unroll
-      for (int w = 0; w < WORDS; ++w) bulk_load(BUF(0, w), arr.in[w] + beg, kSortTile * 4u, &s_bar);
+      for (int w = 0; w < LOADED; ++w) bulk_load(BUF(0, w), arr.in[w] + beg, kSortTile * 4u, &s_bar);
     }
   }
   __syncthreads();
@@ -226,20 +229,25 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
 #pragma unroll
       for (int k = 0; k < kSortItems; ++k)
 #pragma unroll
-        for (int w = 0; w < WORDS; ++w) item[k][w] = BUF(j, w)[warp * (32 * kSortItems) + k * 32 + lane];
+        for (int w = 0; w < LOADED; ++w) item[k][w] = BUF(j, w)[warp * (32 * kSortItems) + k * 32 + lane];
     } else {
 #pragma unroll
       for (int k = 0; k < kSortItems; ++k) {
         const int64_t i = base + warp * (32 * kSortItems) + k * 32 + lane;
 #pragma unroll
-        for (int w = 0; w < WORDS; ++w) item[k][w] = i < end ? __ldg(arr.in[w] + i) : 0u;
+        for (int w = 0; w < LOADED; ++w) item[k][w] = i < end ? __ldg(arr.in[w] + i) : 0u;
       }
+    }
+    if constexpr (IOTA1) {
+#pragma unroll
+      for (int k = 0; k < kSortItems; ++k)
+        item[k][1] = (uint32_t)(base + warp * (32 * kSortItems) + k * 32 + lane - seg_base);
     }
     __syncthreads();  // tile j is in registers: its buffer becomes the reorder buffer
     if (tid == 0 && BULK_TILE(base + kSortTile)) {
       mbar_expect_tx(&s_bar, kTileBytes);
 #pragma unroll
-      for (int w = 0; w < WORDS; ++w) bulk_load(BUF(j + 1, w), arr.in[w] + base + kSortTile, kSortTile * 4u, &s_bar);
+      for (int w = 0; w < LOADED; ++w) bulk_load(BUF(j + 1, w), arr.in[w] + base + kSortTile, kSortTile * 4u, &s_bar);
     }
     // rank within the warp: the leader of each digit group adds the group to the warp's
     // count and hands the previous count to the group
@@ -759,12 +767,12 @@ constexpr size_t scatter_smem() {
   return 2 * WORDS * kSortTile * sizeof(uint32_t);
 }
 
-template <int WORDS, int DW>
+template <int WORDS, int DW, bool IOTA1>
 cudaError_t scatter_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<WORDS, DW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)scatter_smem<WORDS>());
+  cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<WORDS, DW, IOTA1>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem<WORDS>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_radix_scatter<WORDS, DW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(k_radix_scatter<WORDS, DW, IOTA1>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   return e;
 }
@@ -781,10 +789,11 @@ cudaError_t radix_prepare() {
     for (const void* k : {(const void*)k_bin_scatter<true>, (const void*)k_bin_scatter<false>})
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_scatter_smem(kBinGroupTiles));
-    if (e == cudaSuccess) e = scatter_attrs<2, 0>();
-    if (e == cudaSuccess) e = scatter_attrs<2, 1>();  // instantiated by radix_pass<2>, unused
-    if (e == cudaSuccess) e = scatter_attrs<3, 0>();
-    if (e == cudaSuccess) e = scatter_attrs<3, 1>();
+    if (e == cudaSuccess) e = scatter_attrs<2, 0, false>();
+    if (e == cudaSuccess) e = scatter_attrs<2, 0, true>();
+    if (e == cudaSuccess) e = scatter_attrs<2, 1, false>();  // instantiated by radix_pass<2>, unused
+    if (e == cudaSuccess) e = scatter_attrs<3, 0, false>();
+    if (e == cudaSuccess) e = scatter_attrs<3, 1, false>();
     return e;
   }();
   return once;
@@ -792,7 +801,7 @@ cudaError_t radix_prepare() {
 
 template <int WORDS>
 cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, uint32_t mask,
-                       const SortGeom& geom, DevStatus* status, uint32_t* hist, cudaStream_t st) {
+                       const SortGeom& geom, DevStatus* status, uint32_t* hist, cudaStream_t st, bool iota1) {
   const cudaError_t prep = radix_prepare();
   if (prep != cudaSuccess) return prep;
   const int blocks = geom.segments * geom.per_seg;
@@ -807,20 +816,23 @@ cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word
   {
     Timed t(f, kRadixScatter, st);
     constexpr size_t smem = scatter_smem<WORDS>();
-    if (digit_word == 0)
-      k_radix_scatter<WORDS, 0><<<blocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status, geom,
-                                                                     hist);
+    if (digit_word == 0 && iota1 && WORDS == 2)
+      k_radix_scatter<WORDS, 0, WORDS == 2><<<blocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status,
+                                                                                 geom, hist);
+    else if (digit_word == 0)
+      k_radix_scatter<WORDS, 0, false><<<blocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status,
+                                                                            geom, hist);
     else
-      k_radix_scatter<WORDS, 1><<<blocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status, geom,
-                                                                     hist);
+      k_radix_scatter<WORDS, 1, false><<<blocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status,
+                                                                            geom, hist);
   }
   return cudaGetLastError();
 }
 
 template cudaError_t radix_pass<2>(xg_frame*, const SortArrays<2>&, int, int, uint32_t, const SortGeom&, DevStatus*,
-                                    uint32_t*, cudaStream_t);
+                                    uint32_t*, cudaStream_t, bool);
 template cudaError_t radix_pass<3>(xg_frame*, const SortArrays<3>&, int, int, uint32_t, const SortGeom&, DevStatus*,
-                                    uint32_t*, cudaStream_t);
+                                    uint32_t*, cudaStream_t, bool);
 
 cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   const FramePtrs& p = f->p;
@@ -831,14 +843,17 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   // stage 1: every view's n entries, [v*n, (v+1)*n), sorted by the depth bits as a segment
-  // of its own; words: depth bits, Gaussian
+  // of its own; words: depth bits, Gaussian.  The first pass reads the projection's depth
+  // plane (t_z >= 0, whose float bits order like the values) and generates the Gaussian
+  // index, the entry's position in its view.
   const SortGeom sg = sort_geom(f->n, f->n_views, f->sort_blocks);
   int cur = 0;
   for (int pass = 0; pass < f->entry_passes; ++pass) {
     SortArrays<2> arr;
-    arr.in[0] = p.ent_depth[cur], arr.in[1] = p.ent_gid[cur];
+    arr.in[0] = pass == 0 ? reinterpret_cast<const uint32_t*>(p.depth) : p.ent_depth[cur];
+    arr.in[1] = pass == 0 ? nullptr : p.ent_gid[cur];
     arr.out[0] = p.ent_depth[cur ^ 1], arr.out[1] = p.ent_gid[cur ^ 1];
-    const cudaError_t e = radix_pass<2>(f, arr, 0, 8 * pass, 255u, sg, p.status, p.hist, st);
+    const cudaError_t e = radix_pass<2>(f, arr, 0, 8 * pass, 255u, sg, p.status, p.hist, st, pass == 0);
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }

@@ -58,7 +58,7 @@ xg_status noalloc_scratch(cudaStream_t st, unsigned char** out) {
 __global__ void k_noalloc_status(DevStatus* st, int64_t count) {
   if (threadIdx.x != 0) return;
   st->code = XG_OK;
-  st->reserved = 0;
+  st->next_item = 0;
   st->pairs = count;
   st->nonfinite = 0;
   st->fwd_evaluated = st->fwd_contrib = st->bwd_evaluated = st->bwd_contrib = 0;

@@ -5,9 +5,11 @@
 // rectangle of the footprint.  One thread per (Gaussian, view): the five attribute planes
 // are read with unit-stride loads (structure of arrays), the per-view camera is a broadcast.
 //
-// k_project_bwd: the chain rule back from the per-(view, Gaussian) gradients of u and the
-// conic, written by the compositing backward pass, to mean, scale, quaternion, opacity and
-// intensity; one thread per Gaussian sums its views in registers.
+// k_project_bwd: the chain rule back from the per-(view, Gaussian) sums the compositing
+// backward pass writes (moments of dL/dpower over the pixel offsets, and dL/dintensity):
+// first to dL/du, dL/dconic and dL/dopacity of each view (written back in place of the
+// sums), then to mean, scale, quaternion, opacity and intensity; one thread per Gaussian sums
+// its views in registers.
 #include "xg_internal.cuh"
 
 namespace xg {
@@ -18,7 +20,6 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ mean,
                                                  const Camera* __restrict__ cams, int W, int H, int tw, int th,
                                                  float near_mm, float4* __restrict__ rec, float* __restrict__ depth,
                                                  ushort4* __restrict__ rect, uint32_t* __restrict__ count,
-                                                 uint32_t* __restrict__ ent_depth, uint32_t* __restrict__ ent_gid,
                                                  DevStatus* __restrict__ status) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
@@ -126,7 +127,9 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ mean,
     if (!(x0 <= x1 && y0 <= y1)) break;
     const int tx0 = (int)x0 / tw, tx1 = (int)x1 / tw, ty0 = (int)y0 / th, ty1 = (int)y1 / th;
     r0 = make_float4(ux, uy, ca, cb);
-    r1 = make_float4(cc, o, in, 0.f);
+    // the exponent below which the opacity stays under 1/255 for sure, with a margin far
+    // above the error of the FP32 exp: the compositing kernels skip such pairs
+    r1 = make_float4(cc, o, in, fsub(-lg, 1e-4f));
     dz = tz;
     rc = make_ushort4((unsigned short)tx0, (unsigned short)ty0, (unsigned short)tx1, (unsigned short)ty1);
     cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
@@ -137,9 +140,6 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ mean,
   depth[vg] = dz;
   rect[vg] = rc;
   count[vg] = cnt;
-  // keys of the per-view depth sort of the entries
-  ent_depth[vg] = __float_as_uint(dz);
-  ent_gid[vg] = (uint32_t)g;
 }
 
 cudaError_t launch_project(xg_frame* f, const xg_gaussians* g, cudaStream_t st) {
@@ -148,8 +148,7 @@ cudaError_t launch_project(xg_frame* f, const xg_gaussians* g, cudaStream_t st) 
   Timed t(f, kProject, st);
   k_project<<<grid, 256, 0, st>>>(g->mean, g->scale, g->quat, g->opacity, g->intensity, n, f->p.cam, f->width,
                                   f->height, f->cfg.tile_w, f->cfg.tile_h, f->cfg.near_mm, f->p.rec, f->p.depth,
-                                  f->p.rect, f->p.count, f->p.ent_depth[0], f->p.ent_gid[0],
-                                  f->p.status);
+                                  f->p.rect, f->p.count, f->p.status);
   return cudaGetLastError();
 }
 
@@ -158,8 +157,9 @@ cudaError_t launch_project(xg_frame* f, const xg_gaussians* g, cudaStream_t st) 
 // ------------------------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ mean, const float* __restrict__ scale,
-                                                     const float* __restrict__ quat, int64_t n, int n_views,
-                                                     const Camera* __restrict__ cams, const float* __restrict__ g2d,
+                                                     const float* __restrict__ quat, const float* __restrict__ opac,
+                                                     int64_t n, int n_views,
+                                                     const Camera* __restrict__ cams, float* __restrict__ g2d,
                                                      const DevStatus* __restrict__ status, float* __restrict__ g_mean,
                                                      float* __restrict__ g_scale, float* __restrict__ g_quat,
                                                      float* __restrict__ g_opac, float* __restrict__ g_inten) {
@@ -199,14 +199,16 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ m
       for (int k = 0; k < 3; ++k) S[r][k] = M[r][0] * M[k][0] + M[r][1] * M[k][1] + M[r][2] * M[k][2];
     float gS[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 
+    float s1 = 0.f;  // sum over views of S_1
     for (int v = 0; v < n_views; ++v) {
       const int64_t vg = (int64_t)v * n + g;
+      // the compositing pass's sums over the view's pixels: S_x, S_y, S_xx, S_xy, S_yy, S_1
+      // of dp = dL/dpower times (d, d d^T, 1), and dL/dintensity
       const float4 q0 = reinterpret_cast<const float4*>(g2d)[2 * vg];
       const float4 q1 = reinterpret_cast<const float4*>(g2d)[2 * vg + 1];
-      const float gux = q0.x, guy = q0.y, ga = q0.z, gb = q0.w, gc = q1.x;
-      go += q1.y;
+      s1 += q1.y;
       gi += q1.z;
-      if (gux == 0.f && guy == 0.f && ga == 0.f && gb == 0.f && gc == 0.f) continue;
+      if (q0.x == 0.f && q0.y == 0.f && q0.z == 0.f && q0.w == 0.f && q1.x == 0.f && q1.y == 0.f) continue;
       const Camera cam = cams[v];
       const float c = cam.c, s = cam.s, fu = cam.fu, fv = cam.fv;
       const float tx = c * my - s * mx, ty = -mz, tz = -c * mx - s * my + cam.L;
@@ -226,6 +228,13 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ m
       const float C = T1[0] * ST1[0] + T1[1] * ST1[1] + T1[2] * ST1[2] + kDilate;
       const float idet = 1.f / (A * C - B * B);
       const float ka = C * idet, kb = -B * idet, kc = A * idet;
+      // power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = u - p: dL/du = -K (S_x, S_y),
+      // dL/d(a, b, c) = (-S_xx / 2, -S_xy, -S_yy / 2)
+      const float gux = -(ka * q0.x + kb * q0.y), guy = -(kb * q0.x + kc * q0.y);
+      const float ga = -0.5f * q0.z, gb = -q0.w, gc = -0.5f * q1.x;
+      // the view's 2-D gradients replace the sums (dL/dopacity = S_1 / opacity)
+      reinterpret_cast<float4*>(g2d)[2 * vg] = make_float4(gux, guy, ga, gb);
+      reinterpret_cast<float4*>(g2d)[2 * vg + 1] = make_float4(gc, q1.y / opac[g], q1.z, 0.f);
       // conic K = Sigma''^-1; dL/dSigma'' = -K Gh K, Gh = [[ga, gb/2], [gb/2, gc]]
       const float hb = 0.5f * gb;
       const float KG00 = ka * ga + kb * hb, KG01 = ka * hb + kb * gc;
@@ -288,6 +297,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ m
     gq[1] = (gx - x * dot) * inv;
     gq[2] = (gy - y * dot) * inv;
     gq[3] = (gz - z * dot) * inv;
+    go = s1 / opac[g];
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -303,7 +313,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ m
 cudaError_t launch_project_bwd(xg_frame* f, const xg_gaussians* g, const xg_grads* out, cudaStream_t st) {
   const int64_t n = f->n;
   Timed t(f, kProjectBwd, st);
-  k_project_bwd<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->mean, g->scale, g->quat, n, f->n_views, f->p.cam,
+  k_project_bwd<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->mean, g->scale, g->quat, g->opacity, n, f->n_views, f->p.cam,
                                                              f->p.grad2d, f->p.status, out->mean, out->scale,
                                                              out->quat, out->opacity, out->intensity);
   return cudaGetLastError();

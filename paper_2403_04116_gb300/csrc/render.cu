@@ -1,86 +1,127 @@
 // Front-to-back alpha compositing of intensity per detector pixel (Eq. 10) and its
 // backward pass.
 //
-// One CTA per (tile, view).  Each thread owns PPT pixels (1, 2 or 4, 4 rows apart), so
-// a warp owns an 8 x 4*PPT block.  The tile's depth-sorted list is staged through shared
-// memory in batches (the record of each Gaussian read once per CTA and broadcast to all its
-// pixels); a CTA stops fetching as soon as every pixel's transmittance has hit the floor
-// (__syncthreads_count).  Per batch, each warp compacts the staged entries whose footprint
-// can reach its block (box test, then the largest exponent over the block) and walks only
-// those.
+// Work item: one warp's pixel block, 8 columns by 4*PPT rows of one (view, tile).  A thread
+// owns PPT pixels (1, 2 or 4, four rows apart) and takes them in pairs with the packed
+// two-lane FP32 instructions of sm_100 and later (f32x2 add / mul / fma): both pixels of a
+// pair see the same list entry, and each lane is rounded as the scalar operation would be,
+// so results are those of the documented scalar FP32 sequence.
 //
-// A thread's pixels are processed in pairs with the packed two-lane FP32 instructions of
-// sm_100+ (f32x2 add / mul / fma): both pixels of a pair see the same list entry, so the
-// exponent, exp, opacity, transmittance and colour (forward) or gradient terms (backward)
-// of the two run as one instruction stream.  Each lane rounds as the scalar operation
-// would, so results are those of the documented scalar FP32 sequence.
+// The warps of a tile never wait for one another: each walks the tile's depth-sorted list
+// on its own, so no warp idles at a block-wide barrier while another finishes a longer
+// walk.  A warp fetches the list 32 entries a round, one per lane: the Gaussian index, then
+// its 32-byte record copied asynchronously (cp.async) into the warp's ring of RING
+// shared-memory slots, RING - 1 rounds ahead of the round being processed (the frame's
+// "batch" = 32 (RING - 1) records in flight per warp).  Each lane tests its own record --
+// can the footprint reach the warp's block?  (the largest exponent of the footprint over
+// the block's pixel centres, against the record's threshold) -- and the warp walks the
+// entries that can, in list order.
 //
-// Most (pixel, list entry) pairs lie outside the Gaussian's footprint.  Each staged record
-// carries a conservative exponent threshold ln(1/(255 o)) - 1e-4: below it the opacity
-// provably stays under 1/255 (the FP32 exp used for the decision is accurate to 3e-7), so
-// the pair is skipped without evaluating exp.  Every other pair goes through the fixed
-// FP32 decision sequence, so decisions are exactly those of the full test.
+// Most (pixel, entry) pairs of a walked entry still lie outside the footprint.  The record
+// carries the exponent threshold ln(1/(255 o)) - 1e-4, below which the opacity provably
+// stays under 1/255 (the FP32 exp used for the decision is accurate to 3e-7): such a pair
+// skips exp.  Every other pair goes through the fixed FP32 decision sequence, so decisions
+// are exactly those of the full test.
 //
-// The backward pass walks each pixel's list back to front from its last contributor,
-// recovering the transmittance by division instead of storing it.  Per list entry, a warp
-// with contributing pixels sums its 7 per-pixel terms (six moments of dL/dpower and the
-// intensity term) with an 8-value reduce-scatter butterfly (9 shuffles; lane 4k ends with
-// the sum of term k) into shared memory.  After the batch each Gaussian's sums are turned
-// into dL/du, dL/dconic and dL/dopacity and added to global memory with two float4 atomics.
+// The backward pass walks each pixel's list back to front from its last contributor and
+// recovers the transmittance by division instead of storing it: T_j = T_{j+1} / (1 -
+// alpha_j), with 1 - alpha_j in [0.01, 1], as a hardware reciprocal refined by one Newton
+// step and one residual correction of the quotient (Markstein's scheme for correctly
+// rounded division, here without the special cases that cannot occur).  The round's
+// entries that reach the block are first written in a duplicated form (one broadcast load
+// gives both lanes of a packed operand).  Per walked entry, a warp with contributing pixels
+// sums its 7 per-pixel terms -- six moments of dL/dpower (S_1, S_x, S_y, S_xx, S_xy, S_yy
+// over the pixel offsets d = u - p) and the intensity term -- with an 8-value
+// reduce-scatter butterfly (9 shuffles; lane k ends with the sum of term k), and lanes 0-6
+// add them to the (view, Gaussian)'s sums in global memory in one atomic instruction.  The
+// projection's backward pass turns the sums into dL/du, dL/dconic and dL/dopacity.
+//
+// Launch forms: one block per (view, tile), its warps the tile's blocks; or persistent
+// blocks (as many as fit on the device at once) whose warps take work items from a counter
+// in the status word, in longest-tile-list-first order.
+#include <algorithm>
+
 #include "xg_internal.cuh"
+
 
 namespace xg {
 
+// Shared memory per warp: RING rounds of 32 records of 32 bytes, the rounds' Gaussian indices
+// (32 words each), then the current round's entries in the duplicated form (32 x 64 bytes).
+template <int RING>
+__host__ __device__ constexpr int ring_bytes() { return RING * 32 * (32 + 4) + 32 * 64; }
+// the same, for a ring depth known at run time (the launch's dynamic shared memory per warp)
+inline int ring_bytes_rt(int ring) { return ring * 32 * (32 + 4) + 32 * 64; }
+static_assert(ring_bytes<3>() == 3 * 32 * 36 + 2048, "ring layout");
 
-constexpr int kMaxWarps = 16;  // 512-thread tiles
-
-// One list entry staged for the pixel-pair kernels: every field duplicated so that one
-// broadcast shared load yields both lanes of a packed operand.  q0..q3 = (u_x u_x u_y u_y),
-// (na na nb nb), (nc nc o o), (i i thr thr) with na, nb, nc = -a/2, -b, -c/2 and thr the
-// exponent threshold; box = conservative pixel box (x0, x1, y0, y1) of the footprint.
-struct Staged {
-  float4 q0, q1, q2, q3, box;
+struct RenderArgs {
+  const uint2* range;
+  const uint32_t* order;
+  const uint32_t* value;
+  const float4* rec;
+  const Camera* cams;
+  DevStatus* st;
+  uint32_t* counter;  // persistent form: next work item
+  int64_t n;
+  int64_t range_stride;
+  int tiles_per_view, tiles_x, W, H, tw, th;
+  int wpt;            // warps (pixel blocks) per tile
+  uint32_t items;     // work items: views * tiles * wpt
+  // forward
+  float* image;
+  uint32_t* ncontrib;
+  float* tfinal;
+  uint32_t* last;
+  // backward
+  const float* grad_image;
+  const float* tfinal_in;
+  const uint32_t* last_in;
+  float* g2d;
 };
 
-__device__ __forceinline__ Staged stage_record(const float4 a, const float4 b, const Camera& cam) {
-  Staged e;
-  const float na = -0.5f * a.z, nb = -a.w, nc = -0.5f * b.x;
-  // ln(255 o) with the fast hardware log (absolute error below 1e-5 here): the threshold
-  // keeps a 1e-4 margin and the box 0.1 % + 0.01 px, so both stay conservative
-  const float l255o = __logf(255.f * b.y);
-  const float thr = -l255o - 1e-4f;
-  e.q0 = make_float4(a.x, a.x, a.y, a.y);
-  e.q1 = make_float4(na, na, nb, nb);
-  e.q2 = make_float4(nc, nc, b.y, b.y);
-  e.q3 = make_float4(b.z, b.z, thr, thr);
-  const float two_l = 2.f * fmaxf(l255o, 0.f);
-  const float det = a.z * b.x - a.w * a.w;
-  float ex = INFINITY, ey = INFINITY;
-  if (det > 0.f) {
-    const float sdet = __fdividef(two_l, det);
-    ex = __fsqrt_rn(sdet * b.x) * 1.001f + 0.01f;
-    ey = __fsqrt_rn(sdet * a.z) * 1.001f + 0.01f;
-  }
-  const float cx = a.x + cam.hw, cy = a.y + cam.hh;
-  e.box = make_float4(cx - ex, cx + ex, cy - ey, cy + ey);
-  return e;
+// The warp's ring of record slots: slot (round % RING), one 32-byte record per lane.
+template <int RING>
+__device__ __forceinline__ float4* warp_ring(int warp_in_cta) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  return reinterpret_cast<float4*>(s_dyn + (size_t)warp_in_cta * ring_bytes<RING>());
+}
+// Per warp, after the ring: the round's entries in the duplicated form, one per lane:
+// (u_x u_x u_y u_y), (na na nb nb), (nc nc o o), (i i thr thr) as [4][32] float4.
+template <int RING>
+__device__ __forceinline__ float4* warp_stage(int warp_in_cta) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  return reinterpret_cast<float4*>(s_dyn + (size_t)warp_in_cta * ring_bytes<RING>() + RING * 32 * 36);
+}
+template <int RING>
+__device__ __forceinline__ uint32_t* ring_index(int warp_in_cta) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  return reinterpret_cast<uint32_t*>(s_dyn + (size_t)warp_in_cta * ring_bytes<RING>() + RING * 32 * 32);
 }
 
-// Stages list entries [first, first + cnt) of a tile into shared memory for the whole CTA.
-template <int kBatch>
-__device__ __forceinline__ void stage_batch_pairs(const uint32_t* __restrict__ value, const float4* __restrict__ rec,
-                                                  int64_t vn_base, uint32_t first, int cnt, const Camera& cam,
-                                                  float4 (*s_q)[kBatch], float4* s_box, uint32_t* s_g) {
-  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    const uint32_t g = value[first + j];
-    const Staged e = stage_record(rec[2 * (vn_base + g)], rec[2 * (vn_base + g) + 1], cam);
-    s_q[0][j] = e.q0;
-    s_q[1][j] = e.q1;
-    s_q[2][j] = e.q2;
-    s_q[3][j] = e.q3;
-    s_box[j] = e.box;
-    if (s_g) s_g[j] = g;
+// Asynchronous 16-byte global -> shared copies (cp.async, cached in L1: the warps of a tile
+// read the same records), one commit group per round.
+__device__ __forceinline__ void copy16(void* dst, const void* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+// waits until at most N of this thread's commit groups are still pending
+template <int N>
+__device__ __forceinline__ void copy_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Issues the copy of the record of Gaussian g into this lane's place of ring slot `slot`
+// (nothing for a lane past the list), then commits the round's group.
+template <int RING>
+__device__ __forceinline__ void fetch_round(float4* ring, int slot, int lane, bool valid, const float4* rec,
+                                            int64_t vn_base, uint32_t g) {
+  if (valid) {
+    float4* dst = ring + (slot * 32 + lane) * 2;
+    const float4* src = rec + 2 * (vn_base + g);
+    copy16(dst, src);
+    copy16(dst + 1, src + 1);
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 // Largest exponent na dx^2 + nb dx dy + nc dy^2 (na, nc < 0) over the offsets
@@ -104,36 +145,18 @@ __device__ __forceinline__ float max_power_over_rect(float na, float nb, float n
   return best;
 }
 
-// Whether a footprint can reach the warp's pixel block [bx0, bx0+7] x [by0, by1] (pixel
-// indices): its box meets the block and the largest exponent over the block's pixel centres
-// is within a margin (1e-2 + 1e-3 |thr|, far above FP32 rounding of these sums) of the
-// threshold below which no pixel can reach opacity 1/255.  Only entries that no pixel of the
-// block could take fail, so decisions are unchanged.
-__device__ __forceinline__ bool reaches_block(const float4 box, float ux, float uy, float na, float nb, float nc,
-                                              float thr, float bx0, float by0, float by1, const Camera& cam) {
-  if (!(box.x <= bx0 + 7.f && box.y >= bx0 && box.z <= by1 && box.w >= by0)) return false;
-  const float cx = ux + cam.hw, cy = uy + cam.hh;
+// Whether a record's footprint can reach the block [bx0, bx0 + 7] x [by0, by1] (pixel
+// indices): the largest exponent over the block's pixel centres is within a margin
+// (1e-2 + 1e-3 |thr|, far above FP32 rounding of these sums) of the threshold below which
+// no pixel can reach opacity 1/255.  Only entries that no pixel of the block could take
+// fail, so decisions are unchanged.  Records of culled Gaussians are all zero and fail.
+__device__ __forceinline__ bool reaches_block(const float4 a, const float4 b, float bx0, float by0, float by1,
+                                              const Camera& cam) {
+  if (!(b.y > 0.f)) return false;
+  const float na = -0.5f * a.z, nb = -a.w, nc = -0.5f * b.x, thr = b.w;
+  const float cx = a.x + cam.hw, cy = a.y + cam.hh;
   const float best = max_power_over_rect(na, nb, nc, cx - (bx0 + 7.f), cx - bx0, cy - by1, cy - by0);
   return best >= thr - (1e-2f + 1e-3f * fabsf(thr));
-}
-
-// The staged entries that can reach this warp's block (reaches_block), in list order;
-// returns their count.
-template <int kBatch>
-__device__ __forceinline__ int warp_list(const float4 (*s_q)[kBatch], const float4* s_box, int cnt, float bx0,
-                                         float by0, float by1, const Camera& cam, uint16_t* list, int lane) {
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  int m = 0;
-  for (int j0 = 0; j0 < cnt; j0 += 32) {
-    const int j = j0 + lane;
-    const bool hit = j < cnt && reaches_block(s_box[j], s_q[0][j].x, s_q[0][j].z, s_q[1][j].x, s_q[1][j].z,
-                                              s_q[2][j].x, s_q[3][j].z, bx0, by0, by1, cam);
-    const uint32_t mask = __ballot_sync(0xffffffffu, hit);
-    if (hit) list[m + __popc(mask & lt_mask)] = (uint16_t)j;
-    m += __popc(mask);
-  }
-  __syncwarp();
-  return m;
 }
 
 // Work counters: one atomic per warp.
@@ -150,44 +173,81 @@ __device__ __forceinline__ void add_counts(uint32_t ev, uint32_t nc, unsigned lo
   }
 }
 
-// First pixel of thread `tid` inside a tw-wide tile: warps own 8 x 4*PPT blocks, row-major;
-// the thread's other pixels are 4, 8, 12 rows below.
-template <int PPT>
-__device__ __forceinline__ void pixel_in_tile(int tid, int tw, int& lx, int& ly) {
-  const int lane = tid & 31, warp = tid >> 5, wx = tw >> 3;
-  lx = (warp % wx) * 8 + (lane & 7);
-  ly = (warp / wx) * (4 * PPT) + (lane >> 3);
-}
-
-// Sum of v[k] over the warp for k = 0..7, scattered: returns the total of term
-// ((lane >> 2) & 7) in every lane.  9 shuffles instead of 8 x 5.
-__device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int lane) {
+// Sum of v[k] over the warp for k = 0..7, scattered: returns the total of term (lane & 7)
+// in every lane (lanes 0..7 hold terms 0..7).  9 shuffles.
+__device__ __forceinline__ float warp_reduce_scatter8_low(const float (&v)[8], int lane) {
   float a[4], c[2];
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  const bool b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float send = b4 ? v[k] : v[k + 4];
-    a[k] = (b4 ? v[k + 4] : v[k]) + __shfl_xor_sync(0xffffffffu, send, 16);
+    const float send = b2 ? v[k] : v[k + 4];
+    a[k] = (b2 ? v[k + 4] : v[k]) + __shfl_xor_sync(0xffffffffu, send, 4);
   }
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const float send = b3 ? a[k] : a[k + 2];
-    c[k] = (b3 ? a[k + 2] : a[k]) + __shfl_xor_sync(0xffffffffu, send, 8);
+    const float send = b1 ? a[k] : a[k + 2];
+    c[k] = (b1 ? a[k + 2] : a[k]) + __shfl_xor_sync(0xffffffffu, send, 2);
   }
-  float d = (b2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b2 ? c[0] : c[1], 4);
-  d += __shfl_xor_sync(0xffffffffu, d, 2);
-  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  float d = (b0 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b0 ? c[0] : c[1], 1);
+  d += __shfl_xor_sync(0xffffffffu, d, 8);
+  d += __shfl_xor_sync(0xffffffffu, d, 16);
   return d;
 }
 
-// The exponent -1/2 d^T K d = dx (na dx + nb dy) + (nc dy) dy, with na = -a/2, nb = -b,
-// nc = -c/2, in the fixed FP32 sequence.
-__device__ __forceinline__ float power_of(const float4 a, const float nc, float px, float py, float& dx, float& dy) {
-  dx = fsub(a.x, px);
-  dy = fsub(a.y, py);
-  const float t = ffma(a.z, dx, fmul(a.w, dy));
-  return ffma(dx, t, fmul(fmul(nc, dy), dy));
+// T / om for om in [0.01, 1] and T in (0, 1], lane by lane: the hardware reciprocal r0
+// (relative error below 2^-22), one Newton step r = r0 + r0 (1 - om r0), the quotient
+// q = T r and one residual correction q + r (T - q om) with the residual formed exactly by
+// an FMA (Markstein).  No operand is zero, infinite, NaN or subnormal here, so none of the
+// special cases of a general division arise.
+__device__ __forceinline__ float2 div_recover(float2 T, float2 om) {
+  float rx, ry;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rx) : "f"(om.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(om.y));
+  float2 r = make_float2(rx, ry);
+  const float2 nom = make_float2(-om.x, -om.y);
+  const float2 e = ffma2(nom, r, f2(1.0f));
+  r = ffma2(r, e, r);
+  const float2 q = fmul2(T, r);
+  const float2 res = ffma2(make_float2(-q.x, -q.y), om, T);
+  return ffma2(res, r, q);
 }
+
+// The block of work item `item`: its (view, tile) and the warp's block inside the tile.
+struct Item {
+  int v, tile, tx0, ty0, bx, by;  // bx, by: the block's first pixel column and row
+  bool ok;
+};
+
+template <int PPT>
+__device__ __forceinline__ Item item_of(const RenderArgs& A, uint32_t item) {
+  Item it;
+  const uint32_t tile_item = item / (uint32_t)A.wpt, sub = item - tile_item * (uint32_t)A.wpt;
+  const uint32_t work = A.order[tile_item];
+  const uint32_t tiles = (uint32_t)A.tiles_per_view;
+  it.ok = item < A.items && work < A.items / (uint32_t)A.wpt;  // an order that no xg_bin_sort wrote fails
+  it.v = (int)(work / tiles);
+  it.tile = (int)(work - (uint32_t)it.v * tiles);
+  it.tx0 = (it.tile % A.tiles_x) * A.tw;
+  it.ty0 = (it.tile / A.tiles_x) * A.th;
+  const int wx = A.tw >> 3;
+  it.bx = it.tx0 + (int)(sub % (uint32_t)wx) * 8;
+  it.by = it.ty0 + (int)(sub / (uint32_t)wx) * (4 * PPT);
+  return it;
+}
+
+// Next work item of this warp: the persistent form takes one from the counter, the other
+// form has exactly one, blockIdx.x * wpt + warp.
+template <bool PERSIST>
+__device__ __forceinline__ uint32_t next_item(const RenderArgs& A, int lane, int warp, bool first) {
+  if (!PERSIST) return first ? blockIdx.x * (uint32_t)A.wpt + (uint32_t)warp : 0xffffffffu;
+  uint32_t it = 0;
+  if (lane == 0) it = atomicAdd(A.counter, 1u);
+  return __shfl_sync(0xffffffffu, it, 0);
+}
+
+// ------------------------------------------------------------------------------------------
+// forward
+// ------------------------------------------------------------------------------------------
 
 // One list entry for a thread's pixel pairs: exponent, exp, opacity, transmittance and
 // colour of both pixels of each pair with packed instructions, decisions per pixel.
@@ -200,7 +260,6 @@ __device__ __forceinline__ void fwd_entry(const float4 q0, const float4 q1, cons
 #pragma unroll
   for (int pr = 0; pr < NP; ++pr) {
     if (done[pr][0] && done[pr][1]) continue;
-    // the exponent dx (na dx + nb dy) + (nc dy) dy of both pixels
     const float2 dy = fadd2(make_float2(q0.z, q0.w), npy[pr]);
     const float2 t = ffma2(make_float2(q1.x, q1.y), dx, fmul2(make_float2(q1.z, q1.w), dy));
     const float2 p = ffma2(dx, t, fmul2(fmul2(make_float2(q2.x, q2.y), dy), dy));
@@ -234,221 +293,213 @@ __device__ __forceinline__ void fwd_entry(const float4 q0, const float4 q1, cons
   }
 }
 
-// Forward.  A thread's pixels are taken in pairs (4 rows apart; for one pixel per thread
-// the second of the pair is idle), and the exponent, exp, opacity, transmittance and colour
-// of both are computed with packed two-lane instructions; the decisions stay per pixel.
-template <int kBatch, int PPT>
-__global__ void __launch_bounds__(512) k_render_fwd(const uint2* __restrict__ range, const uint32_t* __restrict__ order,
-                                                    int tiles_per_view, const uint32_t* __restrict__ value,
-                                                    const float4* __restrict__ rec, int64_t n, int W, int H,
-                                                    int tiles_x, int64_t range_stride, int tw, int th,
-                                                    const Camera* __restrict__ cams, DevStatus* __restrict__ st,
-                                                    float* __restrict__ image, uint32_t* __restrict__ ncontrib,
-                                                    float* __restrict__ tfinal, uint32_t* __restrict__ last) {
+template <int PPT, int RING, bool PERSIST>
+__global__ void __launch_bounds__(512) k_render_fwd(const RenderArgs A) {
   constexpr int NP = PPT > 1 ? PPT / 2 : 1;  // pixel pairs per thread
-  const uint32_t work = order[blockIdx.x];  // (view, tile) items, longest tile lists first
-  if (work >= gridDim.x) return;            // only an order that no xg_bin_sort wrote
-  const int v = (int)(work / (uint32_t)tiles_per_view), tile = (int)(work % (uint32_t)tiles_per_view);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int lx, ly;
-  pixel_in_tile<PPT>(threadIdx.x, tw, lx, ly);
-  const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
-  const int x = tx0 + lx;
-  const float bx0 = (float)(tx0 + (lx & ~7)), by0 = (float)(ty0 + (ly & ~3));  // this warp's block
-  const float by1 = by0 + (float)(4 * PPT - 1);
-  const Camera cam = cams[v];
-  const float2 npx = f2(-fsub((float)x, cam.hw));
-  const uint2 r = st->code == XG_OK ? range[(int64_t)v * range_stride + tile] : make_uint2(0u, 0u);
-  const int nlist = (int)(r.y - r.x);
-  const int64_t vn_base = (int64_t)v * n;
+  float4* const ring = warp_ring<RING>(warp);
+  const bool status_ok = A.st->code == XG_OK;
+  uint32_t nev = 0, nct = 0;
+  for (uint32_t item = next_item<PERSIST>(A, lane, warp, true);; item = next_item<PERSIST>(A, lane, warp, false)) {
+    if (item >= A.items) break;
+    const Item it = item_of<PPT>(A, item);
+    if (!it.ok) break;
+    const Camera cam = A.cams[it.v];
+    const int x = it.bx + (lane & 7);
+    const float bx0 = (float)it.bx, by0 = (float)it.by, by1 = by0 + (float)(4 * PPT - 1);
+    const float2 npx = f2(-fsub((float)x, cam.hw));
+    const uint2 r = status_ok ? A.range[(int64_t)it.v * A.range_stride + it.tile] : make_uint2(0u, 0u);
+    const int nlist = (int)(r.y - r.x);
+    const int64_t vn_base = (int64_t)it.v * A.n;
 
-  float2 npy[NP], T[NP], C[NP];
-  uint32_t nc[NP][2], lastp[NP][2];
-  bool done[NP][2];
+    float2 npy[NP], T[NP], C[NP];
+    uint32_t nc[NP][2], lastp[NP][2];
+    bool done[NP][2];
 #pragma unroll
-  for (int pr = 0; pr < NP; ++pr) {
-    float ny[2];
+    for (int pr = 0; pr < NP; ++pr) {
+      float ny[2];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int y = ty0 + ly + 4 * (2 * pr + h);
-      ny[h] = -fsub((float)y, cam.hh);
-      nc[pr][h] = lastp[pr][h] = 0;
-      done[pr][h] = !((PPT > 1 || h == 0) && x < W && y < H);
+      for (int h = 0; h < 2; ++h) {
+        const int y = it.by + (lane >> 3) + 4 * (2 * pr + h);
+        ny[h] = -fsub((float)y, cam.hh);
+        nc[pr][h] = lastp[pr][h] = 0;
+        done[pr][h] = !((PPT > 1 || h == 0) && x < A.W && y < A.H);
+      }
+      npy[pr] = make_float2(ny[0], ny[1]);
+      T[pr] = f2(1.0f);
+      C[pr] = f2(0.0f);
     }
-    npy[pr] = make_float2(ny[0], ny[1]);
-    T[pr] = f2(1.0f);
-    C[pr] = f2(0.0f);
-  }
-  uint32_t nev = 0;
-  auto all_done = [&]() {
-    bool d = true;
+    auto all_done = [&]() {
+      bool d = true;
 #pragma unroll
-    for (int pr = 0; pr < NP; ++pr) d = d && done[pr][0] && done[pr][1];
-    return d;
-  };
-  __shared__ float4 s_q[4][kBatch];
-  __shared__ float4 s_box[kBatch];
-  __shared__ uint16_t s_list[kMaxWarps][kBatch];
-  uint16_t* my_list = s_list[warp];
-  for (int base = 0; base < nlist; base += kBatch) {
-    if (__syncthreads_count(all_done()) == (int)blockDim.x) break;
-    const int cnt = min(kBatch, nlist - base);
-    stage_batch_pairs<kBatch>(value, rec, vn_base, r.x + base, cnt, cam, s_q, s_box, nullptr);
-    __syncthreads();
-    if (__all_sync(0xffffffffu, all_done())) continue;
-    const int m = warp_list<kBatch>(s_q, s_box, cnt, bx0, by0, by1, cam, my_list, lane);
-#pragma unroll 2
-    for (int k = 0; k < m; ++k) {
-      if (all_done()) break;
-      const int j = my_list[k];
-      fwd_entry<NP>(s_q[0][j], s_q[1][j], s_q[2][j], s_q[3][j], (uint32_t)(base + j + 1), npx, npy, T, C, nc,
-                    lastp, done, nev);
+      for (int pr = 0; pr < NP; ++pr) d = d && done[pr][0] && done[pr][1];
+      return d;
+    };
+    // round q: list positions [32 q, 32 q + 32), lane l at 32 q + l; the records of the next
+    // RING - 1 rounds are in flight while round q is walked
+    const int rounds = (nlist + 31) / 32;
+#pragma unroll
+    for (int q = 0; q < RING - 1; ++q) {
+      const int e = 32 * q + lane;
+      const uint32_t g = e < nlist ? A.value[r.x + e] : 0u;
+      fetch_round<RING>(ring, q, lane, e < nlist, A.rec, vn_base, g);
     }
-  }
-  uint32_t nct = 0;
+    uint32_t g_next = 32 * (RING - 1) + lane < nlist ? A.value[r.x + 32 * (RING - 1) + lane] : 0u;
+    for (int q = 0; q < rounds; ++q) {
+      if (__all_sync(0xffffffffu, all_done())) break;
+      {
+        const int e = 32 * (q + RING - 1) + lane;
+        fetch_round<RING>(ring, (q + RING - 1) % RING, lane, e < nlist, A.rec, vn_base, g_next);
+        g_next = e + 32 < nlist ? A.value[r.x + e + 32] : 0u;
+      }
+      copy_wait<RING - 1>();  // round q's records have landed
+      __syncwarp();
+      const float4* slot = ring + (q % RING) * 64;
+      const bool hit = 32 * q + lane < nlist && reaches_block(slot[2 * lane], slot[2 * lane + 1], bx0, by0, by1, cam);
+      uint32_t mask = __ballot_sync(0xffffffffu, hit);
+      while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1;
+        if (all_done()) break;
+        const float4 a = slot[2 * k], b = slot[2 * k + 1];
+        const float na = -0.5f * a.z, nb = -a.w, nc2 = -0.5f * b.x;
+        fwd_entry<NP>(make_float4(a.x, a.x, a.y, a.y), make_float4(na, na, nb, nb), make_float4(nc2, nc2, b.y, b.y),
+                      make_float4(b.z, b.z, b.w, b.w), (uint32_t)(32 * q + k + 1), npx, npy, T, C, nc, lastp, done,
+                      nev);
+      }
+      __syncwarp();  // the slot is refilled next round
+    }
+    copy_wait<0>();  // no copy may land after the ring is reused or the block exits
+    __syncwarp();
 #pragma unroll
-  for (int pr = 0; pr < NP; ++pr) {
+    for (int pr = 0; pr < NP; ++pr) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (PPT == 1 && h == 1) continue;
-      const int y = ty0 + ly + 4 * (2 * pr + h);
-      nct += nc[pr][h];
-      if (x < W && y < H) {
-        const int64_t pix = ((int64_t)v * H + y) * W + x;
-        image[pix] = h ? C[pr].y : C[pr].x;
-        tfinal[pix] = h ? T[pr].y : T[pr].x;
-        last[pix] = lastp[pr][h];
-        if (ncontrib) ncontrib[pix] = nc[pr][h];
+      for (int h = 0; h < 2; ++h) {
+        if (PPT == 1 && h == 1) continue;
+        const int y = it.by + (lane >> 3) + 4 * (2 * pr + h);
+        nct += nc[pr][h];
+        if (x < A.W && y < A.H) {
+          const int64_t pix = ((int64_t)it.v * A.H + y) * A.W + x;
+          A.image[pix] = h ? C[pr].y : C[pr].x;
+          A.tfinal[pix] = h ? T[pr].y : T[pr].x;
+          A.last[pix] = lastp[pr][h];
+          if (A.ncontrib) A.ncontrib[pix] = nc[pr][h];
+        }
       }
     }
   }
-  add_counts(nev, nct, &st->fwd_evaluated, &st->fwd_contrib);
-}
-
-cudaError_t launch_render_fwd(xg_frame* f, float* image, uint32_t* n_contrib, cudaStream_t st) {
-  const FramePtrs& p = f->p;
-  const dim3 grid((unsigned)(f->tiles_per_view * f->n_views));
-  Timed t(f, kRenderFwd, st);
-  const int ppt = f->cfg.pixels_per_thread;
-  const int threads = f->cfg.tile_w * f->cfg.tile_h / ppt;
-#define XG_FWD(B, P)                                                                                       \
-  k_render_fwd<B, P><<<grid, threads, 0, st>>>(p.range, p.order, (int)f->tiles_per_view,                  \
-                                               p.value, p.rec, f->n, f->width,            \
-                                               f->height, f->tiles_x, (int64_t)1 << f->tile_bits, f->cfg.tile_w,   \
-                                               f->cfg.tile_h, p.cam, p.status, image, n_contrib, p.tfinal, \
-                                               p.last)
-  switch (ppt * 1000 + f->cfg.batch) {
-    case 1064: XG_FWD(64, 1); break;
-    case 1128: XG_FWD(128, 1); break;
-    case 1256: XG_FWD(256, 1); break;
-    case 2064: XG_FWD(64, 2); break;
-    case 2128: XG_FWD(128, 2); break;
-    case 2256: XG_FWD(256, 2); break;
-    case 4064: XG_FWD(64, 4); break;
-    case 4128: XG_FWD(128, 4); break;
-    default: XG_FWD(256, 4); break;
-  }
-#undef XG_FWD
-  return cudaGetLastError();
+  add_counts(nev, nct, &A.st->fwd_evaluated, &A.st->fwd_contrib);
 }
 
 // ------------------------------------------------------------------------------------------
 // backward
 // ------------------------------------------------------------------------------------------
-// Backward.  Pixels are taken in pairs as in the forward kernel.  A pixel of the pair that
-// does not contribute to an entry takes alpha = 0 there, which leaves its transmittance,
-// its blended-behind intensity and every gradient term unchanged, so the pair's update is
-// one packed, branch-free sequence.
-template <int kBatch, int PPT>
-__global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ range, const uint32_t* __restrict__ order,
-                                                    int tiles_per_view, const uint32_t* __restrict__ value,
-                                                    const float4* __restrict__ rec, int64_t n, int n_views, int W,
-                                                    int H, int tiles_x, int64_t range_stride, int tw, int th,
-                                                    const Camera* __restrict__ cams, DevStatus* __restrict__ st,
-                                                    const float* __restrict__ grad_image,
-                                                    const float* __restrict__ tfinal, const uint32_t* __restrict__ last,
-                                                    float* __restrict__ g2d) {
+// Pixels are taken in pairs as in the forward kernel.  A pixel of a pair that does not
+// contribute to an entry takes alpha = 0 there, which leaves its transmittance, its
+// blended-behind intensity and every gradient term unchanged, so the pair's update is one
+// packed, branch-free sequence.
+template <int PPT, int RING, bool PERSIST>
+__global__ void __launch_bounds__(512) k_render_bwd(const RenderArgs A) {
   constexpr int NP = PPT > 1 ? PPT / 2 : 1;
-  __shared__ float4 s_q[4][kBatch];
-  __shared__ float4 s_box[kBatch];
-  __shared__ uint32_t s_g[kBatch];
-  __shared__ __align__(16) float s_acc[kBatch * 8];
-  __shared__ uint16_t s_list[kMaxWarps][kBatch];
-  __shared__ uint32_t s_maxlast;
-  if (st->code != XG_OK) return;
-  const uint32_t work = order[blockIdx.x];  // (view, tile) items, longest tile lists first
-  if (work >= gridDim.x) return;            // only an order that no xg_bin_sort wrote
-  const int v = (int)(work / (uint32_t)tiles_per_view), tile = (int)(work % (uint32_t)tiles_per_view);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int lx, ly;
-  pixel_in_tile<PPT>(threadIdx.x, tw, lx, ly);
-  const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
-  const int x = tx0 + lx;
-  const float bx0 = (float)(tx0 + (lx & ~7)), by0 = (float)(ty0 + (ly & ~3));
-  const float by1 = by0 + (float)(4 * PPT - 1);
-  const Camera cam = cams[v];
-  const float2 npx = f2(-fsub((float)x, cam.hw));
-  const uint2 r = range[(int64_t)v * range_stride + tile];
-  const int64_t vn_base = (int64_t)v * n;
-  uint16_t* my_list = s_list[warp];
-
-  float2 npy[NP], G[NP], Tc[NP], A[NP];
-  uint32_t L[NP][2];
-  uint32_t lmax = 0;
-#pragma unroll
-  for (int pr = 0; pr < NP; ++pr) {
-    float ny[2], g[2], tc[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int y = ty0 + ly + 4 * (2 * pr + h);
-      ny[h] = -fsub((float)y, cam.hh);
-      g[h] = 0.f;
-      tc[h] = 1.f;
-      L[pr][h] = 0;
-      if ((PPT > 1 || h == 0) && x < W && y < H) {
-        const int64_t pix = ((int64_t)v * H + y) * W + x;
-        g[h] = grad_image[pix];
-        tc[h] = tfinal[pix];
-        L[pr][h] = g[h] != 0.f ? last[pix] : 0u;
-      }
-      lmax = max(lmax, L[pr][h]);
-    }
-    npy[pr] = make_float2(ny[0], ny[1]);
-    G[pr] = make_float2(g[0], g[1]);
-    Tc[pr] = make_float2(tc[0], tc[1]);
-    A[pr] = f2(0.f);  // intensity blended behind the current position, per unit transmittance
-  }
-  if (threadIdx.x == 0) s_maxlast = 0;
-  __syncthreads();
-  if (lmax) atomicMax(&s_maxlast, lmax);
-  __syncthreads();
-  const int maxl = (int)s_maxlast;
-  // the longest prefix any pixel of this warp walks
-  uint32_t wl = lmax;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+  float4* const ring = warp_ring<RING>(warp);
+  uint32_t* const ring_g = ring_index<RING>(warp);
+  float4* const stage = warp_stage<RING>(warp);
+  if (A.st->code != XG_OK) return;
   uint32_t nev = 0, ncon = 0;
+  for (uint32_t item = next_item<PERSIST>(A, lane, warp, true);; item = next_item<PERSIST>(A, lane, warp, false)) {
+    if (item >= A.items) break;
+    const Item it = item_of<PPT>(A, item);
+    if (!it.ok) break;
+    const Camera cam = A.cams[it.v];
+    const int x = it.bx + (lane & 7);
+    const float bx0 = (float)it.bx, by0 = (float)it.by, by1 = by0 + (float)(4 * PPT - 1);
+    const float2 npx = f2(-fsub((float)x, cam.hw));
+    const uint2 r = A.range[(int64_t)it.v * A.range_stride + it.tile];
+    const int64_t vn_base = (int64_t)it.v * A.n;
 
-  for (int end_pos = maxl; end_pos > 0; end_pos -= kBatch) {
-    const int base = max(0, end_pos - kBatch);
-    const int cnt = end_pos - base;
-    stage_batch_pairs<kBatch>(value, rec, vn_base, r.x + base, cnt, cam, s_q, s_box, s_g);
-    for (int i = threadIdx.x; i < cnt * 8; i += blockDim.x) s_acc[i] = 0.f;
-    __syncthreads();
-    if ((uint32_t)base < wl) {
-      const int m = warp_list<kBatch>(s_q, s_box, min(cnt, (int)wl - base), bx0, by0, by1, cam, my_list, lane);
-      for (int k = m - 1; k >= 0; --k) {
-        const int j = my_list[k];
-        const float4 q0 = s_q[0][j], q1 = s_q[1][j], q2 = s_q[2][j], q3 = s_q[3][j];
+    float2 npy[NP], G[NP], Tc[NP], Ab[NP];
+    uint32_t Lp[NP][2];
+    uint32_t lmax = 0;
+#pragma unroll
+    for (int pr = 0; pr < NP; ++pr) {
+      float ny[2], g[2], tc[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int y = it.by + (lane >> 3) + 4 * (2 * pr + h);
+        ny[h] = -fsub((float)y, cam.hh);
+        g[h] = 0.f;
+        tc[h] = 1.f;
+        Lp[pr][h] = 0;
+        if ((PPT > 1 || h == 0) && x < A.W && y < A.H) {
+          const int64_t pix = ((int64_t)it.v * A.H + y) * A.W + x;
+          g[h] = A.grad_image[pix];
+          tc[h] = A.tfinal_in[pix];
+          Lp[pr][h] = g[h] != 0.f ? A.last_in[pix] : 0u;
+        }
+        lmax = max(lmax, Lp[pr][h]);
+      }
+      npy[pr] = make_float2(ny[0], ny[1]);
+      G[pr] = make_float2(g[0], g[1]);
+      Tc[pr] = make_float2(tc[0], tc[1]);
+      Ab[pr] = f2(0.f);  // intensity blended behind the current position, per unit transmittance
+    }
+    // the longest prefix any pixel of this warp walks: positions [0, wl), walked downwards;
+    // round q holds positions wl - 1 - 32 q - l for lanes l (lane 0 the highest)
+    int wl = (int)lmax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+    const int rounds = (wl + 31) / 32;
+#pragma unroll
+    for (int q = 0; q < RING - 1; ++q) {
+      const int e = wl - 1 - 32 * q - lane;
+      const uint32_t g = e >= 0 ? A.value[r.x + e] : 0u;
+      ring_g[q * 32 + lane] = g;
+      fetch_round<RING>(ring, q, lane, e >= 0, A.rec, vn_base, g);
+    }
+    int e_next = wl - 1 - 32 * (RING - 1) - lane;
+    uint32_t g_next = e_next >= 0 ? A.value[r.x + e_next] : 0u;
+    for (int q = 0; q < rounds; ++q) {
+      {
+        const int slot = (q + RING - 1) % RING;
+        ring_g[slot * 32 + lane] = g_next;
+        fetch_round<RING>(ring, slot, lane, e_next >= 0, A.rec, vn_base, g_next);
+        e_next -= 32;
+        g_next = e_next >= 0 ? A.value[r.x + e_next] : 0u;
+      }
+      copy_wait<RING - 1>();  // round q's records have landed
+      __syncwarp();
+      const int sq = q % RING;
+      const float4* slot = ring + sq * 64;
+      const int top = wl - 1 - 32 * q;  // position of lane 0's entry
+      bool hit = false;
+      if (top - lane >= 0) {
+        const float4 a = slot[2 * lane], b = slot[2 * lane + 1];
+        hit = reaches_block(a, b, bx0, by0, by1, cam);
+        if (hit) {
+          const float na = -0.5f * a.z, nb = -a.w, nc = -0.5f * b.x;
+          stage[lane] = make_float4(a.x, a.x, a.y, a.y);
+          stage[32 + lane] = make_float4(na, na, nb, nb);
+          stage[64 + lane] = make_float4(nc, nc, b.y, b.y);
+          stage[96 + lane] = make_float4(b.z, b.z, b.w, b.w);
+        }
+      }
+      uint32_t mask = __ballot_sync(0xffffffffu, hit);
+      __syncwarp();
+      while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float4 q0 = stage[k], q1 = stage[32 + k], q2 = stage[64 + k], q3 = stage[96 + k];
+        const uint32_t gk = ring_g[sq * 32 + k];
+        const uint32_t pos = (uint32_t)(top - k);
         const float2 dx = fadd2(make_float2(q0.x, q0.y), npx);
-        const uint32_t pos = (uint32_t)(base + j);
         // packed sums over the thread's pixels: six moments of dp = dL/dpower (dp, dp d,
         // dp d d^T) and dL/dintensity
         float2 gm[7];  // set by the thread's first contributing pair, then accumulated
         bool contrib = false;
 #pragma unroll
         for (int pr = 0; pr < NP; ++pr) {
-          const bool act0 = pos < L[pr][0], act1 = pos < L[pr][1];
+          const bool act0 = pos < Lp[pr][0], act1 = pos < Lp[pr][1];
           if (!(act0 || act1)) continue;
           nev += (uint32_t)act0 + (uint32_t)act1;
           const float2 dy = fadd2(make_float2(q0.z, q0.w), npy[pr]);
@@ -464,10 +515,10 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
           // alpha of the pixels that contribute, 0 for the other one
           const float2 alm = make_float2(ok0 ? al.x : 0.f, ok1 ? al.y : 0.f);
           const float2 omal = ffma2(alm, f2(-1.0f), f2(1.0f));
-          Tc[pr] = make_float2(__fdividef(Tc[pr].x, omal.x), __fdividef(Tc[pr].y, omal.y));
+          Tc[pr] = div_recover(Tc[pr], omal);
           const float2 gw = fmul2(G[pr], Tc[pr]);  // dL/dC T; gw alm is the dL/d intensity term
-          const float2 dl_dal = fmul2(gw, ffma2(A[pr], f2(-1.0f), make_float2(q3.x, q3.y)));
-          A[pr] = ffma2(alm, make_float2(q3.x, q3.y), fmul2(omal, A[pr]));
+          const float2 dl_dal = fmul2(gw, ffma2(Ab[pr], f2(-1.0f), make_float2(q3.x, q3.y)));
+          Ab[pr] = ffma2(alm, make_float2(q3.x, q3.y), fmul2(omal, Ab[pr]));
           // dp = dL/dalpha alpha where the opacity is not clamped (the clamp has zero slope)
           const float2 aln = make_float2(oe.x < kAlphaMax ? alm.x : 0.f, oe.y < kAlphaMax ? alm.y : 0.f);
           const float2 dp = fmul2(dl_dal, aln);
@@ -496,35 +547,141 @@ __global__ void __launch_bounds__(512) k_render_bwd(const uint2* __restrict__ ra
 #pragma unroll
           for (int t = 0; t < 7; ++t) gv[t] = contrib ? gm[t].x + gm[t].y : 0.f;
           gv[7] = 0.f;
-          const float sum = warp_reduce_scatter8(gv, lane);
-          const int t8 = (lane >> 2) & 7;
-          if ((lane & 3) == 0 && t8 < 7) atomicAdd(&s_acc[j * 8 + t8], sum);
+          // sums over the block's pixels: S_x, S_y, S_xx, S_xy, S_yy, S_1 of dp = dL/dpower
+          // times (d, d d^T, 1), and dL/dintensity.  power = -1/2 (a dx^2 + 2 b dx dy +
+          // c dy^2), d = u - p: dL/du = -(K (S_x, S_y)), dL/d(a, b, c) = (-S_xx / 2, -S_xy,
+          // -S_yy / 2), dL/dopacity = S_1 / opacity.
+          // lane k (k < 7) ends with the sum of term k, added to the Gaussian's moments
+          const float sum = warp_reduce_scatter8_low(gv, lane);
+          if (lane < 7) atomicAdd(A.g2d + 8 * (vn_base + gk) + lane, sum);
         }
       }
+      __syncwarp();  // the slot is refilled next round
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-      // sums over the tile's pixels: S_x, S_y, S_xx, S_xy, S_yy, S_1 of dp = dL/dpower times
-      // (d, d d^T, 1), and dL/dintensity.  power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = u - p:
-      // dL/du = -(K (S_x, S_y)), dL/d(a, b, c) = (-S_xx / 2, -S_xy, -S_yy / 2),
-      // dL/dopacity = S_1 / opacity.
-      const float4 m0 = *reinterpret_cast<const float4*>(&s_acc[j * 8]);
-      const float4 m1 = *reinterpret_cast<const float4*>(&s_acc[j * 8 + 4]);
-      if (m0.x != 0.f || m0.y != 0.f || m0.z != 0.f || m0.w != 0.f || m1.x != 0.f || m1.y != 0.f ||
-          m1.z != 0.f) {
-        const float na = s_q[1][j].x, nb = s_q[1][j].z;  // -a/2, -b
-        const float nc = s_q[2][j].x, o = s_q[2][j].z;   // -c/2, opacity
-        const float4 q0 = make_float4(2.f * na * m0.x + nb * m0.y, nb * m0.x + 2.f * nc * m0.y, -0.5f * m0.z,
-                                      -m0.w);
-        const float4 q1 = make_float4(-0.5f * m1.x, __fdividef(m1.y, o), m1.z, 0.f);
-        float4* dst = reinterpret_cast<float4*>(g2d + 8 * (vn_base + s_g[j]));
-        atomicAdd(dst, q0);
-        atomicAdd(dst + 1, q1);
-      }
-    }
-    __syncthreads();
+    copy_wait<0>();
+    __syncwarp();
   }
-  add_counts(nev, ncon, &st->bwd_evaluated, &st->bwd_contrib);
+  add_counts(nev, ncon, &A.st->bwd_evaluated, &A.st->bwd_contrib);
+}
+
+// ------------------------------------------------------------------------------------------
+// launches
+// ------------------------------------------------------------------------------------------
+namespace {
+
+template <int PPT, int RING, bool PERSIST>
+void* fn_of(bool bwd) { return bwd ? (void*)k_render_bwd<PPT, RING, PERSIST> : (void*)k_render_fwd<PPT, RING, PERSIST>; }
+
+template <int RING>
+void* kernel_ring(bool bwd, int ppt, bool persist) {
+#define XG_PICK(P) \
+  if (ppt == P) return persist ? fn_of<P, RING, true>(bwd) : fn_of<P, RING, false>(bwd);
+  XG_PICK(1) XG_PICK(2) XG_PICK(4)
+#undef XG_PICK
+  return nullptr;
+}
+
+// batch = records in flight per warp = 32 (RING - 1)
+void* kernel_of(bool bwd, int ppt, bool persist, int batch, int* ring) {
+  switch (batch) {
+    case 64: *ring = 3; return kernel_ring<3>(bwd, ppt, persist);
+    case 128: *ring = 5; return kernel_ring<5>(bwd, ppt, persist);
+    case 256: *ring = 9; return kernel_ring<9>(bwd, ppt, persist);
+    default: *ring = 17; return kernel_ring<17>(bwd, ppt, persist);
+  }
+}
+
+constexpr int kPersistWarps = 4;
+
+RenderArgs args_of(const xg_frame* f) {
+  const FramePtrs& p = f->p;
+  RenderArgs A{};
+  A.range = p.range;
+  A.order = p.order;
+  A.value = p.value;
+  A.rec = p.rec;
+  A.cams = p.cam;
+  A.st = p.status;
+  A.counter = &p.status->next_item;
+  A.n = f->n;
+  A.range_stride = (int64_t)1 << f->tile_bits;
+  A.tiles_per_view = (int)f->tiles_per_view;
+  A.tiles_x = f->tiles_x;
+  A.W = f->width;
+  A.H = f->height;
+  A.tw = f->cfg.tile_w;
+  A.th = f->cfg.tile_h;
+  const int ppt = f->cfg.pixels_per_thread;
+  A.wpt = (A.tw / 8) * (A.th / (4 * ppt));
+  A.items = (uint32_t)(f->tiles_per_view * f->n_views * A.wpt);
+  return A;
+}
+
+int ring_of(int batch) { return batch / 32 + 1; }
+
+// Dynamic shared memory of a compositing block of this configuration.
+size_t block_smem(const xg_config* cfg) {
+  const int ppt = cfg->pixels_per_thread == 0 ? 2 : cfg->pixels_per_thread;
+  const int batch = cfg->batch == 0 ? 64 : cfg->batch;
+  const int warps = cfg->persistent ? kPersistWarps : (cfg->tile_w / 8) * (cfg->tile_h / (4 * ppt));
+  return (size_t)warps * (size_t)ring_bytes_rt(ring_of(batch));
+}
+
+cudaError_t launch(xg_frame* f, bool bwd, const RenderArgs& A, cudaStream_t st) {
+  const bool persist = f->cfg.persistent != 0;
+  int ring = 0;
+  void* fn = kernel_of(bwd, f->cfg.pixels_per_thread, persist, f->cfg.batch, &ring);
+  const int warps = persist ? kPersistWarps : A.wpt;
+  unsigned grid = (unsigned)(f->tiles_per_view * f->n_views);
+  if (persist) {
+    const unsigned need = (A.items + kPersistWarps - 1) / kPersistWarps;
+    grid = std::min(need, (unsigned)f->render_blocks[bwd ? 1 : 0]);
+    const cudaError_t e = cudaMemsetAsync(A.counter, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+  }
+  void* params[] = {(void*)&A};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(warps * 32), params, block_smem(&f->cfg), st);
+}
+
+}  // namespace
+
+size_t render_smem_bytes(const xg_config* cfg) { return block_smem(cfg); }
+
+// The compositing kernels' shared-memory limit and, for the persistent form, the blocks
+// that fit on the device at once.  Called at frame creation (outside any stream capture).
+cudaError_t render_prepare(xg_frame* f) {
+  const size_t smem = block_smem(&f->cfg);
+  const bool persist = f->cfg.persistent != 0;
+  const int warps = persist ? kPersistWarps : (f->cfg.tile_w / 8) * (f->cfg.tile_h / (4 * f->cfg.pixels_per_thread));
+  for (int bwd = 0; bwd < 2; ++bwd) {
+    int ring = 0;
+    void* fn = kernel_of(bwd != 0, f->cfg.pixels_per_thread, persist, f->cfg.batch, &ring);
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)attr.maxDynamicSharedSizeBytes < smem) {
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    f->render_blocks[bwd] = 0;
+    if (persist) {
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem);
+      if (e != cudaSuccess) return e;
+      f->render_blocks[bwd] = std::max(1, per_sm) * device_sms();
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_render_fwd(xg_frame* f, float* image, uint32_t* n_contrib, cudaStream_t st) {
+  RenderArgs A = args_of(f);
+  A.image = image;
+  A.ncontrib = n_contrib;
+  A.tfinal = f->p.tfinal;
+  A.last = f->p.last;
+  Timed t(f, kRenderFwd, st);
+  return launch(f, false, A, st);
 }
 
 cudaError_t launch_render_bwd(xg_frame* f, const float* grad_image, cudaStream_t st) {
@@ -536,29 +693,13 @@ cudaError_t launch_render_bwd(xg_frame* f, const float* grad_image, cudaStream_t
     e = cudaMemsetAsync(p.grad2d, 0, sizeof(float) * 8 * (size_t)VN, st);
   }
   if (e != cudaSuccess) return e;
-  const dim3 grid((unsigned)(f->tiles_per_view * f->n_views));
+  RenderArgs A = args_of(f);
+  A.grad_image = grad_image;
+  A.tfinal_in = p.tfinal;
+  A.last_in = p.last;
+  A.g2d = p.grad2d;
   Timed t(f, kRenderBwd, st);
-  const int ppt = f->cfg.pixels_per_thread;
-  const int threads = f->cfg.tile_w * f->cfg.tile_h / ppt;
-#define XG_BWD(B, P)                                                                                            \
-  k_render_bwd<B, P><<<grid, threads, 0, st>>>(p.range, p.order, (int)f->tiles_per_view,                       \
-                                               p.value, p.rec, f->n, f->n_views,               \
-                                               f->width, f->height, f->tiles_x, (int64_t)1 << f->tile_bits,             \
-                                               f->cfg.tile_w, f->cfg.tile_h, p.cam, p.status, grad_image,      \
-                                               p.tfinal, p.last, p.grad2d)
-  switch (ppt * 1000 + f->cfg.batch) {
-    case 1064: XG_BWD(64, 1); break;
-    case 1128: XG_BWD(128, 1); break;
-    case 1256: XG_BWD(256, 1); break;
-    case 2064: XG_BWD(64, 2); break;
-    case 2128: XG_BWD(128, 2); break;
-    case 2256: XG_BWD(256, 2); break;
-    case 4064: XG_BWD(64, 4); break;
-    case 4128: XG_BWD(128, 4); break;
-    default: XG_BWD(256, 4); break;
-  }
-#undef XG_BWD
-  return cudaGetLastError();
+  return launch(f, true, A, st);
 }
 
 }  // namespace xg

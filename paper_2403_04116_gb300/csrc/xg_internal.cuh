@@ -66,7 +66,7 @@ static_assert(sizeof(Camera) == 64, "camera record is 64 bytes");
 
 struct DevStatus {
   int32_t code;
-  int32_t reserved;
+  uint32_t next_item;  // persistent compositing launches: the next work item (zeroed per launch)
   long long pairs;
   unsigned long long nonfinite;
   unsigned long long fwd_evaluated;   // (pixel, list entry) pairs evaluated by the last forward
@@ -168,8 +168,8 @@ struct FramePtrs {
   float* depth;       // [V*n]
   ushort4* rect;      // [V*n]
   uint32_t* count;    // [V*n]
-  uint32_t* ent_depth[2];  // stage-1 sort of the V*n entries (ping-pong): depth key, Gaussian
-  uint32_t* ent_gid[2];
+  uint32_t* ent_depth[2];  // stage-1 sort of the V*n entries (ping-pong): depth key, Gaussian;
+  uint32_t* ent_gid[2];    // the first pass reads `depth` and generates the Gaussian index
   uint32_t* value;    // [capacity]: Gaussian index of every pair, in (tile, view, depth) order
   uint32_t* hist;     // [radix blocks + 1][256]: per-block digit counts, then digit totals
   uint32_t* bin_hist;   // [V][J][T]: pairs of each unit of entries per tile, then their prefix
@@ -242,6 +242,7 @@ struct xg_frame {
   int32_t bin_rows;      // R: tile rows per group (R * tiles_x <= kBinGroupTiles)
   int32_t bin_groups;    // G: ceil(tiles_y / R)
   int32_t sort_blocks;   // CTAs of a radix pass (4 per SM of the device the frame was made on)
+  int32_t render_blocks[2];  // persistent compositing: blocks that fit at once (forward, backward)
   void* workspace;
   size_t workspace_bytes;
   xg_layout layout;
@@ -271,6 +272,11 @@ cudaError_t launch_project(xg_frame* f, const xg_gaussians* g, cudaStream_t st);
 cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st);
 cudaError_t launch_render_fwd(xg_frame* f, float* image, uint32_t* n_contrib, cudaStream_t st);
 cudaError_t launch_render_bwd(xg_frame* f, const float* grad_image, cudaStream_t st);
+// Dynamic shared memory of a compositing block of this configuration.
+size_t render_smem_bytes(const xg_config* cfg);
+// Shared-memory attributes and persistent grid sizes of the frame's compositing kernels
+// (frame creation; outside any stream capture).
+cudaError_t render_prepare(xg_frame* f);
 cudaError_t launch_project_bwd(xg_frame* f, const xg_gaussians* g, const xg_grads* out, cudaStream_t st);
 cudaError_t launch_loss_l1(const float* image, const float* target, int64_t count, float scale, float* grad,
                            float* loss, cudaStream_t st);
@@ -280,9 +286,12 @@ cudaError_t launch_exp_check(const float* x, float* ys, float* yp, int64_t n, cu
 // the digit (arr.in[digit_word] >> shift) & mask (mask <= 255), every segment of `geom`
 // sorted on its own.  `hist` holds (segments * per_seg + 1) * 256 words.  `f` may be NULL
 // (no timing).
+// With iota1 (WORDS == 2, digit word 0), word 1 is not read: each item's is its index within
+// its segment.
 template <int WORDS>
 cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, uint32_t mask,
-                       const SortGeom& geom, DevStatus* status, uint32_t* hist, cudaStream_t st);
+                       const SortGeom& geom, DevStatus* status, uint32_t* hist, cudaStream_t st,
+                       bool iota1 = false);
 // Sets the scatter kernels' shared-memory attributes (once per process); call outside
 // stream capture before the first radix_pass.
 cudaError_t radix_prepare();

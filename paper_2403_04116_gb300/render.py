@@ -37,8 +37,9 @@ class FrameConfig:
     tile_w: int = 16
     tile_h: int = 16
     near_mm: float = NEAR_MM
-    batch: int = 256  # Gaussians staged per round of the compositing kernels
+    batch: int = 64  # list entries whose records each compositing warp keeps in flight
     pixels_per_thread: int = 2  # pixels each compositing thread owns (1, 2 or 4)
+    persistent: int = 0  # 1: as many blocks as fit, warps taking work items from a counter
 
 
 class Frame:
@@ -65,7 +66,7 @@ class Frame:
         self.pair_capacity = int(pair_capacity)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self._c = B.XgConfig(self.cfg.tile_w, self.cfg.tile_h, self.cfg.near_mm, self.cfg.batch, self.pair_capacity,
-                             self.cfg.pixels_per_thread, self.views_per_pass)
+                             self.cfg.pixels_per_thread, self.views_per_pass, self.cfg.persistent, 0)
         nbytes = B.xg_workspace_bytes(self._c, self.n, self.n_scan, self.W, self.H)
         if nbytes == 0:
             raise ValueError("invalid frame configuration")

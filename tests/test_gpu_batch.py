@@ -123,3 +123,37 @@ def test_autotune_choice_keeps_the_image():
         s.replay()
     torch.cuda.synchronize()
     np.testing.assert_array_equal(a.image.cpu().numpy(), b.image.cpu().numpy())
+
+
+@pytest.mark.parametrize("tile,ppt", [((8, 8), 2), ((16, 16), 1), ((32, 16), 4)])
+@pytest.mark.parametrize("batch", [64, 128, 256, 512])
+def test_launch_forms_and_batches_give_identical_images(tile, ppt, batch):
+    """Persistent blocks (warps taking work items from a counter) and one block per (view,
+    tile), at every staging batch the configuration's shared memory allows: the same images
+    bit for bit as the plain one-view-per-launch form, and the same gradients up to the
+    order of float atomics."""
+    g, views, target = _scene(cid=44, V=3)
+    dev = to_device(g)
+    n = dev[4].shape[0]
+    ref_cfg = FrameConfig(8, 8, batch=64)
+    plain = PlainSteps(n, views, ref_cfg, size_pairs(n, views[:1], ref_cfg, dev, margin=2.0))
+    pgrads = tuple(torch.empty_like(t) for t in dev)
+    plain.run(dev, target, pgrads)
+    checked = 0
+    for persistent in (0, 1):
+        cfg = FrameConfig(*tile, batch=batch, pixels_per_thread=ppt, persistent=persistent)
+        try:
+            step = GraphedStep(n, views, cfg, size_pairs(n, views, cfg, dev))
+        except ValueError:
+            continue  # this batch needs more shared memory than one block has
+        step.load(dev, target)
+        step.capture()
+        step.replay()
+        torch.cuda.synchronize()
+        for v in range(len(views)):
+            np.testing.assert_array_equal(step.image[v].cpu().numpy(), plain.images[v][0].cpu().numpy())
+        for a, b in zip(step.grads, pgrads):
+            _close(a.cpu().numpy(), b.cpu().numpy())
+        checked += 1
+    if batch <= 128:
+        assert checked == 2
