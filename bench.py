@@ -74,12 +74,12 @@ FP32_LANES = 128
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels the
 # roofline line may name, from one ncu capture each (profiles/), valid only for the kernel
 # source (sha256 prefix of its .cu file and the shared header), workload and (tile_w,
-# tile_h, batch, pixels_per_thread) they were taken with.
+# tile_h, batch, pixels_per_thread, persistent) they were taken with.
 TRAFFIC = [
-    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "b9be39cdea390350",
-     "bytes_per_launch": 350.7e6},
-    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2), "source_sha": "b9be39cdea390350",
-     "bytes_per_launch": 141.1e6},
+    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "2f4c15bafbbd076a",
+     "bytes_per_launch": 353.4e6},
+    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "2f4c15bafbbd076a",
+     "bytes_per_launch": 150.1e6},
 ]
 
 
@@ -559,7 +559,7 @@ def run_ours(args) -> None:
     src = {"k_render_bwd": "render.cu", "k_render_fwd": "render.cu", "k_radix_scatter": "binning.cu",
            "k_project": "project.cu", "k_bin_scatter": "binning.cu", "k_project_bwd": "project.cu"}.get(dom)
     tr = next((t for t in TRAFFIC if t["kernel"] == dom and src and t["source_sha"] == _source_sha(src)
-               and t["workload"] == args.workload and t["config"] == (tile[0], tile[1], batch, ppt)), None)
+               and t["workload"] == args.workload and t["config"] == (tile[0], tile[1], batch, ppt, persistent)), None)
     roof["traffic"] = tr["bytes_per_launch"] if tr else None
     roof["kernel"] = dom
     roof["peak_source"] = alu_src if roof["bound"] == "alu" else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})"

@@ -38,4 +38,5 @@ def pytest_terminal_summary(terminalreporter):
     for r in GRAD_STATS:
         tr.write_line(f"{r['what']}: {r['checked']} checked, strict {r['strict_ok']} "
                       f"({100 * r['strict_frac']:.3f} %), with allowance {r['widened_ok']}, "
-                      f"max err / strict tol {r['max_err_over_strict']:.3g}")
+                      f"max err / strict tol {r['max_err_over_strict']:.3g}, "
+                      f"allowance needed {r.get('term_rel_needed', float('nan')):.2g}")

@@ -101,7 +101,9 @@ def grad_compare(got, want, mag, what: str) -> dict:
     rec = {"what": what, "checked": int(live.sum()), "strict_ok": int((err <= strict)[live].sum()),
            "widened_ok": int((err <= widened)[live].sum()),
            "max_err_over_strict": float((err / strict)[live].max(initial=0.0)),
-           "bad_widened": int((err > widened).sum())}
+           "bad_widened": int((err > widened).sum()),
+           # the smallest term allowance that would have passed every entry
+           "term_rel_needed": float(((err - strict) / np.where(mag > 0, mag, np.inf))[live].max(initial=0.0))}
     rec["strict_frac"] = rec["strict_ok"] / max(1, rec["checked"])
     GRAD_STATS.append(rec)
     return rec
@@ -110,6 +112,7 @@ def grad_compare(got, want, mag, what: str) -> dict:
 def merge_stats(recs: list, what: str) -> dict:
     out = {"what": what, "checked": sum(r["checked"] for r in recs), "strict_ok": sum(r["strict_ok"] for r in recs),
            "widened_ok": sum(r["widened_ok"] for r in recs), "bad_widened": sum(r["bad_widened"] for r in recs),
-           "max_err_over_strict": max((r["max_err_over_strict"] for r in recs), default=0.0)}
+           "max_err_over_strict": max((r["max_err_over_strict"] for r in recs), default=0.0),
+           "term_rel_needed": max((r.get("term_rel_needed", 0.0) for r in recs), default=0.0)}
     out["strict_frac"] = out["strict_ok"] / max(1, out["checked"])
     return out
