@@ -701,11 +701,12 @@ def _algo_bytes(kernel: str, n: int, VN: int, M: int, entry_passes: int) -> floa
     """Algorithmic DRAM bytes of one step's launches of a memory-bound kernel (each input
     read once, each output written once): projection reads the 48-byte Gaussian and writes
     a 48-byte (record, depth, rectangle, count) per (view, Gaussian); the entry sort moves 2
-    words in and out per pass; the binning kernels read each sorted entry's index, count and
-    rectangle (16 B) and the scatter writes one 4-byte index per pair."""
+    words in and out per pass; the counting pass reads each sorted entry's index, count and
+    rectangle (16 B) and writes the rectangle in entry order (8 B), which the scatter reads
+    with the index (12 B) before writing one 4-byte index per pair."""
     return {"k_radix_scatter": 16 * VN * entry_passes, "k_radix_hist": 4 * VN * entry_passes,
             "k_project": 48 * n + 48 * VN, "k_project_bwd": 32 * VN + 56 * n,
-            "k_bin_count": 16 * VN, "k_bin_scatter": 16 * VN + 4 * M}.get(kernel, 0)
+            "k_bin_count": 24 * VN, "k_bin_scatter": 12 * VN + 4 * M}.get(kernel, 0)
 
 
 def run_scan(args) -> None:

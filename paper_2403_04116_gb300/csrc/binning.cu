@@ -347,13 +347,14 @@ __device__ __forceinline__ BinWork bin_work(const BinGeom& g) {
   return w;
 }
 
-// Sorted entry i's Gaussian and its tile rectangle clipped to the CTA's rows; false if it
-// touches none of them.  A Gaussian index >= n or a rectangle outside the tile grid (which
-// a correct projection and stage 1 never produce) records XG_ERR_CHECK and is skipped.
-__device__ __forceinline__ bool entry_rect(const BinGeom& g, const BinWork& w, int64_t i,
-                                           const uint32_t* __restrict__ ent_gid, const uint32_t* __restrict__ count,
-                                           const ushort4* __restrict__ rect, DevStatus* __restrict__ st,
-                                           uint32_t& gid, int& x0, int& x1, int& ya, int& yb) {
+// Sorted entry i's Gaussian and its whole tile rectangle (rows not clipped); false if the
+// Gaussian touches no tile, or (recording XG_ERR_CHECK) if its index or rectangle is out of
+// range.
+__device__ __forceinline__ bool entry_full_rect(const BinGeom& g, const BinWork& w, int64_t i,
+                                                const uint32_t* __restrict__ ent_gid,
+                                                const uint32_t* __restrict__ count, const ushort4* __restrict__ rect,
+                                                DevStatus* __restrict__ st, uint32_t& gid, int& x0, int& x1, int& y0,
+                                                int& y1) {
   gid = ent_gid[i];
   if (gid >= g.n) {
     st->code = XG_ERR_CHECK;
@@ -368,9 +369,9 @@ __device__ __forceinline__ bool entry_rect(const BinGeom& g, const BinWork& w, i
   }
   x0 = r.x;
   x1 = r.z;
-  ya = max((int)r.y, w.r0);
-  yb = min((int)r.w, w.r0 + w.rows - 1);
-  return ya <= yb;
+  y0 = r.y;
+  y1 = r.w;
+  return true;
 }
 
 // (R + 1) x (tiles_x + 1) words, R * tiles_x <= max(kBinGroupTiles, tiles_x), R and tiles_x <= 512
@@ -379,11 +380,17 @@ constexpr int kBinDiffWords = kBinGroupTiles + 2 * 512 + 1;
 // Stage 2: pairs per tile of one unit (and group of rows).  Every entry adds its rectangle
 // to a 2-D difference array in four shared atomics; prefix sums along the rows and then
 // down the columns turn it into the count of every tile.
+//
+// The CTAs of the first group also write every sorted entry's tile rectangle in entry order
+// (columns x0 | x1 << 16 in ent_x, rows y0 | y1 << 16 in ent_y; ent_y = 1 (y0 > y1) for an
+// entry with no tile), so that the pair scatter reads them sequentially instead of
+// gathering them by Gaussian index again.
 __global__ void __launch_bounds__(kBinThreads) k_bin_count(BinGeom g, const uint32_t* __restrict__ ent_gid,
                                                            const uint32_t* __restrict__ count,
                                                            const ushort4* __restrict__ rect,
                                                            DevStatus* __restrict__ st,
-                                                           uint32_t* __restrict__ bin_hist) {
+                                                           uint32_t* __restrict__ bin_hist,
+                                                           uint32_t* __restrict__ ent_x, uint32_t* __restrict__ ent_y) {
   __shared__ int32_t s_d[kBinDiffWords];
   if (st->code != XG_OK) return;  // stage 1 failed a check: its entries are not to be read
   const BinWork w = bin_work(g);
@@ -391,10 +398,19 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(BinGeom g, const uint
   const int cells = (w.rows + 1) * cols;
   for (int k = threadIdx.x; k < cells; k += kBinThreads) s_d[k] = 0;
   __syncthreads();
+  const bool writer = w.r0 == 0;  // the first group writes the sorted rectangles
   for (int64_t i = w.beg + threadIdx.x; i < w.end; i += kBinThreads) {
     uint32_t gid;
     int x0, x1, ya, yb;
-    if (!entry_rect(g, w, i, ent_gid, count, rect, st, gid, x0, x1, ya, yb)) continue;
+    const bool any = entry_full_rect(g, w, i, ent_gid, count, rect, st, gid, x0, x1, ya, yb);
+    if (writer) {
+      ent_x[i] = any ? (uint32_t)x0 | (uint32_t)x1 << 16 : 0u;
+      ent_y[i] = any ? (uint32_t)ya | (uint32_t)yb << 16 : 1u;
+    }
+    if (!any) continue;
+    ya = max(ya, w.r0);
+    yb = min(yb, w.r0 + w.rows - 1);
+    if (ya > yb) continue;
     const int a = (ya - w.r0) * cols, b = (yb - w.r0 + 1) * cols;
     atomicAdd(&s_d[a + x0], 1);
     atomicAdd(&s_d[a + x1 + 1], -1);
@@ -512,14 +528,20 @@ __global__ void __launch_bounds__(1024) k_bin_base(BinGeom g, int64_t capacity, 
   }
 }
 
-// One staged entry: (x0 | x1 << 16, ya | yb << 16), or ya > yb when it has no tile here.
-__device__ __forceinline__ uint2 stage_entry(const BinGeom& g, const BinWork& w, int64_t i,
-                                             const uint32_t* __restrict__ ent_gid, const uint32_t* __restrict__ count,
-                                             const ushort4* __restrict__ rect, DevStatus* __restrict__ st,
+// One staged entry: (x0 | x1 << 16, ya | yb << 16) with the rows clipped to the CTA's group,
+// or ya > yb when it has no tile here; read in entry order from the rectangles the counting
+// pass wrote (already checked there).
+__device__ __forceinline__ uint2 stage_entry(const BinWork& w, int64_t i, const uint32_t* __restrict__ ent_gid,
+                                             const uint32_t* __restrict__ ent_x, const uint32_t* __restrict__ ent_y,
                                              uint32_t& gid) {
-  int x0, x1, ya, yb;
-  if (i < w.end && entry_rect(g, w, i, ent_gid, count, rect, st, gid, x0, x1, ya, yb))
-    return make_uint2((uint32_t)x0 | (uint32_t)x1 << 16, (uint32_t)ya | (uint32_t)yb << 16);
+  if (i < w.end) {
+    const uint32_t ey = ent_y[i];
+    const int ya = max((int)(ey & 0xffffu), w.r0), yb = min((int)(ey >> 16), w.r0 + w.rows - 1);
+    if (ya <= yb) {
+      gid = ent_gid[i];
+      return make_uint2(ent_x[i], (uint32_t)ya | (uint32_t)yb << 16);
+    }
+  }
   gid = 0u;
   return make_uint2(0u, 1u);
 }
@@ -548,8 +570,8 @@ __host__ __device__ __forceinline__ int bin_padded(int tiles) { return tiles + (
 
 template <bool kMaskRank>
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const uint32_t* __restrict__ ent_gid,
-                                                             const uint32_t* __restrict__ count,
-                                                             const ushort4* __restrict__ rect,
+                                                             const uint32_t* __restrict__ ent_x,
+                                                             const uint32_t* __restrict__ ent_y,
                                                              const uint32_t* __restrict__ bin_hist,
                                                              const uint2* __restrict__ range,
                                                              DevStatus* __restrict__ st, uint32_t* __restrict__ value) {
@@ -588,7 +610,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
   uint32_t gid_next = 0u;
   uint2 ent_next = make_uint2(0u, 1u);
   if (stager) {
-    ent_next = stage_entry(g, w, w.beg + threadIdx.x, ent_gid, count, rect, st, gid_next);
+    ent_next = stage_entry(w, w.beg + threadIdx.x, ent_gid, ent_x, ent_y, gid_next);
     s_ent[0][threadIdx.x] = ent_next;
     s_gid[0][threadIdx.x] = gid_next;
   }
@@ -597,7 +619,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
   for (int64_t blk = w.beg; blk < w.end; blk += kBinStage, buf ^= 1) {
     const bool more = blk + kBinStage < w.end;
     if (more && stager)
-      ent_next = stage_entry(g, w, blk + kBinStage + threadIdx.x, ent_gid, count, rect, st, gid_next);
+      ent_next = stage_entry(w, blk + kBinStage + threadIdx.x, ent_gid, ent_x, ent_y, gid_next);
     for (int sub = 0; sub < kBinStage / 32; ++sub) {
       const uint2 e = s_ent[buf][sub * 32 + lane];
       const int x0 = (int)(e.x & 0xffffu), x1 = (int)(e.x >> 16), ya = (int)(e.y & 0xffffu), yb = (int)(e.y >> 16);
@@ -858,13 +880,16 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     cur ^= 1;
   }
   const uint32_t* ent_gid = p.ent_gid[cur];
+  // the sort's other ping-pong planes are free now: the sorted tile rectangles go there
+  uint32_t* ent_x = p.ent_depth[cur ^ 1];
+  uint32_t* ent_y = p.ent_gid[cur ^ 1];
   // stages 2-4: counts per unit and tile, their prefixes and the ranges, the pairs
   const BinGeom g = {f->n, f->tiles_per_view, f->n_views, f->tiles_x, f->tiles_y, f->tile_bits,
                      f->bin_unit, f->bin_units, f->bin_rows, f->bin_groups};
   const unsigned ctas = (unsigned)((int64_t)f->n_views * f->bin_units * f->bin_groups);
   {
     Timed t(f, kBinCount, st);
-    k_bin_count<<<ctas, kBinThreads, 0, st>>>(g, ent_gid, p.count, p.rect, p.status, p.bin_hist);
+    k_bin_count<<<ctas, kBinThreads, 0, st>>>(g, ent_gid, p.count, p.rect, p.status, p.bin_hist, ent_x, ent_y);
   }
   {
     Timed t(f, kBinColscan, st);
@@ -880,10 +905,10 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     const int group_tiles = f->bin_rows * f->tiles_x;
     if (group_tiles > kBinMaskRankTiles)
       k_bin_scatter<true><<<ctas, kBinThreads, bin_scatter_smem(group_tiles), st>>>(
-          g, ent_gid, p.count, p.rect, p.bin_hist, p.range, p.status, p.value);
+          g, ent_gid, ent_x, ent_y, p.bin_hist, p.range, p.status, p.value);
     else
       k_bin_scatter<false><<<ctas, kBinThreads, bin_scatter_smem(group_tiles), st>>>(
-          g, ent_gid, p.count, p.rect, p.bin_hist, p.range, p.status, p.value);
+          g, ent_gid, ent_x, ent_y, p.bin_hist, p.range, p.status, p.value);
   }
   {
     Timed t(f, kWorkOrder, st);

@@ -29,8 +29,10 @@
 // step and one residual correction of the quotient (Markstein's scheme for correctly
 // rounded division, here without the special cases that cannot occur).  The round's
 // entries that reach the block are first written in a duplicated form (one broadcast load
-// gives both lanes of a packed operand).  Per walked entry, a warp with contributing pixels
-// sums its 7 per-pixel terms -- six moments of dL/dpower (S_1, S_x, S_y, S_xx, S_xy, S_yy
+// gives both lanes of a packed operand).  Per walked entry every lane runs the same
+// branch-free sequence: a pixel that does not take the entry gets alpha = 0, which leaves
+// its state and terms exactly unchanged.  A warp with contributing pixels then sums its 7
+// per-pixel terms -- six moments of dL/dpower (S_1, S_x, S_y, S_xx, S_xy, S_yy
 // over the pixel offsets d = u - p) and the intensity term -- with an 8-value
 // reduce-scatter butterfly (9 shuffles; lane k ends with the sum of term k), and lanes 0-6
 // add them to the (view, Gaussian)'s sums in global memory in one atomic instruction.  The
@@ -493,26 +495,36 @@ __global__ void __launch_bounds__(512) k_render_bwd(const RenderArgs A) {
         const uint32_t gk = ring_g[sq * 32 + k];
         const uint32_t pos = (uint32_t)(top - k);
         const float2 dx = fadd2(make_float2(q0.x, q0.y), npx);
-        // packed sums over the thread's pixels: six moments of dp = dL/dpower (dp, dp d,
-        // dp d d^T) and dL/dintensity
-        float2 gm[7];  // set by the thread's first contributing pair, then accumulated
-        bool contrib = false;
+        // the exponent of every pixel pair; a pixel that is not walking this entry, whose
+        // exponent is below the threshold, or whose opacity stays under 1/255 takes
+        // alpha = 0 below, which leaves its transmittance, blended-behind intensity and
+        // every term unchanged (exactly: division by 1, products with 0)
+        float2 p[NP], dyv[NP];
+        bool in[NP][2];
+        bool any_in = false;
 #pragma unroll
         for (int pr = 0; pr < NP; ++pr) {
           const bool act0 = pos < Lp[pr][0], act1 = pos < Lp[pr][1];
-          if (!(act0 || act1)) continue;
           nev += (uint32_t)act0 + (uint32_t)act1;
-          const float2 dy = fadd2(make_float2(q0.z, q0.w), npy[pr]);
-          const float2 t = ffma2(make_float2(q1.x, q1.y), dx, fmul2(make_float2(q1.z, q1.w), dy));
-          const float2 p = ffma2(dx, t, fmul2(fmul2(make_float2(q2.x, q2.y), dy), dy));
-          const bool in0 = act0 && !(p.x < q3.z), in1 = act1 && !(p.y < q3.z);
-          if (!(in0 || in1)) continue;
-          const float2 oe = fmul2(make_float2(q2.z, q2.w), xg_exp2v(p));
+          dyv[pr] = fadd2(make_float2(q0.z, q0.w), npy[pr]);
+          const float2 t = ffma2(make_float2(q1.x, q1.y), dx, fmul2(make_float2(q1.z, q1.w), dyv[pr]));
+          p[pr] = ffma2(dx, t, fmul2(fmul2(make_float2(q2.x, q2.y), dyv[pr]), dyv[pr]));
+          in[pr][0] = act0 && !(p[pr].x < q3.z);
+          in[pr][1] = act1 && !(p[pr].y < q3.z);
+          any_in |= in[pr][0] || in[pr][1];
+        }
+        if (!__any_sync(0xffffffffu, any_in)) continue;  // no pixel of the warp can reach 1/255
+        // packed sums over the thread's pixels: six moments of dp = dL/dpower (dp, dp d,
+        // dp d d^T) and dL/dintensity
+        float2 gm[7];
+        bool any_ok = false;
+#pragma unroll
+        for (int pr = 0; pr < NP; ++pr) {
+          const float2 oe = fmul2(make_float2(q2.z, q2.w), xg_exp2v(p[pr]));
           const float2 al = make_float2(fminf(kAlphaMax, oe.x), fminf(kAlphaMax, oe.y));
-          const bool ok0 = in0 && !(al.x < kAlphaMin), ok1 = in1 && !(al.y < kAlphaMin);
-          if (!(ok0 || ok1)) continue;
+          const bool ok0 = in[pr][0] && !(al.x < kAlphaMin), ok1 = in[pr][1] && !(al.y < kAlphaMin);
+          any_ok |= ok0 || ok1;
           ncon += (uint32_t)ok0 + (uint32_t)ok1;
-          // alpha of the pixels that contribute, 0 for the other one
           const float2 alm = make_float2(ok0 ? al.x : 0.f, ok1 ? al.y : 0.f);
           const float2 omal = ffma2(alm, f2(-1.0f), f2(1.0f));
           Tc[pr] = div_recover(Tc[pr], omal);
@@ -522,36 +534,33 @@ __global__ void __launch_bounds__(512) k_render_bwd(const RenderArgs A) {
           // dp = dL/dalpha alpha where the opacity is not clamped (the clamp has zero slope)
           const float2 aln = make_float2(oe.x < kAlphaMax ? alm.x : 0.f, oe.y < kAlphaMax ? alm.y : 0.f);
           const float2 dp = fmul2(dl_dal, aln);
-          const float2 sx = fmul2(dp, dx), sy = fmul2(dp, dy);
-          if (!contrib) {
+          const float2 sx = fmul2(dp, dx), sy = fmul2(dp, dyv[pr]);
+          if (pr == 0) {
             gm[0] = sx;
             gm[1] = sy;
             gm[2] = fmul2(sx, dx);
-            gm[3] = fmul2(sx, dy);
-            gm[4] = fmul2(sy, dy);
+            gm[3] = fmul2(sx, dyv[pr]);
+            gm[4] = fmul2(sy, dyv[pr]);
             gm[5] = dp;
             gm[6] = fmul2(gw, alm);
-            contrib = true;
           } else {
             gm[0] = fadd2(gm[0], sx);
             gm[1] = fadd2(gm[1], sy);
             gm[2] = ffma2(sx, dx, gm[2]);
-            gm[3] = ffma2(sx, dy, gm[3]);
-            gm[4] = ffma2(sy, dy, gm[4]);
+            gm[3] = ffma2(sx, dyv[pr], gm[3]);
+            gm[4] = ffma2(sy, dyv[pr], gm[4]);
             gm[5] = fadd2(gm[5], dp);
             gm[6] = ffma2(gw, alm, gm[6]);
           }
         }
-        if (__any_sync(0xffffffffu, contrib)) {
+        if (__any_sync(0xffffffffu, any_ok)) {
           float gv[8];
 #pragma unroll
-          for (int t = 0; t < 7; ++t) gv[t] = contrib ? gm[t].x + gm[t].y : 0.f;
+          for (int t = 0; t < 7; ++t) gv[t] = gm[t].x + gm[t].y;
           gv[7] = 0.f;
           // sums over the block's pixels: S_x, S_y, S_xx, S_xy, S_yy, S_1 of dp = dL/dpower
-          // times (d, d d^T, 1), and dL/dintensity.  power = -1/2 (a dx^2 + 2 b dx dy +
-          // c dy^2), d = u - p: dL/du = -(K (S_x, S_y)), dL/d(a, b, c) = (-S_xx / 2, -S_xy,
-          // -S_yy / 2), dL/dopacity = S_1 / opacity.
-          // lane k (k < 7) ends with the sum of term k, added to the Gaussian's moments
+          // times (d, d d^T, 1), and dL/dintensity; lane k (k < 7) ends with the sum of term
+          // k, added to the Gaussian's sums
           const float sum = warp_reduce_scatter8_low(gv, lane);
           if (lane < 7) atomicAdd(A.g2d + 8 * (vn_base + gk) + lane, sum);
         }

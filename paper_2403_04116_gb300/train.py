@@ -383,7 +383,7 @@ def main() -> None:
     ap.add_argument("--gaussians", type=int, default=200_000)
     ap.add_argument("--detector", type=int, default=512)
     ap.add_argument("--views-per-step", type=int, default=8)
-    ap.add_argument("--tile", default="16x16:128:2")
+    ap.add_argument("--tile", default="16x16:64:2")
     ap.add_argument("--init", choices=["uniform", "acui"], default="uniform")
     ap.add_argument("--acui-grid", type=int, default=256, help="voxels per axis M of Eq. 13")
     ap.add_argument("--acui-interval", type=float, default=8.0, help="sampling interval d of Eq. 13")
