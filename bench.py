@@ -76,9 +76,9 @@ FP32_LANES = 128
 # source (sha256 prefix of its .cu file and the shared header), workload and (tile_w,
 # tile_h, batch, pixels_per_thread, persistent) they were taken with.
 TRAFFIC = [
-    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "2f4c15bafbbd076a",
-     "bytes_per_launch": 353.4e6},
-    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "2f4c15bafbbd076a",
+    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "17aa407f367636bc",
+     "bytes_per_launch": 359.8e6},
+    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "17aa407f367636bc",
      "bytes_per_launch": 150.1e6},
 ]
 
