@@ -550,10 +550,13 @@ __device__ __forceinline__ uint2 stage_entry(const BinWork& w, int64_t i, const 
 // position in shared memory (range start + the unit's prefix).  Blocks of kBinStage entries
 // are staged in shared memory (the next block's loads are in flight while one is processed);
 // warp w walks every entry of the block in order, but only over the tile rows r0 + w,
-// r0 + w + 8, ... of its rectangle, 32 pairs at a time.  Two pairs of one round on the same
-// tile come from different entries and are ranked in lane (= entry) order, by a per-tile
-// lane mask built with shared atomics (kMaskRank; cheaper on large dense groups, whose full
-// rounds hold 32 distinct tiles) or by match_any (cheaper on small groups).
+// r0 + w + 8, ... of its rectangle, 32 pairs at a time.  A pass of the warp takes K
+// consecutive entries per lane (32 K of the block): a warp scan of the lanes' pair counts
+// places them, the entries with pairs are compacted in order, and a round finds each lane's
+// entry by an OR-reduction over the round's entry starts.  Two pairs of one round on the
+// same tile come from different entries and are ranked in lane (= entry) order, by a
+// per-tile lane mask built with shared atomics (kMaskRank; cheaper on large dense groups,
+// whose full rounds hold 32 distinct tiles) or by match_any (cheaper on small groups).
 //
 // Stores are combined per kSlots values (16 bytes) of the output: a tile's values wait in a
 // kSlots-entry shared buffer (slot = position mod kSlots) until the run of kSlots is
@@ -564,11 +567,17 @@ constexpr uint32_t kNoValue = 0xffffffffu;
 constexpr uint32_t kSlots = 4;
 constexpr int kBinStage = 256;  // sorted entries staged per block (one per thread)
 constexpr int kBinMaskRankTiles = 1024;  // groups above this many tiles rank by lane mask
+// entries per lane in a warp's pass over the staged block: more entries give fuller rounds
+// and fewer passes (the measured best: 2 on the large mask-ranked groups, 4 on the others)
+constexpr int kMaskRankLaneEntries = 2;
+constexpr int kMatchLaneEntries = 4;
+static_assert(kBinStage % (32 * kMaskRankLaneEntries) == 0 && kBinStage % (32 * kMatchLaneEntries) == 0,
+              "a staged block holds whole passes");
 
 // Words of a per-tile shared array of `tiles` tiles padded by one word every 32 tiles.
 __host__ __device__ __forceinline__ int bin_padded(int tiles) { return tiles + (tiles >> 5) + 1; }
 
-template <bool kMaskRank>
+template <bool kMaskRank, int K>
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const uint32_t* __restrict__ ent_gid,
                                                              const uint32_t* __restrict__ ent_x,
                                                              const uint32_t* __restrict__ ent_y,
@@ -586,7 +595,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
   uint32_t* const s_buf = s_dyn + 2 * npad;
   __shared__ uint2 s_ent[2][kBinStage];
   __shared__ uint32_t s_gid[2][kBinStage];
-  __shared__ uint4 s_cmp[kW][32];  // per warp: its entries with pairs, compacted (prefix, packed, 1/width, Gaussian)
+  __shared__ uint4 s_cmp[kW][32 * K];  // per warp: its entries with pairs, compacted (prefix, packed, 1/width, Gaussian)
   if (st->code != XG_OK) return;
   const int64_t pairs = st->pairs;
   const BinWork w = bin_work(g);
@@ -620,28 +629,46 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
     const bool more = blk + kBinStage < w.end;
     if (more && stager)
       ent_next = stage_entry(w, blk + kBinStage + threadIdx.x, ent_gid, ent_x, ent_y, gid_next);
-    for (int sub = 0; sub < kBinStage / 32; ++sub) {
-      const uint2 e = s_ent[buf][sub * 32 + lane];
-      const int x0 = (int)(e.x & 0xffffu), x1 = (int)(e.x >> 16), ya = (int)(e.y & 0xffffu), yb = (int)(e.y >> 16);
-      const int yf = ya + ((warp - (ya - w.r0)) & (kW - 1));  // this warp's first row at or after ya
-      const uint32_t wdt = (uint32_t)(x1 - x0 + 1);
-      const uint32_t cnt = yf <= yb ? ((uint32_t)(yb - yf) / kW + 1u) * wdt : 0u;
-      uint32_t incl = cnt;
+    for (int sub = 0; sub < kBinStage / (32 * K); ++sub) {
+      // lane l takes the staged entries sub*32K + l*K + k, k < K (consecutive: the prefix
+      // over the warp's pairs is a warp scan of the lanes' sums)
+      uint32_t cnt[K], pre[K], pk[K], rcp[K], gk[K];
+      uint32_t lsum = 0u, nh = 0u;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int ix = sub * 32 * K + lane * K + k;
+        const uint2 e = s_ent[buf][ix];
+        const int x0 = (int)(e.x & 0xffffu), x1 = (int)(e.x >> 16), ya = (int)(e.y & 0xffffu), yb = (int)(e.y >> 16);
+        const int yf = ya + ((warp - (ya - w.r0)) & (kW - 1));  // this warp's first row at or after ya
+        const uint32_t wdt = (uint32_t)(x1 - x0 + 1);
+        cnt[k] = yf <= yb ? ((uint32_t)(yb - yf) / kW + 1u) * wdt : 0u;
+        pre[k] = lsum;
+        lsum += cnt[k];
+        nh += cnt[k] > 0u ? 1u : 0u;
+        pk[k] = (uint32_t)(yf - w.r0) | (uint32_t)x0 << 10 | (wdt - 1u) << 20;
+        rcp[k] = __float_as_uint(__frcp_rn((float)wdt));
+        gk[k] = s_gid[buf][ix];
+      }
+      uint32_t incl = lsum, hincl = nh;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += y;
+        const uint32_t yh = __shfl_up_sync(0xffffffffu, hincl, d);
+        if (lane >= d) {
+          incl += y;
+          hincl += yh;
+        }
       }
-      const uint32_t pre = incl - cnt;
       const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
       if (tot == 0u) continue;
       // the entries with pairs, compacted in order: entry c's pairs are [pre_c, pre_c + cnt_c)
       {
-        const uint32_t has = __ballot_sync(0xffffffffu, cnt > 0u);
-        if (cnt > 0u)  // local first row, first column and width - 1 (each < 512) in one word
-          s_cmp[warp][__popc(has & lt_mask)] =
-              make_uint4(pre, (uint32_t)(yf - w.r0) | (uint32_t)x0 << 10 | (wdt - 1u) << 20,
-                         __float_as_uint(__frcp_rn((float)wdt)), s_gid[buf][sub * 32 + lane]);
+        uint32_t hb = hincl - nh;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          pre[k] += incl - lsum;
+          if (cnt[k] > 0u) s_cmp[warp][hb++] = make_uint4(pre[k], pk[k], rcp[k], gk[k]);
+        }
         __syncwarp();
       }
       int last = -1;  // compacted entry holding the position before the round
@@ -649,8 +676,10 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
         const uint32_t p = p0 + lane;
         // the round's entry starts as a bit mask over its positions; a lane's entry is the
         // previous round's last one plus the starts at or before its position
-        const uint32_t starts =
-            __reduce_or_sync(0xffffffffu, cnt > 0u && pre - p0 < 32u ? 1u << (pre - p0) : 0u);
+        uint32_t bits = 0u;
+#pragma unroll
+        for (int k = 0; k < K; ++k) bits |= cnt[k] > 0u && pre[k] - p0 < 32u ? 1u << (pre[k] - p0) : 0u;
+        const uint32_t starts = __reduce_or_sync(0xffffffffu, bits);
         const int ei = last + __popc(starts & (0xffffffffu >> (31 - lane)));
         last = __shfl_sync(0xffffffffu, ei, 31);
         const uint4 ce = s_cmp[warp][ei];
@@ -808,7 +837,8 @@ size_t bin_scatter_smem(int group_tiles) { return (size_t)(kSlots + 2) * 4 * (si
 cudaError_t radix_prepare() {
   static cudaError_t once = [] {
     cudaError_t e = cudaSuccess;
-    for (const void* k : {(const void*)k_bin_scatter<true>, (const void*)k_bin_scatter<false>})
+    for (const void* k : {(const void*)k_bin_scatter<true, kMaskRankLaneEntries>,
+                          (const void*)k_bin_scatter<false, kMatchLaneEntries>})
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_scatter_smem(kBinGroupTiles));
     if (e == cudaSuccess) e = scatter_attrs<2, 0, false>();
@@ -904,10 +934,10 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     Timed t(f, kBinScatter, st);
     const int group_tiles = f->bin_rows * f->tiles_x;
     if (group_tiles > kBinMaskRankTiles)
-      k_bin_scatter<true><<<ctas, kBinThreads, bin_scatter_smem(group_tiles), st>>>(
+      k_bin_scatter<true, kMaskRankLaneEntries><<<ctas, kBinThreads, bin_scatter_smem(group_tiles), st>>>(
           g, ent_gid, ent_x, ent_y, p.bin_hist, p.range, p.status, p.value);
     else
-      k_bin_scatter<false><<<ctas, kBinThreads, bin_scatter_smem(group_tiles), st>>>(
+      k_bin_scatter<false, kMatchLaneEntries><<<ctas, kBinThreads, bin_scatter_smem(group_tiles), st>>>(
           g, ent_gid, ent_x, ent_y, p.bin_hist, p.range, p.status, p.value);
   }
   {

@@ -8,6 +8,9 @@ laid out in (tile, view) order):
 * Gaussian counts that are not a multiple of 4, so the sorted entries of every view after
   the first start off a 16-byte boundary (the radix scatter loads those chunks directly
   instead of by bulk copy), and views cut into many units of sorted entries;
+* Gaussians as large as the scene (a fifth to a half of its side): most cover hundreds of
+  the 1,024 tiles of a view, so the pair scatter takes every unit's entries in many chunks
+  of a few entries each;
 * a scan whose last pass has fewer views but more radix blocks than a full pass: 36 views,
   19 per pass (608 blocks) and a last pass of 17 (612 blocks); every view equals the same
   view rendered by a frame of its own, and the last one equals the replica.
@@ -60,6 +63,21 @@ def test_large_tile_grids_bit_exact(name):
     for v, r in enumerate(reps):
         np.testing.assert_array_equal(gpu["image"][v].view(np.uint32), r["image"].view(np.uint32))
         np.testing.assert_array_equal(gpu["last"][v].view(np.uint32), r["last"])
+
+
+def test_scene_sized_gaussians_bit_exact():
+    n, V, W, tile, cid = 2_001, 2, 256, (8, 8), 24
+    g = synth.gaussians(n, synth.scene_side_mm(W), synth.rng(cid, 0), log_scale=(-1.6, -0.7))
+    views = synth.circular_views(V, W, W, first_rad=0.3)
+    gpu = run_forward(g, views, tile)
+    reps, idx = _expected_index(g, views, tile)
+    assert gpu["status"].code == B.XG_OK
+    assert gpu["M"] == idx["M"] > 300 * n * V  # hundreds of tiles per Gaussian on average
+    np.testing.assert_array_equal(gpu["key_tile"], idx["key_tile"])
+    np.testing.assert_array_equal(gpu["value"], idx["value"])
+    np.testing.assert_array_equal(gpu["range"], idx["range"])
+    for v, r in enumerate(reps):
+        np.testing.assert_array_equal(gpu["image"][v].view(np.uint32), r["image"].view(np.uint32))
 
 
 def test_ragged_pass_with_more_radix_blocks():
