@@ -574,6 +574,21 @@ constexpr int kMatchLaneEntries = 4;
 static_assert(kBinStage % (32 * kMaskRankLaneEntries) == 0 && kBinStage % (32 * kMatchLaneEntries) == 0,
               "a staged block holds whole passes");
 
+// K consecutive words from shared memory in one vector load (the address is K-word aligned).
+template <int K>
+__device__ __forceinline__ void load_words(const uint32_t* src, uint32_t (&out)[K]) {
+  if constexpr (K == 4) {
+    const uint4 v = *reinterpret_cast<const uint4*>(src);
+    out[0] = v.x, out[1] = v.y, out[2] = v.z, out[3] = v.w;
+  } else if constexpr (K == 2) {
+    const uint2 v = *reinterpret_cast<const uint2*>(src);
+    out[0] = v.x, out[1] = v.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = src[k];
+  }
+}
+
 // Words of a per-tile shared array of `tiles` tiles padded by one word every 32 tiles.
 __host__ __device__ __forceinline__ int bin_padded(int tiles) { return tiles + (tiles >> 5) + 1; }
 
@@ -593,8 +608,10 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
   uint32_t* const s_pos = s_dyn;
   uint32_t* const s_mask = s_dyn + npad;
   uint32_t* const s_buf = s_dyn + 2 * npad;
-  __shared__ uint2 s_ent[2][kBinStage];
-  __shared__ uint32_t s_gid[2][kBinStage];
+  // staged entries, one plane per word (a lane's K consecutive entries are one vector load)
+  __shared__ __align__(16) uint32_t s_ex[2][kBinStage];
+  __shared__ __align__(16) uint32_t s_ey[2][kBinStage];
+  __shared__ __align__(16) uint32_t s_gid[2][kBinStage];
   __shared__ uint4 s_cmp[kW][32 * K];  // per warp: its entries with pairs, compacted (prefix, packed, 1/width, Gaussian)
   if (st->code != XG_OK) return;
   const int64_t pairs = st->pairs;
@@ -620,7 +637,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
   uint2 ent_next = make_uint2(0u, 1u);
   if (stager) {
     ent_next = stage_entry(w, w.beg + threadIdx.x, ent_gid, ent_x, ent_y, gid_next);
-    s_ent[0][threadIdx.x] = ent_next;
+    s_ex[0][threadIdx.x] = ent_next.x;
+    s_ey[0][threadIdx.x] = ent_next.y;
     s_gid[0][threadIdx.x] = gid_next;
   }
   __syncthreads();
@@ -632,13 +650,16 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
     for (int sub = 0; sub < kBinStage / (32 * K); ++sub) {
       // lane l takes the staged entries sub*32K + l*K + k, k < K (consecutive: the prefix
       // over the warp's pairs is a warp scan of the lanes' sums)
-      uint32_t cnt[K], pre[K], pk[K], rcp[K], gk[K];
+      uint32_t cnt[K], pre[K], pk[K], rcp[K], gk[K], ex[K], ey[K];
       uint32_t lsum = 0u, nh = 0u;
+      const int ix0 = sub * 32 * K + lane * K;
+      load_words<K>(&s_ex[buf][ix0], ex);
+      load_words<K>(&s_ey[buf][ix0], ey);
+      load_words<K>(&s_gid[buf][ix0], gk);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const int ix = sub * 32 * K + lane * K + k;
-        const uint2 e = s_ent[buf][ix];
-        const int x0 = (int)(e.x & 0xffffu), x1 = (int)(e.x >> 16), ya = (int)(e.y & 0xffffu), yb = (int)(e.y >> 16);
+        const int x0 = (int)(ex[k] & 0xffffu), x1 = (int)(ex[k] >> 16), ya = (int)(ey[k] & 0xffffu),
+                  yb = (int)(ey[k] >> 16);
         const int yf = ya + ((warp - (ya - w.r0)) & (kW - 1));  // this warp's first row at or after ya
         const uint32_t wdt = (uint32_t)(x1 - x0 + 1);
         cnt[k] = yf <= yb ? ((uint32_t)(yb - yf) / kW + 1u) * wdt : 0u;
@@ -647,7 +668,6 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
         nh += cnt[k] > 0u ? 1u : 0u;
         pk[k] = (uint32_t)(yf - w.r0) | (uint32_t)x0 << 10 | (wdt - 1u) << 20;
         rcp[k] = __float_as_uint(__frcp_rn((float)wdt));
-        gk[k] = s_gid[buf][ix];
       }
       uint32_t incl = lsum, hincl = nh;
 #pragma unroll
@@ -744,7 +764,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
       }
     }
     if (more && stager) {
-      s_ent[buf ^ 1][threadIdx.x] = ent_next;
+      s_ex[buf ^ 1][threadIdx.x] = ent_next.x;
+      s_ey[buf ^ 1][threadIdx.x] = ent_next.y;
       s_gid[buf ^ 1][threadIdx.x] = gid_next;
     }
     __syncthreads();
