@@ -208,6 +208,13 @@ def test_checkpoint_resume_continues_the_run(tmp_path):
     torch.cuda.synchronize()
     assert a.n == b.n and a.iteration == b.iteration == 160
     assert int(a.step_count.item()) == int(b.step_count.item()) == 160
-    # the same run: equal up to the order of the float atomics in the backward pass
+    # the same run, up to the order of the float atomics in the backward pass.  Adam divides
+    # every gradient by its running RMS, so where a gradient is near zero its sign -- which
+    # that order can set -- decides the step, and a few elements drift apart by about a
+    # learning-rate step; a resume that lost any state (moments, step count, learning-rate
+    # schedule, density statistics) moves most elements
     for k in NAMES:
-        np.testing.assert_allclose(b.p[k].cpu().numpy(), a.p[k].cpu().numpy(), rtol=1e-3, atol=1e-4)
+        got, want = b.p[k].cpu().numpy(), a.p[k].cpu().numpy()
+        off = ~np.isclose(got, want, rtol=1e-3, atol=1e-4)
+        assert off.mean() <= 1e-3, (k, int(off.sum()), off.size)
+        np.testing.assert_allclose(got, want, rtol=1e-2, atol=1e-2)
