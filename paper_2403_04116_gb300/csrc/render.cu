@@ -359,10 +359,11 @@ __global__ void __launch_bounds__(512) k_render_fwd(const RenderArgs A) {
       const float4* slot = ring + (q % RING) * 64;
       const bool hit = 32 * q + lane < nlist && reaches_block(slot[2 * lane], slot[2 * lane + 1], bx0, by0, by1, cam);
       uint32_t mask = __ballot_sync(0xffffffffu, hit);
+      // (a thread whose pixels have stopped skips the remaining entries inside fwd_entry; the
+      // round-level vote above ends the walk once every pixel of the warp has stopped)
       while (mask) {
         const int k = __ffs(mask) - 1;
         mask &= mask - 1;
-        if (all_done()) break;
         const float4 a = slot[2 * k], b = slot[2 * k + 1];
         const float na = -0.5f * a.z, nb = -a.w, nc2 = -0.5f * b.x;
         fwd_entry<NP>(make_float4(a.x, a.x, a.y, a.y), make_float4(na, na, nb, nb), make_float4(nc2, nc2, b.y, b.y),
@@ -487,6 +488,16 @@ __global__ void __launch_bounds__(512) k_render_bwd(const RenderArgs A) {
         }
       }
       uint32_t mask = __ballot_sync(0xffffffffu, hit);
+      // the round's evaluated pairs, counted once per round: a pixel re-evaluates walked entry
+      // k (position top - k) when its last contributor lies beyond it, k >= top - L + 1
+#pragma unroll
+      for (int pr = 0; pr < NP; ++pr)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int sh = top - (int)Lp[pr][h] + 1;
+          const uint32_t ge = sh <= 0 ? 0xffffffffu : (sh >= 32 ? 0u : 0xffffffffu << sh);
+          nev += (uint32_t)__popc(mask & ge);
+        }
       __syncwarp();
       while (mask) {
         const int k = __ffs(mask) - 1;
@@ -505,7 +516,6 @@ __global__ void __launch_bounds__(512) k_render_bwd(const RenderArgs A) {
 #pragma unroll
         for (int pr = 0; pr < NP; ++pr) {
           const bool act0 = pos < Lp[pr][0], act1 = pos < Lp[pr][1];
-          nev += (uint32_t)act0 + (uint32_t)act1;
           dyv[pr] = fadd2(make_float2(q0.z, q0.w), npy[pr]);
           const float2 t = ffma2(make_float2(q1.x, q1.y), dx, fmul2(make_float2(q1.z, q1.w), dyv[pr]));
           p[pr] = ffma2(dx, t, fmul2(fmul2(make_float2(q2.x, q2.y), dyv[pr]), dyv[pr]));
