@@ -68,18 +68,15 @@ BWD_OPS_EVAL, BWD_OPS_CONTRIB = 20, 30
 FWD_OPS_PAIR, BWD_OPS_PAIR = 27, 45
 FP32_LANES = 128
 
-# DRAM traffic per launch from an ncu capture (profiles/k_render_train50k.md), valid while
-# the kernel source is unchanged (sha256 prefix of the .cu file) and for the configuration
-# it was taken with.
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels the
 # roofline line may name, from one ncu capture each (profiles/), valid only for the kernel
 # source (sha256 prefix of its .cu file and the shared header), workload and (tile_w,
 # tile_h, batch, pixels_per_thread, persistent) they were taken with.
 TRAFFIC = [
-    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "17aa407f367636bc",
-     "bytes_per_launch": 359.8e6},
-    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "17aa407f367636bc",
-     "bytes_per_launch": 150.1e6},
+    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "a7e4172121508d29",
+     "bytes_per_launch": 360.1e6},
+    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "a7e4172121508d29",
+     "bytes_per_launch": 150.2e6},
 ]
 
 
