@@ -261,7 +261,6 @@ __device__ __forceinline__ void fwd_entry(const float4 q0, const float4 q1, cons
   const float2 dx = fadd2(make_float2(q0.x, q0.y), npx);
 #pragma unroll
   for (int pr = 0; pr < NP; ++pr) {
-    if (done[pr][0] && done[pr][1]) continue;
     const float2 dy = fadd2(make_float2(q0.z, q0.w), npy[pr]);
     const float2 t = ffma2(make_float2(q1.x, q1.y), dx, fmul2(make_float2(q1.z, q1.w), dy));
     const float2 p = ffma2(dx, t, fmul2(fmul2(make_float2(q2.x, q2.y), dy), dy));

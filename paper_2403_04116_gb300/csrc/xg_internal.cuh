@@ -115,10 +115,14 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return _
 // (x log2 e + 1.5 * 2^23) - 1.5 * 2^23 with packed instructions let the multiply and the
 // add be evaluated with a single rounding, which moves k by one (and the result by a few
 // ulps) where x log2 e lies within a rounding of a half-integer.  Adding 1.5 * 2^23 to the
-// integer k afterwards is exact and puts k in the low mantissa bits for the scale.
+// integer k afterwards is exact and puts k in the low mantissa bits: the bits of
+// k + 1.5 * 2^23 are 0x4B400000 + k, and shifted left by 23 they are k << 23 (the constant's
+// low nine bits are zero).  The scaling by 2^k is then an integer add of k << 23 to the
+// bits of the polynomial's value p: p lies in [0.70, 1.42] and -116 <= k <= 127 (x in
+// [-80, 88], the domain of xg_exp's scale as well), so the result stays normal, and the
+// product p * 2^k that xg_exp rounds is exact -- the same bits.
 __device__ __forceinline__ float2 xg_exp2v(float2 x) {
   constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
-  constexpr int kRoundBits = 0x4B400000;
   x.x = fmaxf(x.x, -80.0f);
   x.y = fmaxf(x.y, -80.0f);
   const float2 xl = fmul2(x, f2(kLog2e));
@@ -132,9 +136,8 @@ __device__ __forceinline__ float2 xg_exp2v(float2 x) {
   p = ffma2(p, r, f2(1.0f));
   p = ffma2(p, r, f2(1.0f));
   const float2 m = fadd2(k, f2(kRound));
-  const float2 scale = make_float2(__int_as_float((__float_as_int(m.x) - kRoundBits + 127) << 23),
-                                   __int_as_float((__float_as_int(m.y) - kRoundBits + 127) << 23));
-  return fmul2(p, scale);
+  return make_float2(__uint_as_float(__float_as_uint(p.x) + (__float_as_uint(m.x) << 23)),
+                     __uint_as_float(__float_as_uint(p.y) + (__float_as_uint(m.y) << 23)));
 }
 
 // ln x for finite x >= 1: x = m 2^e, m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s), s = (m-1)/(m+1).
