@@ -267,7 +267,7 @@ __device__ __forceinline__ void fwd_entry(const float4 q0, const float4 q1, cons
     nev += (uint32_t)!done[pr][0] + (uint32_t)!done[pr][1];
     const bool in0 = !done[pr][0] && !(p.x < q3.z), in1 = !done[pr][1] && !(p.y < q3.z);
     if (!(in0 || in1)) continue;  // opacity provably below 1/255 for both
-    const float2 oe = fmul2(make_float2(q2.z, q2.w), xg_exp2v(p));
+    const float2 oe = fmul2(make_float2(q2.z, q2.w), xg_exp2v_core(p));
     const float2 al = make_float2(fminf(kAlphaMax, oe.x), fminf(kAlphaMax, oe.y));
     const float2 Tn = fmul2(T[pr], ffma2(al, f2(-1.0f), f2(1.0f)));
     const float2 Cn = ffma2(make_float2(q3.x, q3.y), fmul2(al, T[pr]), C[pr]);
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(512) k_render_bwd(const RenderArgs A) {
         bool any_ok = false;
 #pragma unroll
         for (int pr = 0; pr < NP; ++pr) {
-          const float2 oe = fmul2(make_float2(q2.z, q2.w), xg_exp2v(p[pr]));
+          const float2 oe = fmul2(make_float2(q2.z, q2.w), xg_exp2v_core(p[pr]));
           const float2 al = make_float2(fminf(kAlphaMax, oe.x), fminf(kAlphaMax, oe.y));
           const bool ok0 = in[pr][0] && !(al.x < kAlphaMin), ok1 = in[pr][1] && !(al.y < kAlphaMin);
           any_ok |= ok0 || ok1;

@@ -121,10 +121,12 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return _
 // bits of the polynomial's value p: p lies in [0.70, 1.42] and -116 <= k <= 127 (x in
 // [-80, 88], the domain of xg_exp's scale as well), so the result stays normal, and the
 // product p * 2^k that xg_exp rounds is exact -- the same bits.
-__device__ __forceinline__ float2 xg_exp2v(float2 x) {
+//
+// xg_exp2v_core takes x as it is: its value is xg_exp's for x in [-80, 88] and meaningless
+// below.  The compositing kernels call it directly, because they keep exp only where the
+// exponent reaches the record's threshold (above -6) and discard the other lanes' values.
+__device__ __forceinline__ float2 xg_exp2v_core(float2 x) {
   constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
-  x.x = fmaxf(x.x, -80.0f);
-  x.y = fmaxf(x.y, -80.0f);
   const float2 xl = fmul2(x, f2(kLog2e));
   const float2 k = make_float2(rintf(xl.x), rintf(xl.y));
   float2 r = ffma2(k, f2(-kLn2Hi), x);
@@ -138,6 +140,9 @@ __device__ __forceinline__ float2 xg_exp2v(float2 x) {
   const float2 m = fadd2(k, f2(kRound));
   return make_float2(__uint_as_float(__float_as_uint(p.x) + (__float_as_uint(m.x) << 23)),
                      __uint_as_float(__float_as_uint(p.y) + (__float_as_uint(m.y) << 23)));
+}
+__device__ __forceinline__ float2 xg_exp2v(float2 x) {
+  return xg_exp2v_core(make_float2(fmaxf(x.x, -80.0f), fmaxf(x.y, -80.0f)));
 }
 
 // ln x for finite x >= 1: x = m 2^e, m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s), s = (m-1)/(m+1).
