@@ -97,7 +97,7 @@ bool sizes_of(const xg_config* cfg, int64_t n, int64_t n_views, int32_t W, int32
 // Byte offsets of every array in the workspace, public and private, in allocation order.
 struct Offsets {
   size_t status, cameras, records, depth, rect, count;
-  size_t ent_depth[2], ent_gid[2], value, hist, bin_hist, bin_total, range, order, tfinal, last, grad2d;
+  size_t ent_depth[2], ent_gid[2], value, hist, key_span, bin_hist, bin_total, range, order, tfinal, last, grad2d;
   size_t total;
 };
 
@@ -125,7 +125,8 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t n_scan, in
   for (int b = 0; b < 2; ++b) o->ent_gid[b] = take(4 * VN);
   o->value = take(4 * cap);
   // radix blocks of a pass of V' <= V views: V' * ceil(sort_blocks / V') < sort_blocks + V'
-  o->hist = take(4 * 256 * (sort_blocks + (size_t)V + 1));
+  o->hist = take(4 * 256 * (sort_blocks + (size_t)V + 1) + 8);
+  o->key_span = o->hist + 4 * 256 * (sort_blocks + (size_t)V + 1);  // two words after the histograms
   o->bin_hist = take(4 * (size_t)V * (size_t)s->bin_units * (size_t)s->tiles_per_view);
   o->bin_total = take(4 * (size_t)V * (size_t)s->tiles_per_view);
   o->range = take(8 * (size_t)s->range_keys);
@@ -275,6 +276,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   }
   p.value = (uint32_t*)(base + o.value);
   p.hist = (uint32_t*)(base + o.hist);
+  p.key_span = (uint32_t*)(base + o.key_span);
   p.bin_hist = (uint32_t*)(base + o.bin_hist);
   p.bin_total = (uint32_t*)(base + o.bin_total);
   p.range = (uint2*)(base + o.range);

@@ -77,16 +77,46 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T& total) {
 // from array `digit_word`.  Histograms are block-major: hist[block][256], then the 256
 // digit totals.
 // ------------------------------------------------------------------------------------------
+// Whether the digits at `shift` and above are the same for every nonzero key of the span
+// (the keys lying between the smallest and the largest share every bit above the highest
+// bit in which those two differ); false when no key was nonzero.
+__device__ __forceinline__ bool digits_constant(const uint32_t* span, int shift) {
+  const uint32_t mx = span[0], mn = ~span[1];
+  return mx >= mn && ((mx ^ mn) >> shift) == 0u;
+}
+
+// With `span`: at shift 0 the histogram pass also records the range of the nonzero keys
+// (largest key and largest complement, by atomic maxima); at a later shift it does nothing
+// when that pass's digits are constant.
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ word, int shift, uint32_t mask,
-                                                             SortGeom geom, uint32_t* __restrict__ hist) {
+                                                             SortGeom geom, uint32_t* __restrict__ hist,
+                                                             uint32_t* __restrict__ span) {
   __shared__ uint32_t s_h[kWarps][256];
+  if (span && shift > 0 && digits_constant(span, shift)) return;
+  const bool record = span && shift == 0;
   const int warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&s_h[0][0])[i] = 0;
   __syncthreads();
   int seg;
   int64_t beg, end;
   sort_range(geom, seg, beg, end);
-  for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&s_h[warp][(word[i] >> shift) & mask], 1u);
+  uint32_t mx = 0u, mxn = 0u;
+  for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads) {
+    const uint32_t k = word[i];
+    atomicAdd(&s_h[warp][(k >> shift) & mask], 1u);
+    if (record && k != 0u) {
+      mx = max(mx, k);
+      mxn = max(mxn, ~k);
+    }
+  }
+  if (record) {
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    mxn = __reduce_max_sync(0xffffffffu, mxn);
+    if ((threadIdx.x & 31) == 0 && mx != 0u) {
+      atomicMax(&span[0], mx);
+      atomicMax(&span[1], mxn);
+    }
+  }
   __syncthreads();
   uint32_t c = 0;
 #pragma unroll
@@ -98,8 +128,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
 // digit's total in hist[blocks][digit] (counts wrap modulo 2^32; the scatter only takes
 // differences inside one segment).  One CTA per digit; the scatter turns the prefixes into
 // positions inside its segment itself.
-__global__ void __launch_bounds__(256) k_radix_colscan(uint32_t* __restrict__ hist, int blocks) {
+__global__ void __launch_bounds__(256) k_radix_colscan(uint32_t* __restrict__ hist, int blocks,
+                                                       const uint32_t* __restrict__ span, int shift) {
   __shared__ uint32_t s_warp[kWarps];
+  if (span && shift > 0 && digits_constant(span, shift)) return;
   const int d = blockIdx.x;
   const int per = (blocks + 255) / 256;
   const int b0 = min(blocks, (int)threadIdx.x * per), b1 = min(blocks, b0 + per);
@@ -169,7 +201,8 @@ template <int WORDS, int DW, bool IOTA1>
 __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(SortArrays<WORDS> arr, int shift,
                                                                                 uint32_t mask, uint32_t spin,
                                                                 DevStatus* __restrict__ st, SortGeom geom,
-                                                                const uint32_t* __restrict__ hist) {
+                                                                const uint32_t* __restrict__ hist,
+                                                                const uint32_t* __restrict__ span) {
   extern __shared__ __align__(128) uint32_t s_dyn[];  // [2][WORDS][kSortTile]
   // per warp and digit: the tile's count, then the digit's first slot in the reordered tile
   // (16 bits each, two digits per word so that one 32-bit shared atomic adds to a count)
@@ -185,6 +218,13 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
   int64_t beg, end;
   sort_range(geom, seg, beg, end);
   if (beg >= end) return;
+  if (!IOTA1 && span && shift > 0 && digits_constant(span, shift)) {
+    // every nonzero key has the same digit here: the stable pass moves none of them
+    for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads)
+#pragma unroll
+      for (int w = 0; w < WORDS; ++w) arr.out[w][i] = __ldg(arr.in[w] + i);
+    return;
+  }
   const int64_t seg_base = (int64_t)seg * geom.seg_len;
   constexpr int LOADED = IOTA1 ? 1 : WORDS;  // words read from memory (the first LOADED)
   bool aligned = true;  // every tile of the chunk starts 16-byte aligned in every array read
@@ -874,51 +914,56 @@ cudaError_t radix_prepare() {
 
 template <int WORDS>
 cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, uint32_t mask,
-                       const SortGeom& geom, DevStatus* status, uint32_t* hist, cudaStream_t st, bool iota1) {
+                       const SortGeom& geom, DevStatus* status, uint32_t* hist, cudaStream_t st, bool iota1,
+                       uint32_t* key_span) {
+  if (digit_word != 0) key_span = nullptr;  // the span is of the keys in word 0
   const cudaError_t prep = radix_prepare();
   if (prep != cudaSuccess) return prep;
   const int blocks = geom.segments * geom.per_seg;
   {
     Timed t(f, kRadixHist, st);
-    k_radix_hist<<<blocks, kSortThreads, 0, st>>>(arr.in[digit_word], shift, mask, geom, hist);
+    k_radix_hist<<<blocks, kSortThreads, 0, st>>>(arr.in[digit_word], shift, mask, geom, hist, key_span);
   }
   {
     Timed t(f, kRadixScan, st);
-    k_radix_colscan<<<256, 256, 0, st>>>(hist, blocks);
+    k_radix_colscan<<<256, 256, 0, st>>>(hist, blocks, key_span, shift);
   }
   {
     Timed t(f, kRadixScatter, st);
     constexpr size_t smem = scatter_smem<WORDS>();
     if (digit_word == 0 && iota1 && WORDS == 2)
       k_radix_scatter<WORDS, 0, WORDS == 2><<<blocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status,
-                                                                                 geom, hist);
+                                                                                 geom, hist, key_span);
     else if (digit_word == 0)
       k_radix_scatter<WORDS, 0, false><<<blocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status,
-                                                                            geom, hist);
+                                                                            geom, hist, key_span);
     else
       k_radix_scatter<WORDS, 1, false><<<blocks, kSortThreads, smem, st>>>(arr, shift, mask, spin_limit(), status,
-                                                                            geom, hist);
+                                                                            geom, hist, key_span);
   }
   return cudaGetLastError();
 }
 
 template cudaError_t radix_pass<2>(xg_frame*, const SortArrays<2>&, int, int, uint32_t, const SortGeom&, DevStatus*,
-                                    uint32_t*, cudaStream_t, bool);
+                                    uint32_t*, cudaStream_t, bool, uint32_t*);
 template cudaError_t radix_pass<3>(xg_frame*, const SortArrays<3>&, int, int, uint32_t, const SortGeom&, DevStatus*,
-                                    uint32_t*, cudaStream_t, bool);
+                                    uint32_t*, cudaStream_t, bool, uint32_t*);
 
 cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   const FramePtrs& p = f->p;
   // every binning starts from a clean code (a failed check of an earlier call does not stick)
   {
     Timed t(f, kMemset, st);
-    const cudaError_t e = cudaMemsetAsync(&p.status->code, 0, sizeof(p.status->code), st);
+    cudaError_t e = cudaMemsetAsync(&p.status->code, 0, sizeof(p.status->code), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.key_span, 0, 2 * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
   }
   // stage 1: every view's n entries, [v*n, (v+1)*n), sorted by the depth bits as a segment
   // of its own; words: depth bits, Gaussian.  The first pass reads the projection's depth
   // plane (t_z >= 0, whose float bits order like the values) and generates the Gaussian
-  // index, the entry's position in its view.
+  // index, the entry's position in its view.  Culled entries have key 0 and no pairs; the
+  // first pass records the range of the other keys, and a later pass whose digits are the
+  // same for all of them (t_z between 512 and 2048 mm: the top byte) is a copy.
   const SortGeom sg = sort_geom(f->n, f->n_views, f->sort_blocks);
   int cur = 0;
   for (int pass = 0; pass < f->entry_passes; ++pass) {
@@ -926,7 +971,7 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     arr.in[0] = pass == 0 ? reinterpret_cast<const uint32_t*>(p.depth) : p.ent_depth[cur];
     arr.in[1] = pass == 0 ? nullptr : p.ent_gid[cur];
     arr.out[0] = p.ent_depth[cur ^ 1], arr.out[1] = p.ent_gid[cur ^ 1];
-    const cudaError_t e = radix_pass<2>(f, arr, 0, 8 * pass, 255u, sg, p.status, p.hist, st, pass == 0);
+    const cudaError_t e = radix_pass<2>(f, arr, 0, 8 * pass, 255u, sg, p.status, p.hist, st, pass == 0, p.key_span);
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }

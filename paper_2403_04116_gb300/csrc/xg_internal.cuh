@@ -180,6 +180,7 @@ struct FramePtrs {
   uint32_t* ent_gid[2];    // the first pass reads `depth` and generates the Gaussian index
   uint32_t* value;    // [capacity]: Gaussian index of every pair, in (tile, view, depth) order
   uint32_t* hist;     // [radix blocks + 1][256]: per-block digit counts, then digit totals
+  uint32_t* key_span; // [2]: the entry sort's key range over its nonzero keys (max, max of ~key)
   uint32_t* bin_hist;   // [V][J][T]: pairs of each unit of entries per tile, then their prefix
   uint32_t* bin_total;  // [T][V]: pairs per (tile, view)
   uint2* range;       // [V << tile_bits]
@@ -296,10 +297,15 @@ cudaError_t launch_exp_check(const float* x, float* ys, float* yp, int64_t n, cu
 // (no timing).
 // With iota1 (WORDS == 2, digit word 0), word 1 is not read: each item's is its index within
 // its segment.
+// With key_span (digit word 0): the pass at shift 0 records the range of the nonzero keys
+// there (key_span zeroed before it); a later pass whose digit, and every digit above it, is
+// the same for all nonzero keys leaves them in place: it copies its arrays through without
+// histograms.  Zero keys (entries with nothing to sort for) may then stand elsewhere than a
+// full sort would put them; the order of the nonzero keys is that of the full sort.
 template <int WORDS>
 cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, uint32_t mask,
                        const SortGeom& geom, DevStatus* status, uint32_t* hist, cudaStream_t st,
-                       bool iota1 = false);
+                       bool iota1 = false, uint32_t* key_span = nullptr);
 // Sets the scatter kernels' shared-memory attributes (once per process); call outside
 // stream capture before the first radix_pass.
 cudaError_t radix_prepare();

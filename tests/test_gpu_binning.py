@@ -11,6 +11,9 @@ laid out in (tile, view) order):
 * Gaussians as large as the scene (a fifth to a half of its side): most cover hundreds of
   the 1,024 tiles of a view, so the pair scatter takes every unit's entries in many chunks
   of a few entries each;
+* culled entries (key 0) among the sorted ones, in a scene whose depths share their top
+  byte (the entry sort's last pass is then a copy) and in one whose depths cross 512 mm (it
+  is not);
 * a scan whose last pass has fewer views but more radix blocks than a full pass: 36 views,
   19 per pass (608 blocks) and a last pass of 17 (612 blocks); every view equals the same
   view rendered by a frame of its own, and the last one equals the replica.
@@ -24,6 +27,7 @@ import oracle  # noqa: E402
 from paper_2403_04116_gb300 import binding as B  # noqa: E402
 from paper_2403_04116_gb300 import synth  # noqa: E402
 from paper_2403_04116_gb300.render import Frame, FrameConfig  # noqa: E402
+from paper_2403_04116_gb300.synth import View  # noqa: E402
 from tests.gpu_util import run_forward, to_device  # noqa: E402
 from tests.test_gpu_parity import _expected_index  # noqa: E402
 
@@ -73,6 +77,28 @@ def test_scene_sized_gaussians_bit_exact():
     reps, idx = _expected_index(g, views, tile)
     assert gpu["status"].code == B.XG_OK
     assert gpu["M"] == idx["M"] > 300 * n * V  # hundreds of tiles per Gaussian on average
+    np.testing.assert_array_equal(gpu["key_tile"], idx["key_tile"])
+    np.testing.assert_array_equal(gpu["value"], idx["value"])
+    np.testing.assert_array_equal(gpu["range"], idx["range"])
+    for v, r in enumerate(reps):
+        np.testing.assert_array_equal(gpu["image"][v].view(np.uint32), r["image"].view(np.uint32))
+
+
+@pytest.mark.parametrize("sod,side", [(1000.0, 42.7), (600.0, 200.0)])
+def test_culled_entries_and_the_depth_span(sod, side):
+    n, V, W, tile, cid = 6_001, 3, 128, (16, 16), 25
+    g = synth.gaussians(n, side, synth.rng(cid, 0))
+    g["opacity"][::3] = 0.003  # below 1/255: culled in projection, depth key 0
+    views = [View(sod, 1100.0, 1.0, 1.0, 0.4 * k, W, W) for k in range(V)]
+    gpu = run_forward(g, views, tile)
+    depth = gpu["depth"].reshape(V, n)
+    live = depth[depth > 0]
+    assert (depth == 0).sum() >= n // 3 * V and live.size > 1000
+    crosses = bool(live.min() < 512.0 <= live.max())
+    assert crosses == (sod < 1000.0)  # the first scene's depths share the top byte of their bits
+    reps, idx = _expected_index(g, views, tile)
+    assert gpu["status"].code == B.XG_OK
+    assert gpu["M"] == idx["M"] > 10_000
     np.testing.assert_array_equal(gpu["key_tile"], idx["key_tile"])
     np.testing.assert_array_equal(gpu["value"], idx["value"])
     np.testing.assert_array_equal(gpu["range"], idx["range"])
