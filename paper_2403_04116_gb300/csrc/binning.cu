@@ -85,6 +85,21 @@ __device__ __forceinline__ bool digits_constant(const uint32_t* span, int shift)
   return mx >= mn && ((mx ^ mn) >> shift) == 0u;
 }
 
+// The entry sort's two ping-pong plane sets and its key span.  The passes that run write set
+// 1, 0, 1, ... in turn; the passes that the span shows constant are the last ones and leave
+// the planes where they are, so the sorted entries are in set (passes run) mod 2, and the
+// other set is free.
+struct SortedPlanes {
+  uint32_t *depth0, *depth1, *gid0, *gid1;
+  const uint32_t* span;
+  int passes;
+};
+__device__ __forceinline__ int sorted_set(const SortedPlanes& sp) {
+  int run = 1;
+  for (int q = 1; q < sp.passes; ++q) run += digits_constant(sp.span, 8 * q) ? 0 : 1;
+  return run & 1;
+}
+
 // With `span`: at shift 0 the histogram pass also records the range of the nonzero keys
 // (largest key and largest complement, by atomic maxima); at a later shift it does nothing
 // when that pass's digits are constant.
@@ -109,15 +124,22 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
       mxn = max(mxn, ~k);
     }
   }
-  if (record) {
+  __shared__ uint32_t s_span[2];
+  if (record) {  // one pair of atomics per block: the two words are the same for every block
+    if (threadIdx.x == 0) s_span[0] = s_span[1] = 0u;
+    __syncthreads();
     mx = __reduce_max_sync(0xffffffffu, mx);
     mxn = __reduce_max_sync(0xffffffffu, mxn);
-    if ((threadIdx.x & 31) == 0 && mx != 0u) {
-      atomicMax(&span[0], mx);
-      atomicMax(&span[1], mxn);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&s_span[0], mx);
+      atomicMax(&s_span[1], mxn);
     }
   }
   __syncthreads();
+  if (record && threadIdx.x == 0 && s_span[0] != 0u) {
+    atomicMax(&span[0], s_span[0]);
+    atomicMax(&span[1], s_span[1]);
+  }
   uint32_t c = 0;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) c += s_h[w][threadIdx.x];
@@ -218,13 +240,9 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
   int64_t beg, end;
   sort_range(geom, seg, beg, end);
   if (beg >= end) return;
-  if (!IOTA1 && span && shift > 0 && digits_constant(span, shift)) {
-    // every nonzero key has the same digit here: the stable pass moves none of them
-    for (int64_t i = beg + threadIdx.x; i < end; i += kSortThreads)
-#pragma unroll
-      for (int w = 0; w < WORDS; ++w) arr.out[w][i] = __ldg(arr.in[w] + i);
-    return;
-  }
+  // every nonzero key has the same digit here: the stable pass would move none of them, so
+  // the planes stay where they are (the consumers find them through sorted_buffer)
+  if (!IOTA1 && span && shift > 0 && digits_constant(span, shift)) return;
   const int64_t seg_base = (int64_t)seg * geom.seg_len;
   constexpr int LOADED = IOTA1 ? 1 : WORDS;  // words read from memory (the first LOADED)
   bool aligned = true;  // every tile of the chunk starts 16-byte aligned in every array read
@@ -425,14 +443,18 @@ constexpr int kBinDiffWords = kBinGroupTiles + 2 * 512 + 1;
 // (columns x0 | x1 << 16 in ent_x, rows y0 | y1 << 16 in ent_y; ent_y = 1 (y0 > y1) for an
 // entry with no tile), so that the pair scatter reads them sequentially instead of
 // gathering them by Gaussian index again.
-__global__ void __launch_bounds__(kBinThreads) k_bin_count(BinGeom g, const uint32_t* __restrict__ ent_gid,
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(BinGeom g, SortedPlanes sp,
                                                            const uint32_t* __restrict__ count,
                                                            const ushort4* __restrict__ rect,
                                                            DevStatus* __restrict__ st,
-                                                           uint32_t* __restrict__ bin_hist,
-                                                           uint32_t* __restrict__ ent_x, uint32_t* __restrict__ ent_y) {
+                                                           uint32_t* __restrict__ bin_hist) {
   __shared__ int32_t s_d[kBinDiffWords];
   if (st->code != XG_OK) return;  // stage 1 failed a check: its entries are not to be read
+  // the sorted entries, and the free planes of the other set for the rectangles
+  const bool set1 = sorted_set(sp) == 1;
+  const uint32_t* __restrict__ ent_gid = set1 ? sp.gid1 : sp.gid0;
+  uint32_t* __restrict__ ent_x = set1 ? sp.depth0 : sp.depth1;
+  uint32_t* __restrict__ ent_y = set1 ? sp.gid0 : sp.gid1;
   const BinWork w = bin_work(g);
   const int cols = g.tiles_x + 1;
   const int cells = (w.rows + 1) * cols;
@@ -633,9 +655,7 @@ __device__ __forceinline__ void load_words(const uint32_t* src, uint32_t (&out)[
 __host__ __device__ __forceinline__ int bin_padded(int tiles) { return tiles + (tiles >> 5) + 1; }
 
 template <bool kMaskRank, int K>
-__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const uint32_t* __restrict__ ent_gid,
-                                                             const uint32_t* __restrict__ ent_x,
-                                                             const uint32_t* __restrict__ ent_y,
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, SortedPlanes sp,
                                                              const uint32_t* __restrict__ bin_hist,
                                                              const uint2* __restrict__ range,
                                                              DevStatus* __restrict__ st, uint32_t* __restrict__ value) {
@@ -654,6 +674,10 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, const ui
   __shared__ __align__(16) uint32_t s_gid[2][kBinStage];
   __shared__ uint4 s_cmp[kW][32 * K];  // per warp: its entries with pairs, compacted (prefix, packed, 1/width, Gaussian)
   if (st->code != XG_OK) return;
+  const bool set1 = sorted_set(sp) == 1;  // the sorted entries, and the rectangles in the other set
+  const uint32_t* __restrict__ ent_gid = set1 ? sp.gid1 : sp.gid0;
+  const uint32_t* __restrict__ ent_x = set1 ? sp.depth0 : sp.depth1;
+  const uint32_t* __restrict__ ent_y = set1 ? sp.gid0 : sp.gid1;
   const int64_t pairs = st->pairs;
   const BinWork w = bin_work(g);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -963,7 +987,7 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   // plane (t_z >= 0, whose float bits order like the values) and generates the Gaussian
   // index, the entry's position in its view.  Culled entries have key 0 and no pairs; the
   // first pass records the range of the other keys, and a later pass whose digits are the
-  // same for all of them (t_z between 512 and 2048 mm: the top byte) is a copy.
+  // same for all of them (t_z between 512 and 2048 mm: the top byte) does nothing.
   const SortGeom sg = sort_geom(f->n, f->n_views, f->sort_blocks);
   int cur = 0;
   for (int pass = 0; pass < f->entry_passes; ++pass) {
@@ -975,17 +999,16 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }
-  const uint32_t* ent_gid = p.ent_gid[cur];
-  // the sort's other ping-pong planes are free now: the sorted tile rectangles go there
-  uint32_t* ent_x = p.ent_depth[cur ^ 1];
-  uint32_t* ent_y = p.ent_gid[cur ^ 1];
+  // the sorted entries' set is known on the device only (a pass may have been a no-op);
+  // the counting pass writes the sorted rectangles into the other set's free planes
+  const SortedPlanes sp = {p.ent_depth[0], p.ent_depth[1], p.ent_gid[0], p.ent_gid[1], p.key_span, f->entry_passes};
   // stages 2-4: counts per unit and tile, their prefixes and the ranges, the pairs
   const BinGeom g = {f->n, f->tiles_per_view, f->n_views, f->tiles_x, f->tiles_y, f->tile_bits,
                      f->bin_unit, f->bin_units, f->bin_rows, f->bin_groups};
   const unsigned ctas = (unsigned)((int64_t)f->n_views * f->bin_units * f->bin_groups);
   {
     Timed t(f, kBinCount, st);
-    k_bin_count<<<ctas, kBinThreads, 0, st>>>(g, ent_gid, p.count, p.rect, p.status, p.bin_hist, ent_x, ent_y);
+    k_bin_count<<<ctas, kBinThreads, 0, st>>>(g, sp, p.count, p.rect, p.status, p.bin_hist);
   }
   {
     Timed t(f, kBinColscan, st);
@@ -1001,10 +1024,10 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
     const int group_tiles = f->bin_rows * f->tiles_x;
     if (group_tiles > kBinMaskRankTiles)
       k_bin_scatter<true, kMaskRankLaneEntries><<<ctas, kBinThreads, bin_scatter_smem(group_tiles), st>>>(
-          g, ent_gid, ent_x, ent_y, p.bin_hist, p.range, p.status, p.value);
+          g, sp, p.bin_hist, p.range, p.status, p.value);
     else
       k_bin_scatter<false, kMatchLaneEntries><<<ctas, kBinThreads, bin_scatter_smem(group_tiles), st>>>(
-          g, ent_gid, ent_x, ent_y, p.bin_hist, p.range, p.status, p.value);
+          g, sp, p.bin_hist, p.range, p.status, p.value);
   }
   {
     Timed t(f, kWorkOrder, st);

@@ -299,9 +299,11 @@ cudaError_t launch_exp_check(const float* x, float* ys, float* yp, int64_t n, cu
 // its segment.
 // With key_span (digit word 0): the pass at shift 0 records the range of the nonzero keys
 // there (key_span zeroed before it); a later pass whose digit, and every digit above it, is
-// the same for all nonzero keys leaves them in place: it copies its arrays through without
-// histograms.  Zero keys (entries with nothing to sort for) may then stand elsewhere than a
-// full sort would put them; the order of the nonzero keys is that of the full sort.
+// the same for all nonzero keys would move none of them and does nothing: its output arrays
+// are not written, and the sorted arrays are the output of the last pass that ran (the
+// caller finds which from the span).  Zero keys (entries with nothing to sort for) may then
+// stand elsewhere than a full sort would put them; the order of the nonzero keys is that of
+// the full sort.
 template <int WORDS>
 cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word, int shift, uint32_t mask,
                        const SortGeom& geom, DevStatus* status, uint32_t* hist, cudaStream_t st,
