@@ -549,7 +549,7 @@ def run_ours(args) -> None:
     else:
         VN = V * n
         M = int(st.pairs)
-        passes = frame.layout.sort_passes
+        passes = _sort_passes_run(frame.array("depth").cpu().numpy(), frame.layout.sort_passes)
         algo = _algo_bytes(dom, n, VN, M, passes) / max(1, launches // timing_steps)
         roof = {"bound": "hbm", "achieved": algo / (avg_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -694,11 +694,23 @@ def _alu_roof(kernel: str, f_eval: int, f_contrib: int, b_eval: int, b_contrib: 
                        f"per_pair: {BWD_OPS_PAIR if kernel == 'k_render_bwd' else FWD_OPS_PAIR} per evaluated pair")}
 
 
+def _sort_passes_run(depth, passes: int) -> int:
+    """Entry-sort passes that do work: the first, and every later one whose digit (or one
+    above it) differs between the smallest and the largest nonzero depth key -- the passes
+    whose digits are the same for every visible entry are skipped on the device."""
+    k = np.ascontiguousarray(depth, dtype=np.float32).view(np.uint32).ravel()
+    k = k[k != 0]
+    if k.size == 0:
+        return passes
+    d = int(k.max()) ^ int(k.min())
+    return 1 + sum(1 for q in range(1, passes) if d >> (8 * q))
+
+
 def _algo_bytes(kernel: str, n: int, VN: int, M: int, entry_passes: int) -> float:
     """Algorithmic DRAM bytes of one step's launches of a memory-bound kernel (each input
     read once, each output written once): projection reads the 48-byte Gaussian and writes
     a 48-byte (record, depth, rectangle, count) per (view, Gaussian); the entry sort moves 2
-    words in and out per pass; the counting pass reads each sorted entry's index, count and
+    words in and out per pass that runs; the counting pass reads each sorted entry's index, count and
     rectangle (16 B) and writes the rectangle in entry order (8 B), which the scatter reads
     with the index (12 B) before writing one 4-byte index per pair."""
     return {"k_radix_scatter": 16 * VN * entry_passes, "k_radix_hist": 4 * VN * entry_passes,
@@ -790,7 +802,9 @@ def run_scan(args) -> None:
     fp32 = fp32_peak()
     alu_peak, alu_src = _alu_peak(fp32, peaks)
     VN = V * n
-    entry_passes = frame.layout.sort_passes
+    # the passes the last pass of views ran (every pass of this scene: its depths span
+    # 759-1241 mm at most)
+    entry_passes = _sort_passes_run(frame.array("depth").cpu().numpy(), frame.layout.sort_passes)
     stages = {}
     for k, (nl, ms) in sorted(kernels.items()):
         if k == "memset":
