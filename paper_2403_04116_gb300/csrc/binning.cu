@@ -74,8 +74,8 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T& total) {
 
 // ------------------------------------------------------------------------------------------
 // LSD radix sort, one 8-bit digit per pass, of WORDS parallel u32 arrays; the digit comes
-// from array `digit_word`.  Histograms are block-major: hist[block][256], then the 256
-// digit totals.
+// from array `digit_word`.  Histograms are block-major: hist[block][256]; each scatter CTA
+// sums the rows of its own segment's blocks for its positions (no scan over all blocks).
 // ------------------------------------------------------------------------------------------
 // Whether the digits at `shift` and above are the same for every nonzero key of the span
 // (the keys lying between the smallest and the largest share every bit above the highest
@@ -144,29 +144,6 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) c += s_h[w][threadIdx.x];
   hist[blockIdx.x * 256 + threadIdx.x] = c;
-}
-
-// Per digit, the exclusive prefix over all blocks of hist[block][digit], in place, and the
-// digit's total in hist[blocks][digit] (counts wrap modulo 2^32; the scatter only takes
-// differences inside one segment).  One CTA per digit; the scatter turns the prefixes into
-// positions inside its segment itself.
-__global__ void __launch_bounds__(256) k_radix_colscan(uint32_t* __restrict__ hist, int blocks,
-                                                       const uint32_t* __restrict__ span, int shift) {
-  __shared__ uint32_t s_warp[kWarps];
-  if (span && shift > 0 && digits_constant(span, shift)) return;
-  const int d = blockIdx.x;
-  const int per = (blocks + 255) / 256;
-  const int b0 = min(blocks, (int)threadIdx.x * per), b1 = min(blocks, b0 + per);
-  uint32_t local = 0;
-  for (int b = b0; b < b1; ++b) local += hist[b * 256 + d];
-  uint32_t total;
-  uint32_t run = block_exclusive_scan<256>(local, s_warp, total);
-  for (int b = b0; b < b1; ++b) {
-    const uint32_t c = hist[b * 256 + d];
-    hist[b * 256 + d] = run;
-    run += c;
-  }
-  if (threadIdx.x == 0) hist[blocks * 256 + d] = total;
 }
 
 // ---- bulk asynchronous copies into shared memory, completed on an mbarrier ----------------
@@ -256,11 +233,19 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
   // fewer than 2^32 items)
   uint32_t bofs;
   {
-    const uint32_t first = hist[(seg * geom.per_seg) * 256 + tid];
-    const uint32_t in_seg = hist[((seg + 1) * geom.per_seg) * 256 + tid] - first;
+    // the digit's count in this segment and in the segment's blocks before this one, summed
+    // from the blocks' histograms (independent loads, a few to a few hundred per thread)
+    const int b0 = seg * geom.per_seg, b1 = b0 + geom.per_seg, me = (int)blockIdx.x;
+    uint32_t in_seg = 0u, before = 0u;
+#pragma unroll 4
+    for (int b = b0; b < b1; ++b) {
+      const uint32_t c = hist[b * 256 + tid];
+      in_seg += c;
+      before += b < me ? c : 0u;
+    }
     uint32_t all;
     const uint32_t digit_base = block_exclusive_scan<kSortThreads>(in_seg, s_warp, all);
-    bofs = digit_base + (hist[blockIdx.x * 256 + tid] - first);
+    bofs = digit_base + before;
   }
   for (int i = tid; i < kWarps * 128; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
   if (tid == 0) {
@@ -947,10 +932,6 @@ cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word
   {
     Timed t(f, kRadixHist, st);
     k_radix_hist<<<blocks, kSortThreads, 0, st>>>(arr.in[digit_word], shift, mask, geom, hist, key_span);
-  }
-  {
-    Timed t(f, kRadixScan, st);
-    k_radix_colscan<<<256, 256, 0, st>>>(hist, blocks, key_span, shift);
   }
   {
     Timed t(f, kRadixScatter, st);
