@@ -366,7 +366,7 @@ xg_status xg_frame_set_timing(xg_frame* frame, int32_t enable) {
 
 xg_status xg_frame_read_timing(xg_frame* frame, xg_kernel_time* out, int32_t capacity, int32_t* count) {
   static const char* const names[xg::kNumKernels] = {
-      "k_project", "k_bin_count", "k_bin_colscan", "k_bin_base", "k_bin_scatter", "k_radix_hist",
+      "k_project", "k_bin_count", "k_bin_colscan", "k_bin_base", "k_bin_scatter", "k_radix_hist", "k_radix_colscan",
       "k_radix_scatter", "k_work_order", "k_render_fwd", "k_render_bwd", "k_project_bwd", "memset"};
   if (!frame || !count || (capacity > 0 && !out)) return XG_ERR_INVALID_ARG;
   if (frame->nrec > 0) {

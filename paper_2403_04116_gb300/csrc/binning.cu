@@ -29,6 +29,7 @@
 namespace xg {
 
 constexpr int kWarps = kSortThreads / 32;
+constexpr int kLocalPrefixBlocks = 64;  // segments of at most this many blocks: no column scan
 
 // Items [beg, end) of this CTA in a segmented radix pass: segment s = blockIdx.x / per_seg
 // holds items [s * seg_len, (s + 1) * seg_len) and is split among its per_seg CTAs in chunks
@@ -74,8 +75,9 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T& total) {
 
 // ------------------------------------------------------------------------------------------
 // LSD radix sort, one 8-bit digit per pass, of WORDS parallel u32 arrays; the digit comes
-// from array `digit_word`.  Histograms are block-major: hist[block][256]; each scatter CTA
-// sums the rows of its own segment's blocks for its positions (no scan over all blocks).
+// from array `digit_word`.  Histograms are block-major: hist[block][256].  Where a segment
+// has at most kLocalPrefixBlocks blocks, each scatter CTA sums its segment's rows for its
+// positions; otherwise a column scan over all blocks runs first.
 // ------------------------------------------------------------------------------------------
 // Whether the digits at `shift` and above are the same for every nonzero key of the span
 // (the keys lying between the smallest and the largest share every bit above the highest
@@ -144,6 +146,30 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) c += s_h[w][threadIdx.x];
   hist[blockIdx.x * 256 + threadIdx.x] = c;
+}
+
+// Segments of many blocks (more than kLocalPrefixBlocks): per digit, the exclusive prefix
+// over all blocks of hist[block][digit], in place, and the digit's total in
+// hist[blocks][digit] (counts wrap modulo 2^32; the scatter only takes differences inside one
+// segment).  One CTA per digit; the scatter turns the prefixes into positions inside its
+// segment itself.
+__global__ void __launch_bounds__(256) k_radix_colscan(uint32_t* __restrict__ hist, int blocks,
+                                                       const uint32_t* __restrict__ span, int shift) {
+  __shared__ uint32_t s_warp[kWarps];
+  if (span && shift > 0 && digits_constant(span, shift)) return;
+  const int d = blockIdx.x;
+  const int per = (blocks + 255) / 256;
+  const int b0 = min(blocks, (int)threadIdx.x * per), b1 = min(blocks, b0 + per);
+  uint32_t local = 0;
+  for (int b = b0; b < b1; ++b) local += hist[b * 256 + d];
+  uint32_t total;
+  uint32_t run = block_exclusive_scan<256>(local, s_warp, total);
+  for (int b = b0; b < b1; ++b) {
+    const uint32_t c = hist[b * 256 + d];
+    hist[b * 256 + d] = run;
+    run += c;
+  }
+  if (threadIdx.x == 0) hist[blocks * 256 + d] = total;
 }
 
 // ---- bulk asynchronous copies into shared memory, completed on an mbarrier ----------------
@@ -233,15 +259,22 @@ __global__ void __launch_bounds__(kSortThreads, kSortCtasPerSM) k_radix_scatter(
   // fewer than 2^32 items)
   uint32_t bofs;
   {
-    // the digit's count in this segment and in the segment's blocks before this one, summed
-    // from the blocks' histograms (independent loads, a few to a few hundred per thread)
+    // the digit's count in this segment and in the segment's blocks before this one: summed
+    // from the blocks' rows (at most kLocalPrefixBlocks independent loads per thread), or
+    // taken from the column scan's prefixes
     const int b0 = seg * geom.per_seg, b1 = b0 + geom.per_seg, me = (int)blockIdx.x;
     uint32_t in_seg = 0u, before = 0u;
+    if (geom.per_seg <= kLocalPrefixBlocks) {
 #pragma unroll 4
-    for (int b = b0; b < b1; ++b) {
-      const uint32_t c = hist[b * 256 + tid];
-      in_seg += c;
-      before += b < me ? c : 0u;
+      for (int b = b0; b < b1; ++b) {
+        const uint32_t c = hist[b * 256 + tid];
+        in_seg += c;
+        before += b < me ? c : 0u;
+      }
+    } else {
+      const uint32_t first = hist[b0 * 256 + tid];
+      in_seg = hist[b1 * 256 + tid] - first;
+      before = hist[me * 256 + tid] - first;
     }
     uint32_t all;
     const uint32_t digit_base = block_exclusive_scan<kSortThreads>(in_seg, s_warp, all);
@@ -932,6 +965,10 @@ cudaError_t radix_pass(xg_frame* f, const SortArrays<WORDS>& arr, int digit_word
   {
     Timed t(f, kRadixHist, st);
     k_radix_hist<<<blocks, kSortThreads, 0, st>>>(arr.in[digit_word], shift, mask, geom, hist, key_span);
+  }
+  if (geom.per_seg > kLocalPrefixBlocks) {
+    Timed t(f, kRadixScan, st);
+    k_radix_colscan<<<256, 256, 0, st>>>(hist, blocks, key_span, shift);
   }
   {
     Timed t(f, kRadixScatter, st);

@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <stdint.h>
 
 #include "../../include/xg.h"
@@ -179,7 +180,7 @@ struct FramePtrs {
   uint32_t* ent_depth[2];  // stage-1 sort of the V*n entries (ping-pong): depth key, Gaussian;
   uint32_t* ent_gid[2];    // the first pass reads `depth` and generates the Gaussian index
   uint32_t* value;    // [capacity]: Gaussian index of every pair, in (tile, view, depth) order
-  uint32_t* hist;     // [radix blocks][256]: per-block digit counts of the current pass
+  uint32_t* hist;     // [radix blocks + 1][256]: per-block digit counts (prefixes after a column scan)
   uint32_t* key_span; // [2]: the entry sort's key range over its nonzero keys (max, max of ~key)
   uint32_t* bin_hist;   // [V][J][T]: pairs of each unit of entries per tile, then their prefix
   uint32_t* bin_total;  // [T][V]: pairs per (tile, view)
@@ -208,7 +209,9 @@ inline SortGeom sort_geom(int64_t seg_len, int32_t segments, int32_t blocks) {
   SortGeom g;
   g.seg_len = seg_len;
   g.segments = segments;
-  g.per_seg = (blocks + segments - 1) / segments;
+  // no more CTAs per segment than it has radix tiles (the others would sort nothing)
+  const int64_t tiles = (seg_len + kSortTile - 1) / kSortTile;
+  g.per_seg = (int32_t)std::max<int64_t>(1, std::min<int64_t>((blocks + segments - 1) / segments, tiles));
   return g;
 }
 
@@ -223,7 +226,7 @@ struct SortArrays {
 
 namespace xg {
 enum KernelId {
-  kProject, kBinCount, kBinColscan, kBinBase, kBinScatter, kRadixHist, kRadixScatter, kWorkOrder,
+  kProject, kBinCount, kBinColscan, kBinBase, kBinScatter, kRadixHist, kRadixScan, kRadixScatter, kWorkOrder,
   kRenderFwd, kRenderBwd, kProjectBwd, kMemset, kNumKernels
 };
 struct TimingRec {
@@ -291,9 +294,10 @@ cudaError_t launch_loss_l1(const float* image, const float* target, int64_t coun
                            float* loss, cudaStream_t st);
 cudaError_t launch_exp_check(const float* x, float* ys, float* yp, int64_t n, cudaStream_t st);
 
-// One LSD radix pass (histogram, stable scatter; binning.cu) over WORDS arrays,
+// One LSD radix pass (histogram, digit scan where segments have many blocks, stable scatter;
+// binning.cu) over WORDS arrays,
 // the digit (arr.in[digit_word] >> shift) & mask (mask <= 255), every segment of `geom`
-// sorted on its own.  `hist` holds segments * per_seg * 256 words.  `f` may be NULL
+// sorted on its own.  `hist` holds (segments * per_seg + 1) * 256 words.  `f` may be NULL
 // (no timing).
 // With iota1 (WORDS == 2, digit word 0), word 1 is not read: each item's is its index within
 // its segment.

@@ -107,12 +107,14 @@ def test_culled_entries_and_the_depth_span(sod, side):
 
 
 def test_ragged_pass_with_more_radix_blocks():
-    n, V, W, VPP = 4_001, 36, 96, 19
+    # 37 radix tiles per view: enough for ceil(608 / 19) = 32 and ceil(608 / 17) = 36 CTAs per
+    # view (a pass's CTAs never outnumber its tiles)
+    n, V, W, VPP = 75_001, 36, 96, 19
     g = synth.gaussians(n, synth.scene_side_mm(W), synth.rng(23, 0))
     views = synth.circular_views(V, W, W)
     dev = to_device(g)
     cfg = FrameConfig(16, 16)
-    f = Frame(n, views, cfg, 1 << 21, views_per_pass=VPP)
+    f = Frame(n, views, cfg, 1 << 23, views_per_pass=VPP)
     image = torch.full((V, W, W), -1.0, device="cuda")
     for first in (0, VPP):
         nv = f.select(first)
@@ -123,7 +125,7 @@ def test_ragged_pass_with_more_radix_blocks():
         assert f.status().code == B.XG_OK
     f.select(0)
     for v in (0, 18, 19, 27, 35):
-        one = Frame(n, [views[v]], cfg, 1 << 19)
+        one = Frame(n, [views[v]], cfg, 1 << 21)
         one.project(*dev)
         one.bin_sort()
         img = torch.empty(1, W, W, device="cuda")
