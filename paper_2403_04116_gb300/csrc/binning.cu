@@ -890,7 +890,15 @@ __global__ void __launch_bounds__(1024) k_work_order(const uint2* __restrict__ r
     const uint2 r = ok ? range[((int64_t)v << tile_bits) + t] : make_uint2(0u, 0u);
     return length_bucket(r.y - r.x);
   };
-  for (int w = threadIdx.x; w < items; w += blockDim.x) atomicAdd(&s_cnt[bucket_of(w)], 1u);
+  // neighbouring tiles have similar list lengths, so the lanes of a warp mostly share a
+  // bucket: one shared atomic per bucket and warp (its leader adds the group)
+  const int lane = threadIdx.x & 31;
+  for (int w0 = threadIdx.x - lane; w0 < items; w0 += blockDim.x) {
+    const int w = w0 + lane;
+    const int b = w < items ? bucket_of(w) : -1;
+    const uint32_t peers = __match_any_sync(0xffffffffu, b);
+    if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[b], (uint32_t)__popc(peers));
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
@@ -900,7 +908,16 @@ __global__ void __launch_bounds__(1024) k_work_order(const uint2* __restrict__ r
     }
   }
   __syncthreads();
-  for (int w = threadIdx.x; w < items; w += blockDim.x) order[atomicAdd(&s_base[bucket_of(w)], 1u)] = (uint32_t)w;
+  for (int w0 = threadIdx.x - lane; w0 < items; w0 += blockDim.x) {
+    const int w = w0 + lane;
+    const int b = w < items ? bucket_of(w) : -1;
+    const uint32_t peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    uint32_t first = 0u;
+    if (b >= 0 && lane == leader) first = atomicAdd(&s_base[b], (uint32_t)__popc(peers));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    if (b >= 0) order[first + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)w;
+  }
 }
 
 // ------------------------------------------------------------------------------------------
