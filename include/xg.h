@@ -144,7 +144,10 @@ typedef struct {
  *   tfinal     float[V][H][W] transmittance after the last contributor
  *   last       uint32[V][H][W] 1-based position in the tile's list of the last contributor
  *   grad2d     float[V*n][8]  per (view, Gaussian): dL/du_x, dL/du_y, dL/da, dL/db, dL/dc,
- *                             dL/dopacity, dL/dintensity, 0 (written by xg_render_bwd) */
+ *                             dL/dopacity, dL/dintensity, 0 (written by xg_render_bwd)
+ *   order      uint32[V*T]    the compositing work items, view * T + tile, by descending
+ *                             bucket of list length (four buckets per octave; the order
+ *                             inside a bucket is unspecified), written by xg_bin_sort */
 typedef struct {
   size_t status, cameras, records, depth, rect, count;
   size_t value, range, tfinal, last, grad2d;
@@ -152,6 +155,7 @@ typedef struct {
   int32_t tiles_x, tiles_y;
   int32_t sort_passes;  /* radix passes over the V*n entries */
   int32_t range_stride; /* S: power of two >= tiles_per_view */
+  size_t order;
 } xg_layout;
 
 typedef struct xg_frame xg_frame;

@@ -66,7 +66,7 @@ class XgLayout(ctypes.Structure):
                 ("status", "cameras", "records", "depth", "rect", "count", "value", "range", "tfinal", "last",
                  "grad2d")] + [
         ("tiles_per_view", ctypes.c_int64), ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
-        ("sort_passes", ctypes.c_int32), ("range_stride", ctypes.c_int32)]
+        ("sort_passes", ctypes.c_int32), ("range_stride", ctypes.c_int32), ("order", ctypes.c_size_t)]
 
 
 class XgRawGaussians(ctypes.Structure):

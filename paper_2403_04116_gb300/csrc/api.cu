@@ -97,7 +97,7 @@ bool sizes_of(const xg_config* cfg, int64_t n, int64_t n_views, int32_t W, int32
 // Byte offsets of every array in the workspace, public and private, in allocation order.
 struct Offsets {
   size_t status, cameras, records, depth, rect, count;
-  size_t ent_depth[2], ent_gid[2], value, hist, key_span, bin_hist, bin_total, range, order, tfinal, last, grad2d;
+  size_t ent_depth[2], ent_gid[2], value, hist, key_span, bin_hist, bin_total, range, order, order_base, tfinal, last, grad2d;
   size_t total;
 };
 
@@ -131,6 +131,7 @@ bool make_offsets(const xg_config* cfg, int64_t n, int32_t V, int32_t n_scan, in
   o->bin_total = take(4 * (size_t)V * (size_t)s->tiles_per_view);
   o->range = take(8 * (size_t)s->range_keys);
   o->order = take(4 * (size_t)V * (size_t)s->tiles_per_view);
+  o->order_base = take(4 * (size_t)xg::kOrderBuckets);
   o->tfinal = take(4 * pix);
   o->last = take(4 * pix);
   o->grad2d = take(4 * 8 * VN);
@@ -281,6 +282,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   p.bin_total = (uint32_t*)(base + o.bin_total);
   p.range = (uint2*)(base + o.range);
   p.order = (uint32_t*)(base + o.order);
+  p.order_base = (uint32_t*)(base + o.order_base);
   p.tfinal = (float*)(base + o.tfinal);
   p.last = (uint32_t*)(base + o.last);
   p.grad2d = (float*)(base + o.grad2d);
@@ -297,6 +299,7 @@ xg_status xg_frame_create(xg_frame** out, const xg_config* cfg, int64_t n, const
   L.tfinal = o.tfinal;
   L.last = o.last;
   L.grad2d = o.grad2d;
+  L.order = o.order;
   L.tiles_per_view = s.tiles_per_view;
   L.tiles_x = s.tiles_x;
   L.tiles_y = s.tiles_y;

@@ -571,13 +571,33 @@ __global__ void __launch_bounds__(256) k_bin_colscan(BinGeom g, const DevStatus*
   }
 }
 
+// The compositing kernels take the (view, tile) work items in order of descending list
+// length bucket (four buckets per octave), so the long lists start in the first waves and
+// the short ones fill the tail.  k_bin_base counts the items of every bucket as it writes
+// the ranges and leaves each bucket's first position in order_base; k_work_order, a grid
+// of CTAs, then places its items: one shared atomic per run of lanes with the same bucket
+// (neighbouring tiles mostly share a bucket), one global atomic per bucket and CTA.
+constexpr int kOrderThreads = 512;
+
+__device__ __forceinline__ int length_bucket(uint32_t len) {
+  if (len == 0) return 0;
+  const int lead = 31 - __clz(len);                                    // floor(log2 len)
+  const int frac = lead >= 2 ? (int)((len >> (lead - 2)) & 3u) : (int)((len << (2 - lead)) & 3u);
+  return 1 + 4 * lead + frac;                                          // 1 .. 128
+}
+
 // Stage 3b: the exclusive prefix of bin_total in (tile, view) order gives every (view,
 // tile) list its place; written as range[view << B | tile] = [start, end), with [0, 0) for
 // empty lists and the keys past the last tile.  The pair count and the capacity check go to the status word
-// (on a failed stage 1 or capacity overflow every range is empty).  One CTA.
+// (on a failed stage 1 or capacity overflow every range is empty).  The items of each list
+// length bucket are counted on the way, and order_base[b] receives the first work-order
+// position of bucket b (longest first).  One CTA.
 __global__ void __launch_bounds__(1024) k_bin_base(BinGeom g, int64_t capacity, const uint32_t* __restrict__ bin_total,
-                                                   DevStatus* __restrict__ st, uint2* __restrict__ range) {
+                                                   DevStatus* __restrict__ st, uint2* __restrict__ range,
+                                                   uint32_t* __restrict__ order_base) {
   __shared__ unsigned long long s_warp[32];
+  __shared__ uint32_t s_bucket[kOrderBuckets];
+  for (int b = threadIdx.x; b < kOrderBuckets; b += 1024) s_bucket[b] = 0u;
   const bool failed = st->code != XG_OK;
   const int64_t nb = g.tiles * g.n_views;
   const int64_t per = (nb + 1023) / 1024;
@@ -593,7 +613,34 @@ __global__ void __launch_bounds__(1024) k_bin_base(BinGeom g, int64_t capacity, 
     const int64_t t = q / g.n_views;
     const int64_t v = q - t * g.n_views;
     range[(v << g.tile_bits) + t] = c ? make_uint2((uint32_t)run, (uint32_t)(run + c)) : make_uint2(0u, 0u);
+    atomicAdd(&s_bucket[length_bucket(c)], 1u);
     run += c;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // descending exclusive scan of the bucket counts: lane l takes buckets 128 - 5l .. 124 - 5l
+    const int lane = threadIdx.x;
+    uint32_t own = 0u;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const int b = kOrderBuckets - 1 - (5 * lane + j);
+      if (b >= 0) own += s_bucket[b];
+    }
+    uint32_t incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t at = incl - own;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const int b = kOrderBuckets - 1 - (5 * lane + j);
+      if (b >= 0) {
+        order_base[b] = at;
+        at += s_bucket[b];
+      }
+    }
   }
   const int64_t pad = ((int64_t)1 << g.tile_bits) - g.tiles;
   for (int64_t k = threadIdx.x; k < pad * g.n_views; k += 1024) {
@@ -865,58 +912,52 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinGeom g, SortedPl
   if (bad) st->code = XG_ERR_CHECK;
 }
 
-// The compositing kernels take the (view, tile) work items in this order: by descending
-// bucket of list length (four buckets per octave), so the long lists start in the first
-// waves and the short ones fill the tail.  One CTA: a histogram, its scan, a scatter.
-constexpr int kOrderBuckets = 129;
-
-__device__ __forceinline__ int length_bucket(uint32_t len) {
-  if (len == 0) return 0;
-  const int lead = 31 - __clz(len);                                    // floor(log2 len)
-  const int frac = lead >= 2 ? (int)((len >> (lead - 2)) & 3u) : (int)((len << (2 - lead)) & 3u);
-  return 1 + 4 * lead + frac;                                          // 1 .. 128
-}
-
-__global__ void __launch_bounds__(1024) k_work_order(const uint2* __restrict__ range, int n_views, int tiles_per_view,
-                                                     int tile_bits, const DevStatus* __restrict__ st,
-                                                     uint32_t* __restrict__ order) {
+// The work order (see k_bin_base): one item per thread; an item of bucket b lands at
+// order_base[b] (advanced by one global atomic per bucket and CTA) plus its place among the
+// CTA's items of that bucket.  The ranges k_bin_base wrote give the lengths it counted, so
+// every position lies inside the array; a position outside it (ranges from another call)
+// records XG_ERR_CHECK and is not written.
+__global__ void __launch_bounds__(kOrderThreads) k_work_order(const uint2* __restrict__ range, int n_views,
+                                                              int tiles_per_view, int tile_bits,
+                                                              DevStatus* __restrict__ st,
+                                                              uint32_t* __restrict__ order_base,
+                                                              uint32_t* __restrict__ order) {
   __shared__ uint32_t s_cnt[kOrderBuckets], s_base[kOrderBuckets];
   const int items = n_views * tiles_per_view;
-  const bool ok = st->code == XG_OK;
-  for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_cnt[b] = 0;
+  for (int b = threadIdx.x; b < kOrderBuckets; b += kOrderThreads) s_cnt[b] = 0u;
   __syncthreads();
-  auto bucket_of = [&](int w) {
-    const int v = w / tiles_per_view, t = w - v * tiles_per_view;
-    const uint2 r = ok ? range[((int64_t)v << tile_bits) + t] : make_uint2(0u, 0u);
-    return length_bucket(r.y - r.x);
-  };
-  // neighbouring tiles have similar list lengths, so the lanes of a warp mostly share a
-  // bucket: one shared atomic per bucket and warp (its leader adds the group)
   const int lane = threadIdx.x & 31;
-  for (int w0 = threadIdx.x - lane; w0 < items; w0 += blockDim.x) {
-    const int w = w0 + lane;
-    const int b = w < items ? bucket_of(w) : -1;
-    const uint32_t peers = __match_any_sync(0xffffffffu, b);
-    if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[b], (uint32_t)__popc(peers));
+  const uint32_t le_mask = 0xffffffffu >> (31 - lane);  // lanes 0 .. lane
+  const int w = (int)blockIdx.x * kOrderThreads + (int)threadIdx.x;
+  int b = -1;
+  if (w < items) {
+    const int v = w / tiles_per_view, t = w - v * tiles_per_view;
+    const uint2 r = range[((int64_t)v << tile_bits) + t];
+    b = length_bucket(r.y - r.x);
+  }
+  // runs of consecutive lanes with the same bucket: a lane leads a run if its bucket differs
+  // from the previous lane's; the leader reserves the run's places
+  const int prev = __shfl_up_sync(0xffffffffu, b, 1);
+  const uint32_t leads = __ballot_sync(0xffffffffu, lane == 0 || b != prev);
+  const uint32_t after = leads & ~le_mask;
+  const int run_end = after ? __ffs(after) - 1 : 32;
+  const int leader = 31 - __clz(leads & le_mask);
+  uint32_t local = 0u;
+  if (b >= 0 && leader == lane) local = atomicAdd(&s_cnt[b], (uint32_t)(run_end - lane));
+  local = __shfl_sync(0xffffffffu, local, leader) + (uint32_t)(lane - leader);
+  __syncthreads();
+  for (int k = threadIdx.x; k < kOrderBuckets; k += kOrderThreads) {
+    const uint32_t c = s_cnt[k];
+    s_base[k] = c ? atomicAdd(&order_base[k], c) : 0u;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int b = kOrderBuckets - 1; b >= 0; --b) {  // longest first
-      s_base[b] = run;
-      run += s_cnt[b];
+  if (b >= 0) {
+    const uint32_t at = s_base[b] + local;
+    if (at < (uint32_t)items) {
+      order[at] = (uint32_t)w;
+    } else {
+      st->code = XG_ERR_CHECK;
     }
-  }
-  __syncthreads();
-  for (int w0 = threadIdx.x - lane; w0 < items; w0 += blockDim.x) {
-    const int w = w0 + lane;
-    const int b = w < items ? bucket_of(w) : -1;
-    const uint32_t peers = __match_any_sync(0xffffffffu, b);
-    const int leader = __ffs(peers) - 1;
-    uint32_t first = 0u;
-    if (b >= 0 && lane == leader) first = atomicAdd(&s_base[b], (uint32_t)__popc(peers));
-    first = __shfl_sync(0xffffffffu, first, leader);
-    if (b >= 0) order[first + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)w;
   }
 }
 
@@ -1052,7 +1093,7 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   }
   {
     Timed t(f, kBinBase, st);
-    k_bin_base<<<1, 1024, 0, st>>>(g, f->cfg.pair_capacity, p.bin_total, p.status, p.range);
+    k_bin_base<<<1, 1024, 0, st>>>(g, f->cfg.pair_capacity, p.bin_total, p.status, p.range, p.order_base);
   }
   {
     Timed t(f, kBinScatter, st);
@@ -1066,7 +1107,9 @@ cudaError_t launch_bin_sort(xg_frame* f, cudaStream_t st) {
   }
   {
     Timed t(f, kWorkOrder, st);
-    k_work_order<<<1, 1024, 0, st>>>(p.range, f->n_views, (int)f->tiles_per_view, f->tile_bits, p.status, p.order);
+    const int64_t items = (int64_t)f->n_views * f->tiles_per_view;
+    k_work_order<<<(unsigned)((items + kOrderThreads - 1) / kOrderThreads), kOrderThreads, 0, st>>>(
+        p.range, f->n_views, (int)f->tiles_per_view, f->tile_bits, p.status, p.order_base, p.order);
   }
   return cudaGetLastError();
 }

@@ -33,8 +33,9 @@
 // branch-free sequence: a pixel that does not take the entry gets alpha = 0, which leaves
 // its state and terms exactly unchanged.  A warp with contributing pixels then sums its 7
 // per-pixel terms -- six moments of dL/dpower (S_1, S_x, S_y, S_xx, S_xy, S_yy
-// over the pixel offsets d = u - p) and the intensity term -- with an 8-value
-// reduce-scatter butterfly (9 shuffles; lane k ends with the sum of term k), and lanes 0-6
+// over the pixel offsets d = u - p) and the intensity term -- by a transpose through the
+// current ring slot (each lane writes its 7 values, four lanes per term add 8 each, two
+// shuffles combine them; lane k ends with the sum of term k), and lanes 0-6
 // add them to the (view, Gaussian)'s sums in global memory in one atomic instruction.  The
 // projection's backward pass turns the sums into dL/du, dL/dconic and dL/dopacity.
 //
@@ -175,25 +176,25 @@ __device__ __forceinline__ void add_counts(uint32_t ev, uint32_t nc, unsigned lo
   }
 }
 
-// Sum of v[k] over the warp for k = 0..7, scattered: returns the total of term (lane & 7)
-// in every lane (lanes 0..7 hold terms 0..7).  9 shuffles.
-__device__ __forceinline__ float warp_reduce_scatter8_low(const float (&v)[8], int lane) {
-  float a[4], c[2];
-  const bool b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+// Sums over the warp of the 7 per-lane values v[0..6] through shared memory, with no
+// lane-dependent register selection: lane j writes v[t] to row t (a row of 36 words: 32 lanes
+// and 4 of padding), then lane l adds the 8 values of row (l & 7) written by lanes
+// 8 (l >> 3) .. 8 (l >> 3) + 7 (two 16-byte loads; rows 36 words apart put the 8 lanes of
+// each quarter-warp load on distinct banks) and two shuffles combine the four lanes of the
+// same row.  Lanes 0..6 return the sums of terms 0..6; lanes with (l & 7) == 7 re-read row 6
+// and return a value that is not used.  `buf` holds 7 x 36 words; the warp must be
+// converged.
+__device__ __forceinline__ float warp_sum7_transposed(const float (&v)[7], float* buf, int lane) {
+  __syncwarp();  // the previous call's loads are done before the rows are rewritten
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float send = b2 ? v[k] : v[k + 4];
-    a[k] = (b2 ? v[k + 4] : v[k]) + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const float send = b1 ? a[k] : a[k + 2];
-    c[k] = (b1 ? a[k + 2] : a[k]) + __shfl_xor_sync(0xffffffffu, send, 2);
-  }
-  float d = (b0 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b0 ? c[0] : c[1], 1);
-  d += __shfl_xor_sync(0xffffffffu, d, 8);
-  d += __shfl_xor_sync(0xffffffffu, d, 16);
-  return d;
+  for (int t = 0; t < 7; ++t) buf[t * 36 + lane] = v[t];
+  __syncwarp();
+  const int row = min(lane & 7, 6);
+  const float4* src = reinterpret_cast<const float4*>(buf + row * 36 + 8 * (lane >> 3));
+  const float4 a = src[0], b = src[1];
+  float s = fadd(fadd(fadd(a.x, a.y), fadd(a.z, a.w)), fadd(fadd(b.x, b.y), fadd(b.z, b.w)));
+  s = fadd(s, __shfl_xor_sync(0xffffffffu, s, 8));
+  return fadd(s, __shfl_xor_sync(0xffffffffu, s, 16));
 }
 
 // T / om for om in [0.01, 1] and T in (0, 1], lane by lane: the hardware reciprocal r0
@@ -563,14 +564,14 @@ __global__ void __launch_bounds__(512) k_render_bwd(const RenderArgs A) {
           }
         }
         if (__any_sync(0xffffffffu, any_ok)) {
-          float gv[8];
+          float gv[7];
 #pragma unroll
           for (int t = 0; t < 7; ++t) gv[t] = gm[t].x + gm[t].y;
-          gv[7] = 0.f;
           // sums over the block's pixels: S_x, S_y, S_xx, S_xy, S_yy, S_1 of dp = dL/dpower
           // times (d, d d^T, 1), and dL/dintensity; lane k (k < 7) ends with the sum of term
-          // k, added to the Gaussian's sums
-          const float sum = warp_reduce_scatter8_low(gv, lane);
+          // k, added to the Gaussian's sums.  The rows are the current ring slot's record
+          // area: its records were staged above and the slot is refilled only next round.
+          const float sum = warp_sum7_transposed(gv, reinterpret_cast<float*>(ring + sq * 64), lane);
           if (lane < 7) atomicAdd(A.g2d + 8 * (vn_base + gk) + lane, sum);
         }
       }

@@ -38,6 +38,8 @@ constexpr int kBinGroupTiles = 2048;
 // iteration limit of every spin-wait in a kernel; on expiry the kernel records
 // XG_ERR_CHECK in the status word and returns
 constexpr uint32_t kSpinLimit = 1u << 22;
+// buckets of tile-list length that order the compositing work items (four per octave)
+constexpr int kOrderBuckets = 129;
 // The limit the kernels' first waits use: kSpinLimit, or the XG_SPIN_LIMIT environment
 // variable (read once per process) to make waits expire for fault-injection tests.  Waits
 // that drain copies in flight before a kernel returns always use kSpinLimit.
@@ -186,6 +188,7 @@ struct FramePtrs {
   uint32_t* bin_total;  // [T][V]: pairs per (tile, view)
   uint2* range;       // [V << tile_bits]
   uint32_t* order;    // [V*T] (view, tile) work items, longest tile lists first
+  uint32_t* order_base;  // [kOrderBuckets]: first work-order position of each list-length bucket
   float* tfinal;      // [V*H*W]
   uint32_t* last;     // [V*H*W]
   float* grad2d;      // [V*n][8]

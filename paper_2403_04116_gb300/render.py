@@ -147,6 +147,7 @@ class Frame:
             "count": (torch.int32, (VN,)), "value": (torch.int32, (cap,)),
             "range": (torch.int32, (self.V * self.range_stride, 2)), "tfinal": (torch.float32, (P,)),
             "last": (torch.int32, (P,)), "grad2d": (torch.float32, (VN, 8)),
+            "order": (torch.int32, (self.V * self.layout.tiles_per_view,)),
         }
         dtype, shape = spec[name]
         off = getattr(self.layout, name)

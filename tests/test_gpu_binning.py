@@ -134,3 +134,37 @@ def test_ragged_pass_with_more_radix_blocks():
         assert torch.equal(img[0], image[v]), v
     rep = oracle.replica_full(g, views[35], (16, 16))
     np.testing.assert_array_equal(image[35].cpu().numpy().view(np.uint32), rep["image"].view(np.uint32))
+
+
+def _length_bucket(n: np.ndarray) -> np.ndarray:
+    """Four buckets per octave of list length: 0 for an empty list, else 1 + 4 floor(log2 n)
+    + the two bits below the leading one."""
+    n = n.astype(np.int64)
+    out = np.zeros(n.shape, np.int64)
+    nz = n > 0
+    lead = np.floor(np.log2(np.where(nz, n, 1))).astype(np.int64)
+    frac = np.where(lead >= 2, (n >> np.maximum(lead - 2, 0)) & 3, (n << np.maximum(2 - lead, 0)) & 3)
+    out[nz] = 1 + 4 * lead[nz] + frac[nz]
+    return out
+
+
+@pytest.mark.parametrize("views_n,tile", [(50, (16, 8)), (7, (8, 8))])
+def test_work_order_is_longest_first_permutation(views_n, tile):
+    """The compositing work items: every (view, tile) exactly once, by non-increasing bucket
+    of list length (more items than the ordering CTA's threads times its unroll)."""
+    n, W, cid = 8_000, 256, 26
+    g = synth.gaussians(n, synth.scene_side_mm(W), synth.rng(cid, 0))
+    views = synth.circular_views(views_n, W, W)
+    gpu = run_forward(g, views, tile)
+    f = gpu["frame"]
+    T = int(f.layout.tiles_per_view)
+    items = views_n * T
+    order = f.array("order").cpu().numpy().view(np.uint32).astype(np.int64)
+    assert order.size == items and (items > 8 * 1024) == (views_n == 50)
+    np.testing.assert_array_equal(np.sort(order), np.arange(items))
+    v, t = order // T, order % T
+    rng = gpu["range"].astype(np.int64)
+    length = rng[v * f.range_stride + t, 1] - rng[v * f.range_stride + t, 0]
+    b = _length_bucket(length)
+    assert (np.diff(b) <= 0).all()
+    assert b[0] == _length_bucket(np.array([length.max()]))[0] and length.max() > 0
