@@ -8,8 +8,8 @@
 // k_project_bwd: the chain rule back from the per-(view, Gaussian) sums the compositing
 // backward pass writes (moments of dL/dpower over the pixel offsets, and dL/dintensity):
 // first to dL/du, dL/dconic and dL/dopacity of each view (written back in place of the
-// sums), then to mean, scale, quaternion, opacity and intensity; one thread per Gaussian sums
-// its views in registers.
+// sums), then to mean, scale, quaternion, opacity and intensity; eight threads per Gaussian
+// (one per warp of a block) sum its views, each every eighth view.
 #include "xg_internal.cuh"
 
 namespace xg {
@@ -156,28 +156,42 @@ cudaError_t launch_project(xg_frame* f, const xg_gaussians* g, cudaStream_t st) 
 // backward
 // ------------------------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ mean, const float* __restrict__ scale,
+// k_project_bwd: a block takes 32 Gaussians (one per lane) and its 8 warps split the views
+// (warp w takes views w, w + 8, ...); the warps' partial sums meet in shared memory and
+// warp 0 finishes the chain rule.  The kernel waits on its loads more than it computes, so
+// it is compiled for 4 resident blocks per SM (64 registers).
+constexpr int kPbGaussians = 32;
+constexpr int kPbWarps = 8;
+
+__global__ void __launch_bounds__(32 * kPbWarps, 4) k_project_bwd(const float* __restrict__ mean, const float* __restrict__ scale,
                                                      const float* __restrict__ quat, const float* __restrict__ opac,
                                                      int64_t n, int n_views,
                                                      const Camera* __restrict__ cams, float* __restrict__ g2d,
                                                      const DevStatus* __restrict__ status, float* __restrict__ g_mean,
                                                      float* __restrict__ g_scale, float* __restrict__ g_quat,
                                                      float* __restrict__ g_opac, float* __restrict__ g_inten) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n) return;
+  // per warp and Gaussian: the partial sums over the warp's views (gS: 6 of the symmetric
+  // 3x3, mean: 3, S_1, dL/dintensity), a padded column per Gaussian
+  __shared__ float s_part[kPbWarps][11][kPbGaussians + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t g = (int64_t)blockIdx.x * kPbGaussians + lane;
+  const bool live = g < n;
   float gm[3] = {0.f, 0.f, 0.f}, gsc[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
   float go = 0.f, gi = 0.f;
+  float gSu[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma, upper triangle (symmetric)
+  float s1 = 0.f;  // sum over views of S_1
+  float w = 0.f, x = 0.f, y = 0.f, z = 0.f, inv = 0.f, R[3][3] = {}, M[3][3] = {};
 
-  const float mx = mean[g], my = mean[n + g], mz = mean[2 * n + g];
-  const float s3[3] = {scale[g], scale[n + g], scale[2 * n + g]};
-  const float q4[4] = {quat[g], quat[n + g], quat[2 * n + g], quat[3 * n + g]};
+  const int64_t gl = live ? g : 0;  // lanes past n load Gaussian 0 and store nothing
+  const float mx = mean[gl], my = mean[n + gl], mz = mean[2 * n + gl];
+  const float s3[3] = {scale[gl], scale[n + gl], scale[2 * n + gl]};
+  const float q4[4] = {quat[gl], quat[n + gl], quat[2 * n + gl], quat[3 * n + gl]};
   const float qq = q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3];
-  const bool usable = status->code == XG_OK && qq > 0.f && isfinite(qq) && isfinite(mx) && isfinite(my) &&
+  const bool usable = live && status->code == XG_OK && qq > 0.f && isfinite(qq) && isfinite(mx) && isfinite(my) &&
                       isfinite(mz) && isfinite(s3[0]) && isfinite(s3[1]) && isfinite(s3[2]);
   if (usable) {
-    const float inv = rsqrtf(qq);
-    const float w = q4[0] * inv, x = q4[1] * inv, y = q4[2] * inv, z = q4[3] * inv;
-    float R[3][3];
+    inv = rsqrtf(qq);
+    w = q4[0] * inv, x = q4[1] * inv, y = q4[2] * inv, z = q4[3] * inv;
     R[0][0] = 1.f - 2.f * (y * y + z * z);
     R[0][1] = 2.f * (x * y - w * z);
     R[0][2] = 2.f * (x * z + w * y);
@@ -187,20 +201,19 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ m
     R[2][0] = 2.f * (x * z - w * y);
     R[2][1] = 2.f * (y * z + w * x);
     R[2][2] = 1.f - 2.f * (x * x + y * y);
-    float M[3][3];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int k = 0; k < 3; ++k) M[r][k] = R[r][k] * s3[k];
-    float S[3][3];
+    // Sigma = M M^T, symmetric: its 6 entries S[r][k], r <= k, in Su (row-major upper triangle)
+    float Su[6];
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
+    for (int r = 0, i = 0; r < 3; ++r)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) S[r][k] = M[r][0] * M[k][0] + M[r][1] * M[k][1] + M[r][2] * M[k][2];
-    float gS[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-
-    float s1 = 0.f;  // sum over views of S_1
-    for (int v = 0; v < n_views; ++v) {
+      for (int k = r; k < 3; ++k, ++i) Su[i] = M[r][0] * M[k][0] + M[r][1] * M[k][1] + M[r][2] * M[k][2];
+    auto S = [&](int r, int k) { return r <= k ? Su[r * 3 + k - (r * (r + 1)) / 2] : Su[k * 3 + r - (k * (k + 1)) / 2]; };
+    // this warp's views: warp, warp + kPbWarps, ...
+    for (int v = warp; v < n_views; v += kPbWarps) {
       const int64_t vg = (int64_t)v * n + g;
       // the compositing pass's sums over the view's pixels: S_x, S_y, S_xx, S_xy, S_yy, S_1
       // of dp = dL/dpower times (d, d d^T, 1), and dL/dintensity
@@ -220,8 +233,8 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ m
       float ST0[3], ST1[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        ST0[r] = S[r][0] * T0[0] + S[r][1] * T0[1] + S[r][2] * T0[2];
-        ST1[r] = S[r][0] * T1[0] + S[r][1] * T1[1] + S[r][2] * T1[2];
+        ST0[r] = S(r, 0) * T0[0] + S(r, 1) * T0[1] + S(r, 2) * T0[2];
+        ST1[r] = S(r, 0) * T1[0] + S(r, 1) * T1[1] + S(r, 2) * T1[2];
       }
       const float A = T0[0] * ST0[0] + T0[1] * ST0[1] + T0[2] * ST0[2] + kDilate;
       const float B = T1[0] * ST0[0] + T1[1] * ST0[1] + T1[2] * ST0[2];
@@ -244,10 +257,10 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ m
       const float g11 = -(KG10 * kb + KG11 * kc);
       // Sigma'' = T Sigma T^T + 0.3 I with rows T0, T1
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
+      for (int r = 0, i = 0; r < 3; ++r)
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-          gS[r][k] += g00 * T0[r] * T0[k] + g01 * (T0[r] * T1[k] + T1[r] * T0[k]) + g11 * T1[r] * T1[k];
+        for (int k = r; k < 3; ++k, ++i)
+          gSu[i] += g00 * T0[r] * T0[k] + g01 * (T0[r] * T1[k] + T1[r] * T0[k]) + g11 * T1[r] * T1[k];
       float gT0[3], gT1[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
@@ -271,6 +284,30 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ m
       gm[1] += c * gtx - s * gtz;
       gm[2] += -gty;
     }
+  }
+  {
+    const float part[11] = {gSu[0], gSu[1], gSu[2], gSu[3], gSu[4], gSu[5], gm[0], gm[1], gm[2], s1, gi};
+#pragma unroll
+    for (int k = 0; k < 11; ++k) s_part[warp][k][lane] = part[k];
+  }
+  __syncthreads();
+  if (warp != 0 || !live) return;
+  {
+    float tot[11];
+#pragma unroll
+    for (int k = 0; k < 11; ++k) {
+      tot[k] = 0.f;
+#pragma unroll
+      for (int j = 0; j < kPbWarps; ++j) tot[k] += s_part[j][k][lane];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) gSu[k] = tot[k];
+    gm[0] = tot[6], gm[1] = tot[7], gm[2] = tot[8];
+    s1 = tot[9];
+    gi = tot[10];
+  }
+  if (usable) {
+    const float gS[3][3] = {{gSu[0], gSu[1], gSu[2]}, {gSu[1], gSu[3], gSu[4]}, {gSu[2], gSu[4], gSu[5]}};
     // Sigma = M M^T, M = R S
     float gM[3][3];
 #pragma unroll
@@ -313,7 +350,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ m
 cudaError_t launch_project_bwd(xg_frame* f, const xg_gaussians* g, const xg_grads* out, cudaStream_t st) {
   const int64_t n = f->n;
   Timed t(f, kProjectBwd, st);
-  k_project_bwd<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->mean, g->scale, g->quat, g->opacity, n, f->n_views, f->p.cam,
+  k_project_bwd<<<(unsigned)((n + kPbGaussians - 1) / kPbGaussians), 32 * kPbWarps, 0, st>>>(g->mean, g->scale, g->quat, g->opacity, n, f->n_views, f->p.cam,
                                                              f->p.grad2d, f->p.status, out->mean, out->scale,
                                                              out->quat, out->opacity, out->intensity);
   return cudaGetLastError();
