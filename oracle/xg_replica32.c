@@ -11,8 +11,9 @@
  * pinned against the FP64 oracle and against brute-force checks in the tests.
  *
  * Transcendentals used in a decision are computed here from basic operations:
- *   exp: Cody-Waite reduction by ln 2 (split into its float rounding and the float of the
- *        remainder), then the degree-6 Taylor polynomial of e^r, |r| <= ln2/2, scaled by 2^k;
+ *   exp: k = the integer nearest x log2 e (from one fused multiply-add), Cody-Waite
+ *        reduction by ln 2 (split into its float rounding and the float of the remainder),
+ *        then the degree-6 Taylor polynomial of e^r, |r| <= ln2/2, scaled by 2^k;
  *   log: x = m 2^e with m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh((m-1)/(m+1)) by its odd
  *        series to s^9, plus e ln 2.
  * Readings of the paper used here: focal in pixels L_SD / pitch; pixel centres at
@@ -56,7 +57,9 @@ static uint32_t f_bits(float f) {
 
 float xr_exp(float x) {
   x = fmaxf(x, -80.0f);
-  float k = rintf(x * R_L2E);
+  /* k: the integer nearest x log2 e (ties to even), rounded once from the exact product:
+   * x log2 e + 1.5 * 2^23 in one fmaf keeps it in the last mantissa bits */
+  float k = fmaf(x, R_L2E, 12582912.0f) - 12582912.0f;
   float r = fmaf(k, -R_LN2_HI, x);
   r = fmaf(k, -R_LN2_LO, r);
   float p = fmaf(r, (float)(1.0 / 720.0), (float)(1.0 / 120.0));

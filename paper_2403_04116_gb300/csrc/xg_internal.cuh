@@ -91,9 +91,13 @@ __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b)
 __device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
 
 // e^x: Cody-Waite reduction by ln 2, degree-6 Taylor polynomial on |r| <= ln2/2, times 2^k.
+// k = rint(x log2 e) is the nearest integer (ties to even) to the exact product, taken from
+// one fused multiply-add: m = x log2 e + 1.5 * 2^23 rounded once holds it in its last
+// mantissa bits (|x log2 e| < 2^22), and k = m - 1.5 * 2^23 is exact.
+constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
 __device__ __forceinline__ float xg_exp(float x) {
   x = fmaxf(x, -80.0f);
-  const float k = rintf(fmul(x, kLog2e));
+  const float k = fsub(ffma(x, kLog2e, kRound), kRound);
   float r = ffma(k, -kLn2Hi, x);
   r = ffma(k, -kLn2Lo, r);
   float p = ffma(r, (float)(1.0 / 720.0), (float)(1.0 / 120.0));
@@ -113,25 +117,20 @@ __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// xg_exp of two values, lane for lane bit-identical to it.  The integer k = rint(x log2 e)
-// is rounded per lane with rintf from the rounded product: forming it as
-// (x log2 e + 1.5 * 2^23) - 1.5 * 2^23 with packed instructions let the multiply and the
-// add be evaluated with a single rounding, which moves k by one (and the result by a few
-// ulps) where x log2 e lies within a rounding of a half-integer.  Adding 1.5 * 2^23 to the
-// integer k afterwards is exact and puts k in the low mantissa bits: the bits of
-// k + 1.5 * 2^23 are 0x4B400000 + k, and shifted left by 23 they are k << 23 (the constant's
-// low nine bits are zero).  The scaling by 2^k is then an integer add of k << 23 to the
-// bits of the polynomial's value p: p lies in [0.70, 1.42] and -116 <= k <= 127 (x in
-// [-80, 88], the domain of xg_exp's scale as well), so the result stays normal, and the
-// product p * 2^k that xg_exp rounds is exact -- the same bits.
+// xg_exp of two values, lane for lane bit-identical to it: m and k as in xg_exp, one packed
+// fused multiply-add and one packed add.  The bits of m are 0x4B400000 + k, and shifted
+// left by 23 they are k << 23 (the constant's low nine bits are zero), so the scaling by
+// 2^k is an integer add of those bits to the bits of the polynomial's value p: p lies in
+// [0.70, 1.42] and -116 <= k <= 127 (x in [-80, 88], the domain of xg_exp's scale as
+// well), so the result stays normal, and the product p * 2^k that xg_exp rounds is exact
+// -- the same bits.
 //
 // xg_exp2v_core takes x as it is: its value is xg_exp's for x in [-80, 88] and meaningless
 // below.  The compositing kernels call it directly, because they keep exp only where the
 // exponent reaches the record's threshold (above -6) and discard the other lanes' values.
 __device__ __forceinline__ float2 xg_exp2v_core(float2 x) {
-  constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
-  const float2 xl = fmul2(x, f2(kLog2e));
-  const float2 k = make_float2(rintf(xl.x), rintf(xl.y));
+  const float2 m = ffma2(x, f2(kLog2e), f2(kRound));
+  const float2 k = fadd2(m, f2(-kRound));
   float2 r = ffma2(k, f2(-kLn2Hi), x);
   r = ffma2(k, f2(-kLn2Lo), r);
   float2 p = ffma2(r, f2((float)(1.0 / 720.0)), f2((float)(1.0 / 120.0)));
@@ -140,7 +139,6 @@ __device__ __forceinline__ float2 xg_exp2v_core(float2 x) {
   p = ffma2(p, r, f2(0.5f));
   p = ffma2(p, r, f2(1.0f));
   p = ffma2(p, r, f2(1.0f));
-  const float2 m = fadd2(k, f2(kRound));
   return make_float2(__uint_as_float(__float_as_uint(p.x) + (__float_as_uint(m.x) << 23)),
                      __uint_as_float(__float_as_uint(p.y) + (__float_as_uint(m.y) << 23)));
 }

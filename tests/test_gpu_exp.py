@@ -1,8 +1,9 @@
 """The compositing kernels' decision exponential on the device, scalar and two-lane packed,
 bit-identical to the FP32 replica's (an independent C implementation of the same published
 method) on 16 M inputs: uniform over [-80, 0] and every float within a few ulps of the
-range-reduction boundaries x log2 e = k - 1/2, where rounding x log2 e to k must not be
-fused with anything else (a packed multiply-add there once moved k by one)."""
+range-reduction boundaries x log2 e = k - 1/2, where both sides must take k as the integer
+nearest the exact product x log2 e (one fused multiply-add), not as the rounding of a
+separately rounded product."""
 import numpy as np
 import pytest
 
