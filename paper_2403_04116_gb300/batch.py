@@ -86,34 +86,49 @@ class GraphedStep:
     def replay(self) -> None:
         self.graph.replay()
 
-    def capture_host(self, host_gaussians: tuple, host_target: torch.Tensor) -> None:
+    def capture_host(self, host_gaussians: tuple, host_target: torch.Tensor, slots: int = 2) -> None:
         """Record the step with its transfers: the Gaussians and the targets copied in from
         these pinned host tensors (the targets on a side stream, overlapped with the forward
-        pass and joined before the loss) and the loss copied out to ``host_loss``.  Each
-        replay_host reads whatever the host tensors hold at that moment."""
-        self.host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+        pass and joined before the loss) and the loss copied out to a pinned slot.  ``slots``
+        graphs are recorded, identical but for their loss slot, so a loop can enqueue the
+        next step before it reads the previous step's loss (``replay_host`` then
+        ``loss_of``).  Each replay reads whatever the host tensors hold when its copies run."""
+        self.host_losses = [torch.empty(1, dtype=torch.float32).pin_memory() for _ in range(slots)]
+        self.host_loss = self.host_losses[0]
         self._host_in = (tuple(host_gaussians), host_target)  # keep the sources alive
+        self._host_done = [torch.cuda.Event() for _ in range(slots)]
         copy = torch.cuda.Stream()
         f = self.frame
-        self.graph_host = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph_host):
-            main = torch.cuda.current_stream()
-            for dst, src in zip(self.inputs, host_gaussians):
-                dst.copy_(src, non_blocking=True)
-            copy.wait_stream(main)
-            with torch.cuda.stream(copy):
-                self.target.copy_(host_target, non_blocking=True)
-            f.project(*self.inputs)
-            f.bin_sort()
-            f.render_fwd(self.image)
-            main.wait_stream(copy)
-            loss_l1_into(self.image, self.target, self.grad_image, self.loss)
-            f.render_bwd(self.inputs, self.grad_image, self.grads)
-            self.host_loss.copy_(self.loss, non_blocking=True)
+        self.graphs_host = []
+        for k in range(slots):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                main = torch.cuda.current_stream()
+                for dst, src in zip(self.inputs, host_gaussians):
+                    dst.copy_(src, non_blocking=True)
+                copy.wait_stream(main)
+                with torch.cuda.stream(copy):
+                    self.target.copy_(host_target, non_blocking=True)
+                f.project(*self.inputs)
+                f.bin_sort()
+                f.render_fwd(self.image)
+                main.wait_stream(copy)
+                loss_l1_into(self.image, self.target, self.grad_image, self.loss)
+                f.render_bwd(self.inputs, self.grad_image, self.grads)
+                self.host_losses[k].copy_(self.loss, non_blocking=True)
+            self.graphs_host.append(g)
+        self.graph_host = self.graphs_host[0]
 
-    def replay_host(self) -> None:
-        """One step from the host inputs; ``host_loss`` is valid once the stream reaches it."""
-        self.graph_host.replay()
+    def replay_host(self, slot: int = 0) -> None:
+        """One step from the host inputs, its loss to slot ``slot`` (``host_losses[slot]``,
+        valid once the stream reaches it: ``loss_of``)."""
+        self.graphs_host[slot].replay()
+        self._host_done[slot].record()
+
+    def loss_of(self, slot: int = 0) -> float:
+        """Wait for the last step replayed into ``slot`` and return its loss."""
+        self._host_done[slot].synchronize()
+        return float(self.host_losses[slot][0])
 
 
 class GraphedScan:

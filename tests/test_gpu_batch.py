@@ -88,6 +88,15 @@ def test_graph_with_host_transfers_matches_the_device_step():
         assert float(step.host_loss[0]) == pytest.approx(float(loss), rel=1e-6)
         for a, b in zip(step.grads, grads):
             _close(a.cpu().numpy(), b.cpu().numpy())
+    # pipelined: the step in its second loss slot is enqueued before the first one's loss is
+    # read; both read the same host inputs, so both losses equal the device step's
+    step.replay()
+    torch.cuda.synchronize()
+    loss = float(step.loss)
+    step.replay_host(0)
+    step.replay_host(1)
+    assert step.loss_of(0) == pytest.approx(loss, rel=1e-6)
+    assert step.loss_of(1) == pytest.approx(loss, rel=1e-6)
 
 
 def test_plain_per_view_form_matches_batched():
