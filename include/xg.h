@@ -130,7 +130,10 @@ typedef struct {
 /* Byte offsets, inside the workspace, of the frame's intermediate arrays (for inspection).
  * V views of the current pass, n Gaussians, T tiles per view, cap = pair_capacity; the
  * camera table (at `cameras`) holds every view of the frame:
- *   records    float[V*n][8]  (u_x, u_y, conic a, b, c, opacity, intensity, 0); u centred
+ *   records    float[V*n][8]  (u_x, u_y, -a/2, -b, -c/2, opacity, intensity, thr): (a, b, c)
+ *                             the conic, so the exponent at pixel offset d = u - p is
+ *                             (-a/2) dx^2 + (-b) dx dy + (-c/2) dy^2; thr = -ln(255 opacity)
+ *                             - 1e-4, below which the opacity stays under 1/255; u centred
  *                             on the principal point; zero where the Gaussian touches no tile
  *   depth      float[V*n]     t_z (0 where it touches no tile)
  *   rect       uint16[V*n][4] tile rectangle (x0, y0, x1, y1), inclusive

@@ -101,7 +101,8 @@ static int all_finite(const float* v, int k) {
 
 /*
  * Projection of every Gaussian under one view.
- *   rec[8n]: (u_x, u_y, conic a, b, c, opacity, intensity, -ln(255 opacity) - 1e-4), u centred on
+ *   rec[8n]: (u_x, u_y, -a/2, -b, -c/2 of the conic (a, b, c), opacity, intensity,
+ *   -ln(255 opacity) - 1e-4), u centred on
  *   the principal point; the last field is the exponent below which sigma stays under 1/255
  *   with a margin (a skip test that never changes a decision)
  *   depth[n]: t_z;  rect[4n]: tile rectangle (x0, y0, x1, y1), inclusive;  count[n]: tiles touched
@@ -212,9 +213,9 @@ int64_t xr_project(int64_t n, const float* mean, const float* scale, const float
     int tx0 = (int)x0 / tile_w, tx1 = (int)x1 / tile_w, ty0 = (int)y0 / tile_h, ty1 = (int)y1 / tile_h;
     rg[0] = ux;
     rg[1] = uy;
-    rg[2] = ca;
-    rg[3] = cb;
-    rg[4] = cc;
+    rg[2] = -0.5f * ca; /* the exponent's coefficients (-a/2, -b, -c/2) */
+    rg[3] = -cb;
+    rg[4] = -0.5f * cc;
     rg[5] = o;
     rg[6] = in;
     rg[7] = -lg - 1e-4f; /* exponent below which sigma < 1/255 for sure (the kernels' skip test) */
@@ -311,7 +312,7 @@ void xr_render(const float* rec, const uint32_t* range, const int32_t* list, con
       uint32_t nc = 0, lst = 0;
       for (uint32_t k = b; k < e; ++k) {
         const float* r = rec + 8 * (int64_t)list[k];
-        float na = -0.5f * r[2], nb = -r[3], nc2 = -0.5f * r[4];
+        float na = r[2], nb = r[3], nc2 = r[4];
         float dx = r[0] - px, dy = r[1] - py;
         /* dx (na dx + nb dy) + (nc dy) dy */
         float t = fmaf(na, dx, nb * dy);

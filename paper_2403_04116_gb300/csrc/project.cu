@@ -126,10 +126,12 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ mean,
     const float y0 = fmaxf(ceilf(fsub(cy, rad)), 0.0f), y1 = fminf(floorf(fadd(cy, rad)), (float)(H - 1));
     if (!(x0 <= x1 && y0 <= y1)) break;
     const int tx0 = (int)x0 / tw, tx1 = (int)x1 / tw, ty0 = (int)y0 / th, ty1 = (int)y1 / th;
-    r0 = make_float4(ux, uy, ca, cb);
+    // the exponent's coefficients: power = na dx^2 + nb dx dy + nc dy^2 with
+    // (na, nb, nc) = (-a/2, -b, -c/2) of the conic (a, b, c) (exact halvings and negations)
+    r0 = make_float4(ux, uy, fmul(-0.5f, ca), -cb);
     // the exponent below which the opacity stays under 1/255 for sure, with a margin far
     // above the error of the FP32 exp: the compositing kernels skip such pairs
-    r1 = make_float4(cc, o, in, fsub(-lg, 1e-4f));
+    r1 = make_float4(fmul(-0.5f, cc), o, in, fsub(-lg, 1e-4f));
     dz = tz;
     rc = make_ushort4((unsigned short)tx0, (unsigned short)ty0, (unsigned short)tx1, (unsigned short)ty1);
     cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));

@@ -156,7 +156,7 @@ __device__ __forceinline__ float max_power_over_rect(float na, float nb, float n
 __device__ __forceinline__ bool reaches_block(const float4 a, const float4 b, float bx0, float by0, float by1,
                                               const Camera& cam) {
   if (!(b.y > 0.f)) return false;
-  const float na = -0.5f * a.z, nb = -a.w, nc = -0.5f * b.x, thr = b.w;
+  const float na = a.z, nb = a.w, nc = b.x, thr = b.w;
   const float cx = a.x + cam.hw, cy = a.y + cam.hh;
   const float best = max_power_over_rect(na, nb, nc, cx - (bx0 + 7.f), cx - bx0, cy - by1, cy - by0);
   return best >= thr - (1e-2f + 1e-3f * fabsf(thr));
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(512) k_render_fwd(const RenderArgs A) {
         const int k = __ffs(mask) - 1;
         mask &= mask - 1;
         const float4 a = slot[2 * k], b = slot[2 * k + 1];
-        const float na = -0.5f * a.z, nb = -a.w, nc2 = -0.5f * b.x;
+        const float na = a.z, nb = a.w, nc2 = b.x;
         fwd_entry<NP>(make_float4(a.x, a.x, a.y, a.y), make_float4(na, na, nb, nb), make_float4(nc2, nc2, b.y, b.y),
                       make_float4(b.z, b.z, b.w, b.w), (uint32_t)(32 * q + k + 1), npx, npy, T, C, nc, lastp, done,
                       nev);
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(512) k_render_bwd(const RenderArgs A) {
         const float4 a = slot[2 * lane], b = slot[2 * lane + 1];
         hit = reaches_block(a, b, bx0, by0, by1, cam);
         if (hit) {
-          const float na = -0.5f * a.z, nb = -a.w, nc = -0.5f * b.x;
+          const float na = a.z, nb = a.w, nc = b.x;
           stage[lane] = make_float4(a.x, a.x, a.y, a.y);
           stage[32 + lane] = make_float4(na, na, nb, nb);
           stage[64 + lane] = make_float4(nc, nc, b.y, b.y);
