@@ -73,10 +73,10 @@ FP32_LANES = 128
 # source (sha256 prefix of its .cu file and the shared header), workload and (tile_w,
 # tile_h, batch, pixels_per_thread, persistent) they were taken with.
 TRAFFIC = [
-    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "3e23bff8af7b69b5",
-     "bytes_per_launch": 359.9e6},
-    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "3e23bff8af7b69b5",
-     "bytes_per_launch": 149.5e6},
+    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "ccd96c6bc1437efe",
+     "bytes_per_launch": 358.7e6},
+    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "ccd96c6bc1437efe",
+     "bytes_per_launch": 149.7e6},
 ]
 
 
