@@ -608,13 +608,16 @@ __global__ void __launch_bounds__(1024) k_bin_base(BinGeom g, int64_t capacity, 
   unsigned long long total;
   unsigned long long run = block_exclusive_scan<1024>(sum, s_warp, total);
   const bool ok = !failed && total <= (unsigned long long)capacity;
+  int64_t t = q0 / g.n_views, v = q0 - t * g.n_views;  // q = t * V + v, advanced in step with q
   for (int64_t q = q0; q < q1; ++q) {
     const uint32_t c = ok ? bin_total[q] : 0u;
-    const int64_t t = q / g.n_views;
-    const int64_t v = q - t * g.n_views;
     range[(v << g.tile_bits) + t] = c ? make_uint2((uint32_t)run, (uint32_t)(run + c)) : make_uint2(0u, 0u);
     atomicAdd(&s_bucket[length_bucket(c)], 1u);
     run += c;
+    if (++v == g.n_views) {
+      v = 0;
+      ++t;
+    }
   }
   __syncthreads();
   if (threadIdx.x < 32) {

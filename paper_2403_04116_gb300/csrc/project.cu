@@ -17,7 +17,7 @@ namespace xg {
 __global__ void __launch_bounds__(256) k_project(const float* __restrict__ mean, const float* __restrict__ scale,
                                                  const float* __restrict__ quat, const float* __restrict__ opac,
                                                  const float* __restrict__ inten, int64_t n,
-                                                 const Camera* __restrict__ cams, int W, int H, int tw, int th,
+                                                 const Camera* __restrict__ cams, int W, int H, int tw_shift, int th_shift,
                                                  float near_mm, float4* __restrict__ rec, float* __restrict__ depth,
                                                  ushort4* __restrict__ rect, uint32_t* __restrict__ count,
                                                  DevStatus* __restrict__ status) {
@@ -125,7 +125,9 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ mean,
     const float x0 = fmaxf(ceilf(fsub(cx, rad)), 0.0f), x1 = fminf(floorf(fadd(cx, rad)), (float)(W - 1));
     const float y0 = fmaxf(ceilf(fsub(cy, rad)), 0.0f), y1 = fminf(floorf(fadd(cy, rad)), (float)(H - 1));
     if (!(x0 <= x1 && y0 <= y1)) break;
-    const int tx0 = (int)x0 / tw, tx1 = (int)x1 / tw, ty0 = (int)y0 / th, ty1 = (int)y1 / th;
+    // tile sizes are powers of two (8, 16 or 32) and the pixel indices non-negative
+    const int tx0 = (int)x0 >> tw_shift, tx1 = (int)x1 >> tw_shift, ty0 = (int)y0 >> th_shift,
+              ty1 = (int)y1 >> th_shift;
     // the exponent's coefficients: power = na dx^2 + nb dx dy + nc dy^2 with
     // (na, nb, nc) = (-a/2, -b, -c/2) of the conic (a, b, c) (exact halvings and negations)
     r0 = make_float4(ux, uy, fmul(-0.5f, ca), -cb);
@@ -149,7 +151,8 @@ cudaError_t launch_project(xg_frame* f, const xg_gaussians* g, cudaStream_t st) 
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)f->n_views);
   Timed t(f, kProject, st);
   k_project<<<grid, 256, 0, st>>>(g->mean, g->scale, g->quat, g->opacity, g->intensity, n, f->p.cam, f->width,
-                                  f->height, f->cfg.tile_w, f->cfg.tile_h, f->cfg.near_mm, f->p.rec, f->p.depth,
+                                  f->height, __builtin_ctz((unsigned)f->cfg.tile_w),
+                                  __builtin_ctz((unsigned)f->cfg.tile_h), f->cfg.near_mm, f->p.rec, f->p.depth,
                                   f->p.rect, f->p.count, f->p.status);
   return cudaGetLastError();
 }
