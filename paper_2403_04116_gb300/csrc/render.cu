@@ -524,9 +524,10 @@ __global__ void __launch_bounds__(512) k_render_bwd(const RenderArgs A) {
           any_in |= in[pr][0] || in[pr][1];
         }
         if (!__any_sync(0xffffffffu, any_in)) continue;  // no pixel of the warp can reach 1/255
-        // packed sums over the thread's pixels: six moments of dp = dL/dpower (dp, dp d,
-        // dp d d^T) and dL/dintensity
-        float2 gm[7];
+        // sums over the thread's pixels of the six moments of dp = dL/dpower (dp, dp d,
+        // dp d d^T) and of dL/dintensity.  The pixels of a pair share their column, so
+        // dx is the same for both: S_x = S_1 dx, S_xx = S_x dx and S_xy = S_y dx.
+        float gv[7];  // S_x, S_y, S_xx, S_xy, S_yy, S_1, dL/di
         bool any_ok = false;
 #pragma unroll
         for (int pr = 0; pr < NP; ++pr) {
@@ -539,34 +540,26 @@ __global__ void __launch_bounds__(512) k_render_bwd(const RenderArgs A) {
           const float2 omal = ffma2(alm, f2(-1.0f), f2(1.0f));
           Tc[pr] = div_recover(Tc[pr], omal);
           const float2 gw = fmul2(G[pr], Tc[pr]);  // dL/dC T; gw alm is the dL/d intensity term
-          const float2 dl_dal = fmul2(gw, ffma2(Ab[pr], f2(-1.0f), make_float2(q3.x, q3.y)));
-          Ab[pr] = ffma2(alm, make_float2(q3.x, q3.y), fmul2(omal, Ab[pr]));
+          const float2 ib = ffma2(Ab[pr], f2(-1.0f), make_float2(q3.x, q3.y));  // i - Ab
+          const float2 dl_dal = fmul2(gw, ib);
+          Ab[pr] = ffma2(alm, ib, Ab[pr]);  // Ab + alpha (i - Ab): the blend behind the previous entry
           // dp = dL/dalpha alpha where the opacity is not clamped (the clamp has zero slope)
           const float2 aln = make_float2(oe.x < kAlphaMax ? alm.x : 0.f, oe.y < kAlphaMax ? alm.y : 0.f);
           const float2 dp = fmul2(dl_dal, aln);
-          const float2 sx = fmul2(dp, dx), sy = fmul2(dp, dyv[pr]);
+          const float2 sy = fmul2(dp, dyv[pr]);
+          const float2 di = fmul2(gw, alm);
+          const float s1 = fadd(dp.x, dp.y), sy1 = fadd(sy.x, sy.y), si = fadd(di.x, di.y);
+          const float syy = ffma(sy.x, dyv[pr].x, fmul(sy.y, dyv[pr].y));
           if (pr == 0) {
-            gm[0] = sx;
-            gm[1] = sy;
-            gm[2] = fmul2(sx, dx);
-            gm[3] = fmul2(sx, dyv[pr]);
-            gm[4] = fmul2(sy, dyv[pr]);
-            gm[5] = dp;
-            gm[6] = fmul2(gw, alm);
+            gv[5] = s1, gv[1] = sy1, gv[4] = syy, gv[6] = si;
           } else {
-            gm[0] = fadd2(gm[0], sx);
-            gm[1] = fadd2(gm[1], sy);
-            gm[2] = ffma2(sx, dx, gm[2]);
-            gm[3] = ffma2(sx, dyv[pr], gm[3]);
-            gm[4] = ffma2(sy, dyv[pr], gm[4]);
-            gm[5] = fadd2(gm[5], dp);
-            gm[6] = ffma2(gw, alm, gm[6]);
+            gv[5] = fadd(gv[5], s1), gv[1] = fadd(gv[1], sy1), gv[4] = fadd(gv[4], syy), gv[6] = fadd(gv[6], si);
           }
         }
         if (__any_sync(0xffffffffu, any_ok)) {
-          float gv[7];
-#pragma unroll
-          for (int t = 0; t < 7; ++t) gv[t] = gm[t].x + gm[t].y;
+          gv[0] = fmul(gv[5], dx.x);
+          gv[2] = fmul(gv[0], dx.x);
+          gv[3] = fmul(gv[1], dx.x);
           // sums over the block's pixels: S_x, S_y, S_xx, S_xy, S_yy, S_1 of dp = dL/dpower
           // times (d, d d^T, 1), and dL/dintensity; lane k (k < 7) ends with the sum of term
           // k, added to the Gaussian's sums.  The rows are the current ring slot's record
