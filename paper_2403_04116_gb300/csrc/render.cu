@@ -197,21 +197,22 @@ __device__ __forceinline__ float warp_sum7_transposed(const float (&v)[7], float
   return fadd(s, __shfl_xor_sync(0xffffffffu, s, 16));
 }
 
-// T / om for om in [0.01, 1] and T in (0, 1], lane by lane: the hardware reciprocal r0
-// (relative error below 2^-22), one Newton step r = r0 + r0 (1 - om r0), the quotient
-// q = T r and one residual correction q + r (T - q om) with the residual formed exactly by
-// an FMA (Markstein).  No operand is zero, infinite, NaN or subnormal here, so none of the
-// special cases of a general division arise.
-__device__ __forceinline__ float2 div_recover(float2 T, float2 om) {
+// T / om for om = 1 - alpha in [0.01, 1] and T in (0, 1], lane by lane, given nom = -om =
+// alpha - 1 (exact, as is 1 - alpha): the hardware reciprocal r0 of om (relative error
+// below 2^-22), one Newton step r = r0 + r0 (1 - om r0), the quotient q = T r and one
+// residual correction q + r (T - q om) with the residual formed exactly by an FMA
+// (Markstein).  Every product with om is written as one with nom, so no operand needs a
+// negation.  No operand is zero, infinite, NaN or subnormal here, so none of the special
+// cases of a general division arise.
+__device__ __forceinline__ float2 div_recover(float2 T, float2 nom) {
   float rx, ry;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rx) : "f"(om.x));
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(om.y));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rx) : "f"(-nom.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(-nom.y));
   float2 r = make_float2(rx, ry);
-  const float2 nom = make_float2(-om.x, -om.y);
-  const float2 e = ffma2(nom, r, f2(1.0f));
+  const float2 e = ffma2(nom, r, f2(1.0f));  // 1 - om r
   r = ffma2(r, e, r);
   const float2 q = fmul2(T, r);
-  const float2 res = ffma2(make_float2(-q.x, -q.y), om, T);
+  const float2 res = ffma2(q, nom, T);  // T - q om
   return ffma2(res, r, q);
 }
 
@@ -537,8 +538,7 @@ __global__ void __launch_bounds__(512) k_render_bwd(const RenderArgs A) {
           any_ok |= ok0 || ok1;
           ncon += (uint32_t)ok0 + (uint32_t)ok1;
           const float2 alm = make_float2(ok0 ? al.x : 0.f, ok1 ? al.y : 0.f);
-          const float2 omal = ffma2(alm, f2(-1.0f), f2(1.0f));
-          Tc[pr] = div_recover(Tc[pr], omal);
+          Tc[pr] = div_recover(Tc[pr], fadd2(alm, f2(-1.0f)));  // T / (1 - alpha)
           const float2 gw = fmul2(G[pr], Tc[pr]);  // dL/dC T; gw alm is the dL/d intensity term
           const float2 ib = ffma2(Ab[pr], f2(-1.0f), make_float2(q3.x, q3.y));  // i - Ab
           const float2 dl_dal = fmul2(gw, ib);
