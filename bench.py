@@ -73,9 +73,9 @@ FP32_LANES = 128
 # source (sha256 prefix of its .cu file and the shared header), workload and (tile_w,
 # tile_h, batch, pixels_per_thread, persistent) they were taken with.
 TRAFFIC = [
-    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "ccd96c6bc1437efe",
-     "bytes_per_launch": 358.7e6},
-    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "ccd96c6bc1437efe",
+    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "bfc57a76d0bb68c4",
+     "bytes_per_launch": 359.7e6},
+    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "bfc57a76d0bb68c4",
      "bytes_per_launch": 149.7e6},
 ]
 
