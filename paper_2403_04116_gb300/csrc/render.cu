@@ -53,8 +53,9 @@ namespace xg {
 // (32 words each), then the current round's entries in the duplicated form (32 x 64 bytes).
 template <int RING>
 __host__ __device__ constexpr int ring_bytes() { return RING * 32 * (32 + 4) + 32 * 64; }
-// the same, for a ring depth known at run time (the launch's dynamic shared memory per warp)
-inline int ring_bytes_rt(int ring) { return ring * 32 * (32 + 4) + 32 * 64; }
+// the same, for a ring depth known at run time (the launch's dynamic shared memory per warp);
+// the forward kernel keeps only the record slots (no indices, no duplicated form)
+inline int ring_bytes_rt(int ring, bool bwd) { return bwd ? ring * 32 * (32 + 4) + 32 * 64 : ring * 32 * 32; }
 static_assert(ring_bytes<3>() == 3 * 32 * 36 + 2048, "ring layout");
 
 struct RenderArgs {
@@ -87,6 +88,12 @@ template <int RING>
 __device__ __forceinline__ float4* warp_ring(int warp_in_cta) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   return reinterpret_cast<float4*>(s_dyn + (size_t)warp_in_cta * ring_bytes<RING>());
+}
+// the forward kernel's ring: RING slots of 32 records, nothing else
+template <int RING>
+__device__ __forceinline__ float4* warp_ring_fwd(int warp_in_cta) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  return reinterpret_cast<float4*>(s_dyn + (size_t)warp_in_cta * RING * 32 * 32);
 }
 // Per warp, after the ring: the round's entries in the duplicated form, one per lane:
 // (u_x u_x u_y u_y), (na na nb nb), (nc nc o o), (i i thr thr) as [4][32] float4.
@@ -300,7 +307,7 @@ template <int PPT, int RING, bool PERSIST>
 __global__ void __launch_bounds__(512) k_render_fwd(const RenderArgs A) {
   constexpr int NP = PPT > 1 ? PPT / 2 : 1;  // pixel pairs per thread
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4* const ring = warp_ring<RING>(warp);
+  float4* const ring = warp_ring_fwd<RING>(warp);
   const bool status_ok = A.st->code == XG_OK;
   uint32_t nev = 0, nct = 0;
   for (uint32_t item = next_item<PERSIST>(A, lane, warp, true);; item = next_item<PERSIST>(A, lane, warp, false)) {
@@ -632,11 +639,11 @@ RenderArgs args_of(const xg_frame* f) {
 int ring_of(int batch) { return batch / 32 + 1; }
 
 // Dynamic shared memory of a compositing block of this configuration.
-size_t block_smem(const xg_config* cfg) {
+size_t block_smem(const xg_config* cfg, bool bwd = true) {
   const int ppt = cfg->pixels_per_thread == 0 ? 2 : cfg->pixels_per_thread;
   const int batch = cfg->batch == 0 ? 64 : cfg->batch;
   const int warps = cfg->persistent ? kPersistWarps : (cfg->tile_w / 8) * (cfg->tile_h / (4 * ppt));
-  return (size_t)warps * (size_t)ring_bytes_rt(ring_of(batch));
+  return (size_t)warps * (size_t)ring_bytes_rt(ring_of(batch), bwd);
 }
 
 cudaError_t launch(xg_frame* f, bool bwd, const RenderArgs& A, cudaStream_t st) {
@@ -652,7 +659,7 @@ cudaError_t launch(xg_frame* f, bool bwd, const RenderArgs& A, cudaStream_t st) 
     if (e != cudaSuccess) return e;
   }
   void* params[] = {(void*)&A};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(warps * 32), params, block_smem(&f->cfg), st);
+  return cudaLaunchKernel(fn, dim3(grid), dim3(warps * 32), params, block_smem(&f->cfg, bwd), st);
 }
 
 }  // namespace
@@ -662,12 +669,12 @@ size_t render_smem_bytes(const xg_config* cfg) { return block_smem(cfg); }
 // The compositing kernels' shared-memory limit and, for the persistent form, the blocks
 // that fit on the device at once.  Called at frame creation (outside any stream capture).
 cudaError_t render_prepare(xg_frame* f) {
-  const size_t smem = block_smem(&f->cfg);
   const bool persist = f->cfg.persistent != 0;
   const int warps = persist ? kPersistWarps : (f->cfg.tile_w / 8) * (f->cfg.tile_h / (4 * f->cfg.pixels_per_thread));
   for (int bwd = 0; bwd < 2; ++bwd) {
     int ring = 0;
     void* fn = kernel_of(bwd != 0, f->cfg.pixels_per_thread, persist, f->cfg.batch, &ring);
+    const size_t smem = block_smem(&f->cfg, bwd != 0);
     cudaFuncAttributes attr;
     cudaError_t e = cudaFuncGetAttributes(&attr, fn);
     if (e != cudaSuccess) return e;
