@@ -199,7 +199,10 @@ __device__ __forceinline__ float warp_sum7_transposed(const float (&v)[7], float
   const int row = min(lane & 7, 6);
   const float4* src = reinterpret_cast<const float4*>(buf + row * 36 + 8 * (lane >> 3));
   const float4 a = src[0], b = src[1];
-  float s = fadd(fadd(fadd(a.x, a.y), fadd(a.z, a.w)), fadd(fadd(b.x, b.y), fadd(b.z, b.w)));
+  // the 8 values as four packed pairs: three packed adds and one scalar add
+  const float2 h = fadd2(fadd2(make_float2(a.x, a.y), make_float2(a.z, a.w)),
+                         fadd2(make_float2(b.x, b.y), make_float2(b.z, b.w)));
+  float s = fadd(h.x, h.y);
   s = fadd(s, __shfl_xor_sync(0xffffffffu, s, 8));
   return fadd(s, __shfl_xor_sync(0xffffffffu, s, 16));
 }
