@@ -73,9 +73,9 @@ FP32_LANES = 128
 # source (sha256 prefix of its .cu file and the shared header), workload and (tile_w,
 # tile_h, batch, pixels_per_thread, persistent) they were taken with.
 TRAFFIC = [
-    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "64550e2e2d263017",
-     "bytes_per_launch": 358.9e6},
-    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "64550e2e2d263017",
+    {"kernel": "k_render_bwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "b750b828f4f1a1db",
+     "bytes_per_launch": 360.3e6},
+    {"kernel": "k_render_fwd", "workload": "train50k", "config": (16, 8, 64, 2, 0), "source_sha": "b750b828f4f1a1db",
      "bytes_per_launch": 149.3e6},
 ]
 
