@@ -452,6 +452,7 @@ __device__ __forceinline__ bool entry_full_rect(const BinGeom& g, const BinWork&
 
 // (R + 1) x (tiles_x + 1) words, R * tiles_x <= max(kBinGroupTiles, tiles_x), R and tiles_x <= 512
 constexpr int kBinDiffWords = kBinGroupTiles + 2 * 512 + 1;
+constexpr int kCountBatch = 4;  // sorted entries a counting thread loads at a time
 
 // Stage 2: pairs per tile of one unit (and group of rows).  Every entry adds its rectangle
 // to a 2-D difference array in four shared atomics; prefix sums along the rows and then
@@ -479,23 +480,54 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(BinGeom g, SortedPlan
   for (int k = threadIdx.x; k < cells; k += kBinThreads) s_d[k] = 0;
   __syncthreads();
   const bool writer = w.r0 == 0;  // the first group writes the sorted rectangles
-  for (int64_t i = w.beg + threadIdx.x; i < w.end; i += kBinThreads) {
-    uint32_t gid;
-    int x0, x1, ya, yb;
-    const bool any = entry_full_rect(g, w, i, ent_gid, count, rect, st, gid, x0, x1, ya, yb);
-    if (writer) {
-      ent_x[i] = any ? (uint32_t)x0 | (uint32_t)x1 << 16 : 0u;
-      ent_y[i] = any ? (uint32_t)ya | (uint32_t)yb << 16 : 1u;
+  // kCountBatch entries per thread at a time: every load of the batch is issued before any
+  // of its results is used (the Gaussian index, then its count and rectangle together)
+  for (int64_t i0 = w.beg + threadIdx.x; i0 < w.end; i0 += kCountBatch * kBinThreads) {
+    uint32_t gid[kCountBatch], cnt[kCountBatch];
+    ushort4 rc[kCountBatch];
+#pragma unroll
+    for (int u = 0; u < kCountBatch; ++u) {
+      const int64_t i = i0 + (int64_t)u * kBinThreads;
+      gid[u] = i < w.end ? ent_gid[i] : 0xffffffffu;
     }
-    if (!any) continue;
-    ya = max(ya, w.r0);
-    yb = min(yb, w.r0 + w.rows - 1);
-    if (ya > yb) continue;
-    const int a = (ya - w.r0) * cols, b = (yb - w.r0 + 1) * cols;
-    atomicAdd(&s_d[a + x0], 1);
-    atomicAdd(&s_d[a + x1 + 1], -1);
-    atomicAdd(&s_d[b + x0], -1);
-    atomicAdd(&s_d[b + x1 + 1], 1);
+#pragma unroll
+    for (int u = 0; u < kCountBatch; ++u) {
+      const bool ok = gid[u] < (uint64_t)g.n;
+      const int64_t vg = (int64_t)w.v * g.n + (ok ? gid[u] : 0u);
+      cnt[u] = ok ? count[vg] : 0u;
+      rc[u] = ok ? rect[vg] : make_ushort4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < kCountBatch; ++u) {
+      const int64_t i = i0 + (int64_t)u * kBinThreads;
+      if (i >= w.end) break;
+      bool any = false;
+      int x0 = 0, x1 = 0, ya = 0, yb = 0;
+      if (gid[u] >= (uint64_t)g.n) {
+        st->code = XG_ERR_CHECK;
+      } else if (cnt[u] != 0u) {
+        const ushort4 r = rc[u];
+        if (r.x > r.z || r.y > r.w || r.z >= g.tiles_x || r.w >= g.tiles_y) {
+          st->code = XG_ERR_CHECK;
+        } else {
+          any = true;
+          x0 = r.x, x1 = r.z, ya = r.y, yb = r.w;
+        }
+      }
+      if (writer) {
+        ent_x[i] = any ? (uint32_t)x0 | (uint32_t)x1 << 16 : 0u;
+        ent_y[i] = any ? (uint32_t)ya | (uint32_t)yb << 16 : 1u;
+      }
+      if (!any) continue;
+      ya = max(ya, w.r0);
+      yb = min(yb, w.r0 + w.rows - 1);
+      if (ya > yb) continue;
+      const int a = (ya - w.r0) * cols, b = (yb - w.r0 + 1) * cols;
+      atomicAdd(&s_d[a + x0], 1);
+      atomicAdd(&s_d[a + x1 + 1], -1);
+      atomicAdd(&s_d[b + x0], -1);
+      atomicAdd(&s_d[b + x1 + 1], 1);
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
